@@ -1,0 +1,396 @@
+"""Benchmark of the GB300 column-wise SpGEMM (one JSON line on rank 0).
+
+A step is one pass of the whole hot path over the workload: input
+validation, Op_j and binning, symbolic pass, scan, numeric pass with sorted
+output (spgemm_symbolic + spgemm_numeric through the C ABI).  Default
+workload: C = A x A with A an R-MAT power-law matrix (2^18 rows, a,b,c,d =
+0.57,0.19,0.19,0.05, 8 edges per row drawn, columns capped at 2000 entries,
+FP64 values U[-1,1]), the largest single product of the workload set.
+
+Metric: GFLOP/s = 2 x sum_j Op_j / step time (Op_j = products of column j).
+Roofline: the binned numeric pass, algorithmic bytes over its event-timed
+duration against the measured HBM copy bandwidth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    3: "C=AxA R-MAT 2^18 (a,b,c,d=0.57,0.19,0.19,0.05, 8 edges/row, col cap 2000), FP64",
+    2: "C=AxB random 2^20 x 2^20, nnz/col U{1..8}, FP64",
+    1: "C=AxA 2D 5-point Laplacian 32x32, FP64",
+}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", type=int, default=3, choices=[1, 2, 3])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="target CPU seconds of the oracle sample")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(A, B, products, nnzC, w):
+    """Numeric pass, per launch: B columns (colptr, rows, values), the
+    gathered A column pointers and A entries of every product, and C written
+    once (colptr read, rows and values written)."""
+    nB = B.ncols
+    nnzB = int(B.colptr[-1])
+    return (8 * (nB + 1) + nnzB * (4 + w) + 16 * nnzB + products * (4 + w)
+            + 8 * (nB + 1) + nnzC * (4 + w))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        out.update(sm_mhz=float(np.median(sm)) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+# --------------------------------------------------------------- workloads
+def make_workload(k):
+    from paper_2303_02471_gb300 import synth
+    A, B = synth.workload(k)
+    return A, B
+
+
+def column_sample(B, frac, seed=0):
+    """Every column of B kept with probability `frac` (a CSC of the subset)."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(seed)
+    cols = np.nonzero(rng.random(B.ncols) < frac)[0]
+    cnt = np.diff(B.colptr)[cols]
+    cp = np.zeros(len(cols) + 1, np.int64)
+    np.cumsum(cnt, out=cp[1:])
+    starts = B.colptr[cols]
+    idx = (np.repeat(starts - cp[:-1], cnt) + np.arange(int(cp[-1]))).astype(np.int64)
+    return SimpleNamespace(nrows=B.nrows, ncols=len(cols), colptr=cp, rowidx=B.rowidx[idx],
+                           values=B.values[idx]), cols
+
+
+def cpu_baseline(A, B, target_s, unit):
+    """The oracle as it stands, on a bounded column sample, all host cores."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    op = oracle.op_counts(A, B)
+    threads = oracle.threads(cores)
+    # estimate the rate on a small sample, then size the timed one
+    small, cols = column_sample(B, 0.005, seed=1)
+    t0 = time.perf_counter()
+    oracle.spgemm(A, small, nthreads=threads)
+    rate = max(1.0, op[cols].sum()) / max(1e-3, time.perf_counter() - t0)
+    frac = min(1.0, target_s * rate / max(1, op.sum()))
+    sample, cols = column_sample(B, frac, seed=2)
+    products = int(op[cols].sum())
+    t0 = time.perf_counter()
+    oracle.spgemm(A, sample, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * products / dt / 1e9, "unit": unit, "cores": threads, "kind": "oracle",
+            "sample": f"{len(cols)} of {B.ncols} columns of B (seeded, p={frac:.4f}), "
+                      f"{products} products, {dt:.2f} s"}
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, rank, world):
+    unit = "GFLOP/s"
+    if rank != 0:
+        return None
+    A, B = make_workload(args.workload)
+    base = cpu_baseline(A, B, min(args.cpu_seconds, 20.0), unit)
+    line = {"impl": "reference", "metric": "SpGEMM GFLOP/s (2 x intermediate products / s)",
+            "value": base["value"], "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": unit, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    return line
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2303_02471_gb300 import _native as N
+    from paper_2303_02471_gb300 import ops
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    A_h, B_h = make_workload(args.workload)
+    w = 8
+    A = ops.CscMatrix.from_host(A_h, device=dev)
+    B = A if B_h is A_h else ops.CscMatrix.from_host(B_h, device=dev)
+    cfg = ops.Config()
+    ncfg = cfg.native()
+    lib = N.lib()
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    cA, cB = ops._csc(A), ops._csc(B)
+    ws = torch.empty(ops.workspace_size(A, B, cfg), dtype=torch.uint8, device=dev)
+    colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def symbolic():
+        nnz, h = ctypes.c_int64(), ctypes.c_void_p()
+        N.check(lib.spgemm_symbolic(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(ncfg),
+                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                    ctypes.c_void_p(colptr.data_ptr()), ctypes.byref(nnz),
+                                    ctypes.byref(h), sp), "spgemm_symbolic")
+        return h, nnz.value
+
+    h, nnz = symbolic()
+    info = ops.Plan(h, ws, A, B, colptr, nnz, cfg).info()
+    products = info["products"]
+    rowidx = torch.empty(nnz, dtype=torch.int32, device=dev)
+    values = torch.empty(nnz, dtype=torch.float64, device=dev)
+    nonempty = sum(1 for b in info["bins"][1:] if b)
+    launches_per_step = 2 + 1 + 1 + nonempty + 3 + nonempty
+
+    def numeric(hh):
+        N.check(lib.spgemm_numeric(hh, ctypes.byref(cA), ctypes.byref(cB),
+                                   ctypes.c_void_p(colptr.data_ptr()),
+                                   ctypes.c_void_p(rowidx.data_ptr()),
+                                   ctypes.c_void_p(values.data_ptr()), sp), "spgemm_numeric")
+
+    lib.spg_plan_destroy(h)
+    for _ in range(args.warmup):
+        hh, _ = symbolic()
+        numeric(hh)
+        lib.spg_plan_destroy(hh)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)  # evict A and B from L2 between steps
+        ev[i][0].record(stream)
+        hh, _ = symbolic()
+        ev[i][1].record(stream)
+        numeric(hh)
+        ev[i][2].record(stream)
+        stream.synchronize()
+        st = lib.spg_plan_check(hh, sp)
+        lib.spg_plan_destroy(hh)
+        N.check(st, "spg_plan_check")
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    num_ms = [b.elapsed_time(c) for a, b, c in ev]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 2.0 * products / (ms * 1e-3) / 1e9
+
+    # roofline of the binned numeric pass
+    peak, peak_kind = peaks()
+    alg = algorithmic_bytes(A_h, B_h, products, nnz, w)
+    num_avg = float(np.mean(num_ms))
+    achieved = alg / (num_avg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "numeric pass (all bin kernels of spgemm_numeric)",
+            "algorithmic_bytes": int(alg), "ms": round(num_avg, 4), "peak_kind": peak_kind}
+
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, A_h, B_h, products, lib, ncfg, dev, stream, world)
+
+    line = None
+    if rank == 0:
+        base = None
+        if not args.no_cpu_baseline and world == 1:
+            base = cpu_baseline(A_h, B_h, args.cpu_seconds, "GFLOP/s")
+        line = {"metric": "SpGEMM GFLOP/s (2 x intermediate products / s)", "value": round(value, 3),
+                "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.workload], "products": int(products),
+                           "nnz_C": int(nnz), "l2": "512 MiB buffer written between timed steps",
+                           "parallelism": f"replicas x{world}"},
+                "phases_ms": {"symbolic": round(float(np.mean([a.elapsed_time(b) for a, b, c in ev])), 4),
+                              "numeric": round(num_avg, 4)},
+                "roofline": roof, "cpu_baseline": base, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps,
+                "clocks": clk}
+    return line
+
+
+def run_e2e(args, A_h, B_h, products, lib, ncfg, dev, stream, world):
+    """Same metric with host inputs and outputs: pinned host CSC in, H2D copy,
+    both phases, D2H copy of C, every step."""
+    import torch
+    from paper_2303_02471_gb300 import _native as N
+    from paper_2303_02471_gb300 import ops
+
+    def pin(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    hA = [pin(A_h.colptr), pin(A_h.rowidx.astype(np.int32)), pin(A_h.values)]
+    same = B_h is A_h
+    hB = hA if same else [pin(B_h.colptr), pin(B_h.rowidx.astype(np.int32)), pin(B_h.values)]
+    dA = [torch.empty_like(x, device=dev) for x in hA]
+    dB = dA if same else [torch.empty_like(x, device=dev) for x in hB]
+    A = ops.CscMatrix(A_h.nrows, A_h.ncols, *dA)
+    B = ops.CscMatrix(B_h.nrows, B_h.ncols, *dB)
+    cA, cB = ops._csc(A), ops._csc(B)
+    ws = torch.empty(ops.workspace_size(A, B), dtype=torch.uint8, device=dev)
+    colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=dev)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    h2d = sum(x.numel() * x.element_size() for x in hA) + (0 if same else sum(x.numel() * x.element_size() for x in hB))
+    out = {}
+
+    def step():
+        for d, hsrc in zip(dA, hA):
+            d.copy_(hsrc, non_blocking=True)
+        if not same:
+            for d, hsrc in zip(dB, hB):
+                d.copy_(hsrc, non_blocking=True)
+        nnz, h = ctypes.c_int64(), ctypes.c_void_p()
+        N.check(lib.spgemm_symbolic(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(ncfg),
+                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                    ctypes.c_void_p(colptr.data_ptr()), ctypes.byref(nnz),
+                                    ctypes.byref(h), sp), "spgemm_symbolic")
+        n = nnz.value
+        if "row" not in out or out["row"].numel() != n:
+            out["row"] = torch.empty(n, dtype=torch.int32, device=dev)
+            out["val"] = torch.empty(n, dtype=torch.float64, device=dev)
+            out["hrow"] = torch.empty(n, dtype=torch.int32, pin_memory=True)
+            out["hval"] = torch.empty(n, dtype=torch.float64, pin_memory=True)
+            out["hcp"] = torch.empty(B.ncols + 1, dtype=torch.int64, pin_memory=True)
+        N.check(lib.spgemm_numeric(h, ctypes.byref(cA), ctypes.byref(cB),
+                                   ctypes.c_void_p(colptr.data_ptr()),
+                                   ctypes.c_void_p(out["row"].data_ptr()),
+                                   ctypes.c_void_p(out["val"].data_ptr()), sp), "spgemm_numeric")
+        out["hcp"].copy_(colptr, non_blocking=True)
+        out["hrow"].copy_(out["row"], non_blocking=True)
+        out["hval"].copy_(out["val"], non_blocking=True)
+        stream.synchronize()
+        st = lib.spg_plan_check(h, sp)
+        lib.spg_plan_destroy(h)
+        N.check(st, "spg_plan_check")
+        return n
+
+    for _ in range(max(1, args.warmup)):
+        n = step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        n = step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    d2h = 8 * (B.ncols + 1) + n * 12
+    return {"value": round(world * 2.0 * products / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": round(ms, 3), "steps": steps}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * spgemm.h -- C ABI of the GB300 (sm_103a) column-wise sparse product
+ * C = A x B on CSC matrices, after arXiv 2303.02471 ("Optimization of SpGEMM
+ * with RISC-V vector instructions").
+ *
+ * The method (Section 3.3, H-HASH(t)): every column j of B gets the
+ * operation count Op_j = sum over stored B_kj of Z^A_k (Section 3.1, Z^A_k =
+ * entries of column k of A).  Columns with Op_j >= t accumulate in a dense
+ * sparse accumulator (SPA, Algorithm 1/2); lighter columns accumulate in a
+ * hash table whose size follows Op_j (Section 3.2, "hash table size
+ * adaptation").  Here the "sort by decreasing Op_j" of Section 3.1 becomes
+ * binning of columns by Op_j, the dense SPA keeps its flags in a bitmap, and
+ * each output column is emitted in ascending row order.
+ *
+ * Conventions for every entry point
+ *   - Matrices are CSC (Section 2.1): column pointers int64[ncols + 1] with
+ *     colptr[0] = 0 and colptr[ncols] = nnz, row indices int32[nnz], values
+ *     double or float[nnz].  Rows inside an input column may come in any
+ *     order but must not repeat.  All matrix arrays are DEVICE pointers.
+ *   - The caller owns all device memory (inputs, outputs, workspace); the
+ *     library never allocates device memory.  It owns only the host-side
+ *     plan object (spg_plan), freed by spg_plan_destroy.
+ *   - Every call returns spg_status; no C++ exception crosses the ABI.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Kernels
+ *     are enqueued on it; calls documented as synchronising wait for it.
+ *   - Errors found by a kernel (bad input, table overflow) are written to an
+ *     error word in the workspace and reported by the next synchronising
+ *     call (spgemm_symbolic, spg_plan_check).
+ *   - The output pattern is the structural boolean product of the stored
+ *     patterns: an entry formed by at least one product A_ik * B_kj is
+ *     stored even if the products cancel to 0 (Algorithm 1 flags every
+ *     touched row).  Output rows are sorted ascending in every column.
+ */
+#ifndef SPGEMM_GB300_H
+#define SPGEMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque CUDA stream (binary-compatible with cudaStream_t). */
+typedef struct CUstream_st *spg_stream;
+
+typedef enum {
+    SPG_OK = 0,
+    SPG_ERR_INVALID = 1,        /* bad argument or malformed CSC input */
+    SPG_ERR_WORKSPACE = 2,      /* workspace missing or too small */
+    SPG_ERR_TABLE_OVERFLOW = 3, /* a hash table ran out of slots (bounded probe) */
+    SPG_ERR_TIMEOUT = 4,        /* a bounded device loop hit its limit */
+    SPG_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    SPG_ERR_UNSUPPORTED = 6,    /* shape or option outside what is built */
+    SPG_ERR_INDEX_OVERFLOW = 7  /* a size does not fit the index types */
+} spg_status;
+
+typedef enum { SPG_F64 = 0, SPG_F32 = 1 } spg_dtype;
+
+/* A CSC matrix on the device (Section 2.1).  `values` may be NULL where only
+ * the pattern is read (symbolic phase). */
+typedef struct {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    const int64_t *colptr; /* device, ncols + 1 */
+    const int32_t *rowidx; /* device, nnz */
+    const void *values;    /* device, nnz elements of `dtype` */
+    int32_t dtype;         /* spg_dtype */
+} spg_csc;
+
+/* Tuning knobs.  spg_config_default fills the defaults. */
+typedef struct {
+    /* Threshold t of H-HASH(t) (Section 3.3): a column with Op_j >= t uses
+     * the dense SPA, a column with 0 < Op_j < t a hash table.  t = 0 sends
+     * every non-empty column to the dense SPA; INT64_MAX ("infinity") sends
+     * all to hash tables; a negative value picks the library default
+     * (hash_cta_max + 1). */
+    int64_t t;
+    /* Largest Op_j served by shared-memory hash tables; must be one of
+     * 256, 512, 1024, 2048, 4096 or 8192.  Hash columns above it use a
+     * per-CTA global-memory table. */
+    int32_t hash_cta_max;
+    /* Threads per CTA for the CTA-per-column kernels (128..1024, multiple
+     * of 32). */
+    int32_t cta_threads;
+    /* Nonzero: check the CSC inputs on the device in spgemm_symbolic
+     * (colptr monotone with colptr[0] = 0 and colptr[n] = nnz, rows in
+     * range) and fail with SPG_ERR_INVALID. */
+    int32_t validate;
+    /* Test knob, normally 0: divide every hash-table size by 2^shrink so
+     * that the bounded probe loop reports SPG_ERR_TABLE_OVERFLOW. */
+    int32_t table_shrink;
+    /* Cap on the bytes of per-CTA global scratch (global hash tables and
+     * bitmaps); the number of CTAs that use such scratch shrinks to fit. */
+    int64_t scratch_cap_bytes;
+} spg_config;
+
+typedef struct spg_plan spg_plan;
+
+/* Fill `cfg` with the defaults. */
+spg_status spg_config_default(spg_config *cfg);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *spg_status_string(spg_status s);
+
+/*
+ * Bytes of device workspace that spgemm_symbolic needs for C = A x B with
+ * `cfg` (NULL = defaults).  Depends only on the shapes, nnz and dtype of A
+ * and B, so it can be queried before any data exists.  The workspace also
+ * holds the plan's device state (Op_j, bins) used later by spgemm_numeric
+ * and spgemm_backward, so it must stay allocated and unmodified until the
+ * plan is destroyed.  Does not touch the device.
+ */
+spg_status spgemm_workspace_size(const spg_csc *A, const spg_csc *B,
+                                 const spg_config *cfg, size_t *bytes);
+
+/*
+ * Symbolic phase of C = A x B (Gustavson by columns, Section 2.1).
+ *
+ * Steps on `stream`: (optional) input validation; Op_j of every column of B
+ * (Section 3.1) and its bin (empty / hash table sized by Op_j / dense SPA,
+ * Sections 3.2-3.3); per-bin column lists; nnz of every C column by the
+ * bin's accumulator; exclusive scan into C_colptr.
+ *
+ * A, B     device CSC; values are not read.  A->ncols == B->nrows,
+ *          A->dtype == B->dtype.
+ * cfg      tuning (NULL = defaults); copied into the plan.
+ * workspace, ws_bytes   device buffer of at least spgemm_workspace_size
+ *          bytes, 256-byte aligned, owned by the caller.
+ * C_colptr device int64[B->ncols + 1], written (C_colptr[0] = 0).
+ * nnzC     host, receives nnz(C) = C_colptr[B->ncols].
+ * plan     receives a new plan (host object) on success; NULL on error.
+ *
+ * Synchronises `stream` (it reads the bin histogram and nnz(C) back to the
+ * host).  Errors: SPG_ERR_INVALID (shapes, dtypes, NULL pointers, or a
+ * malformed input when cfg->validate), SPG_ERR_WORKSPACE, SPG_ERR_INDEX_OVERFLOW
+ * (a dimension beyond int32 rows), SPG_ERR_TABLE_OVERFLOW, SPG_ERR_CUDA.
+ */
+spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B,
+                           const spg_config *cfg, void *workspace,
+                           size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC,
+                           spg_plan **plan, spg_stream stream);
+
+/*
+ * Numeric phase: values and sorted row indices of C = A x B into caller
+ * buffers, column by column with the accumulator the plan chose per bin
+ * (dense SPA of Algorithm 1 for Op_j >= t, hash table of Section 3.2
+ * otherwise), then each column in ascending row order.
+ *
+ * plan     from spgemm_symbolic on the same A and B patterns (values may
+ *          differ); its workspace must still be allocated.
+ * A, B     device CSC with values of the plan's dtype.
+ * C_colptr the array spgemm_symbolic wrote.
+ * C_rowidx device int32[nnzC], written.
+ * C_values device values[nnzC] of the plan's dtype, written.  Values are
+ *          summed in the input dtype (float inputs accumulate in float).
+ *
+ * Asynchronous: does not synchronise.  Kernel-side errors surface in
+ * spg_plan_check.  Errors returned directly: SPG_ERR_INVALID (plan/shape
+ * mismatch, NULL pointers), SPG_ERR_CUDA (launch failure).
+ */
+spg_status spgemm_numeric(spg_plan *plan, const spg_csc *A, const spg_csc *B,
+                          const int64_t *C_colptr, int32_t *C_rowidx,
+                          void *C_values, spg_stream stream);
+
+/*
+ * Backward of C = A x B with respect to the stored values of A and B (the
+ * patterns are fixed):
+ *   dA_ik = sum_{j: B_kj stored} dC_ij B_kj   for every stored (i, k) of A,
+ *   dB_kj = sum_i A_ik dC_ij                  for every stored (k, j) of B,
+ * i.e. dA = (dC B^T) sampled on pattern(A) and dB = (A^T dC) sampled on
+ * pattern(B).  The paper has no backward; these are the derivatives of
+ * C_ij = sum_k A_ik B_kj.  Both are masked products that walk the same
+ * products as the forward, reusing the plan's bins: per column j, dC[:, j]
+ * is loaded into the bin's accumulator (hash table or dense SPA) and every
+ * product A_ik B_kj looks up dC_ij.
+ *
+ * C_colptr, C_rowidx   the forward's output pattern (sorted rows).
+ * dC_values            device values[nnzC] (plan dtype).
+ * dA_values            device values[A->nnz] or NULL (not computed).
+ * dB_values            device values[B->nnz] or NULL (not computed).
+ * Asynchronous; errors as for spgemm_numeric.
+ */
+spg_status spgemm_backward(spg_plan *plan, const spg_csc *A, const spg_csc *B,
+                           const int64_t *C_colptr, const int32_t *C_rowidx,
+                           const void *dC_values, void *dA_values,
+                           void *dB_values, spg_stream stream);
+
+/* Synchronise `stream` and report the first kernel-side error recorded in
+ * the plan's workspace since spgemm_symbolic (SPG_OK if none). */
+spg_status spg_plan_check(spg_plan *plan, spg_stream stream);
+
+/* Release the host plan (the workspace stays the caller's). */
+spg_status spg_plan_destroy(spg_plan *plan);
+
+/*
+ * Plan introspection for tests and reports (host side, no device work):
+ *   nbins        receives the number of bins (may be NULL);
+ *   bin_counts   host int64[nbins]: columns per bin (may be NULL);
+ *   products     receives sum_j Op_j (may be NULL);
+ *   t_effective  receives the threshold t the plan used (may be NULL).
+ * Bin order: 0 empty (Op_j = 0); 1..6 warp-level hash bins for
+ * Op_j <= 8, 16, 32, 64, 128, 256; 7..11 CTA-level shared-memory hash bins for
+ * Op_j <= 512 .. 8192; 12 global-memory hash; 13 dense SPA (Op_j >= t).
+ */
+spg_status spg_plan_info(const spg_plan *plan, int32_t *nbins,
+                         int64_t *bin_counts, int64_t *products,
+                         int64_t *t_effective);
+
+/* Copy Op_j (int64[B->ncols], Section 3.1) from the plan's workspace into
+ * the device buffer `op_out` on `stream` (asynchronous). */
+spg_status spg_plan_op_counts(const spg_plan *plan, int64_t *op_out,
+                              spg_stream stream);
+
+/*
+ * Transpose of a CSC matrix M (m x n) into CSC of M^T (n x m): row k of M
+ * becomes column k.  Pure data movement; the Galerkin product P^T (A P) of
+ * the differentiable workload needs P^T as a CSC operand.
+ *
+ * M            device CSC (values may be NULL: then T_values is not written).
+ * T_colptr     device int64[M->nrows + 1], written.
+ * T_rowidx     device int32[M->nnz], written; rows inside each output column
+ *              are in ascending order.
+ * T_values     device values[M->nnz] (M's dtype) or NULL.
+ * perm         device int64[M->nnz] or NULL: T_values[e] = M.values[perm[e]].
+ * workspace    device buffer of spg_transpose_workspace_size bytes.
+ * Asynchronous.  Errors: SPG_ERR_INVALID, SPG_ERR_WORKSPACE, SPG_ERR_CUDA.
+ */
+spg_status spg_transpose_workspace_size(const spg_csc *M, size_t *bytes);
+spg_status spg_csc_transpose(const spg_csc *M, int64_t *T_colptr,
+                             int32_t *T_rowidx, void *T_values, int64_t *perm,
+                             void *workspace, size_t ws_bytes,
+                             spg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_GB300_H */

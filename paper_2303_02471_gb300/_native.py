@@ -1,0 +1,81 @@
+"""ctypes view of the C ABI in include/spgemm.h (libspgemm.so, built in-tree).
+
+There is no fallback: if the library is missing or fails to load, every call
+raises.  Build it with ``python -m paper_2303_02471_gb300.build`` or
+``__graft_entry__.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspgemm.so")
+
+i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+SPG_F64, SPG_F32 = 0, 1
+STATUS = {
+    0: "SPG_OK", 1: "SPG_ERR_INVALID", 2: "SPG_ERR_WORKSPACE", 3: "SPG_ERR_TABLE_OVERFLOW",
+    4: "SPG_ERR_TIMEOUT", 5: "SPG_ERR_CUDA", 6: "SPG_ERR_UNSUPPORTED", 7: "SPG_ERR_INDEX_OVERFLOW",
+}
+INT64_MAX = (1 << 63) - 1
+
+
+class SpgCsc(ctypes.Structure):
+    _fields_ = [("nrows", i64), ("ncols", i64), ("nnz", i64), ("colptr", vp), ("rowidx", vp),
+                ("values", vp), ("dtype", i32)]
+
+
+class SpgConfig(ctypes.Structure):
+    _fields_ = [("t", i64), ("hash_cta_max", i32), ("cta_threads", i32), ("validate", i32),
+                ("table_shrink", i32), ("scratch_cap_bytes", i64)]
+
+
+class SpgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        self.name = STATUS.get(status, f"status {status}")
+        super().__init__(f"{where}: {self.name}")
+
+
+# name -> (restype, argtypes); every symbol include/spgemm.h declares
+SIGNATURES = {
+    "spg_config_default": (i32, [vp]),
+    "spg_status_string": (ctypes.c_char_p, [i32]),
+    "spgemm_workspace_size": (i32, [vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "spgemm_symbolic": (i32, [vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(i64),
+                              ctypes.POINTER(vp), vp]),
+    "spgemm_numeric": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+    "spgemm_backward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "spg_plan_check": (i32, [vp, vp]),
+    "spg_plan_destroy": (i32, [vp]),
+    "spg_plan_info": (i32, [vp, ctypes.POINTER(i32), vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+    "spg_plan_op_counts": (i32, [vp, vp, vp]),
+    "spg_transpose_workspace_size": (i32, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "spg_csc_transpose": (i32, [vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is not built; run `python -m paper_2303_02471_gb300.build` "
+                "(the CUDA path has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != 0:
+        raise SpgError(status, where)

@@ -1,0 +1,376 @@
+// Host side of the C ABI (include/spgemm.h): argument checks, workspace
+// layout, plan object, and the launch sequence of the symbolic, numeric and
+// backward phases.  No device memory is allocated here: everything lives in
+// the caller's workspace and output buffers.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "kernels.cuh"
+
+using namespace spg;
+
+namespace {
+
+struct DeviceInfo {
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+
+DeviceInfo device_info(int dev) {
+    static std::mutex mu;
+    static DeviceInfo cache[64];
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64) return DeviceInfo{};
+    if (cache[dev].sms == 0) {
+        int sms = 0, optin = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cache[dev].sms = sms > 0 ? sms : 1;
+        // keep a little room for the kernels' static shared memory
+        cache[dev].smem_optin = optin > 4096 ? (size_t)optin - 1024 : 48 * 1024;
+    }
+    return cache[dev];
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t ctrl = 0, op = 0, cols = 0, tiles = 0, scratch = 0, total = 0;
+    size_t scratch_stride = 0;
+    int64_t scratch_ctas = 0;
+};
+
+spg_config normalized(const spg_config *cfg) {
+    spg_config c;
+    spg_config_default(&c);
+    if (cfg) c = *cfg;
+    return c;
+}
+
+int64_t effective_t(const spg_config &c) { return c.t < 0 ? (int64_t)c.hash_cta_max + 1 : c.t; }
+
+bool valid_hash_max(int32_t h) {
+    return h == 256 || h == 512 || h == 1024 || h == 2048 || h == 4096 || h == 8192;
+}
+
+Layout make_layout(int64_t m, int64_t nB, int64_t nnzA, int dtype, const spg_config &c, int sms) {
+    Layout L;
+    const size_t w = dtype == SPG_F64 ? 8 : 4;
+    const int64_t W = ceil_div(m, 32);
+    const int64_t hmax = c.hash_cta_max;
+    size_t off = 0;
+    L.ctrl = off; off = align256(off + sizeof(Ctrl));
+    L.op = off; off = align256(off + (size_t)nB * 8);
+    L.cols = off; off = align256(off + (size_t)nB * 4);
+    L.tiles = off; off = align256(off + (size_t)scan_tile_count(nB) * 8);
+    // per-CTA global scratch: a bitmap (uint2 per 32 rows) plus, for hash
+    // tables that do not fit shared memory, keys and values
+    const int64_t reach = std::min<int64_t>(std::max<int64_t>(nnzA, 1), std::max<int64_t>(m, 1));
+    size_t tab = (size_t)num_slots(std::min<int64_t>(hmax, reach)) * (4 + w) + 32;
+    if (effective_t(c) > hmax + 1) {
+        const size_t sym = (size_t)global_sym_slots(reach, m) * 4;
+        const size_t num = (size_t)num_slots(reach) * (4 + w) + 32;
+        tab = std::max(tab, std::max(sym, num));
+    }
+    L.scratch_stride = align256((size_t)W * 8) + align256(tab);
+    int64_t ctas = 2 * (int64_t)sms;
+    if (c.scratch_cap_bytes > 0) {
+        int64_t fit = c.scratch_cap_bytes / (int64_t)L.scratch_stride;
+        if (fit < ctas) ctas = fit;
+    }
+    if (ctas < 1) ctas = 1;
+    L.scratch_ctas = ctas;
+    L.scratch = off;
+    off = align256(off + (size_t)ctas * L.scratch_stride);
+    L.total = off;
+    return L;
+}
+
+spg_status check_csc(const spg_csc *M, bool need_values) {
+    if (!M) return SPG_ERR_INVALID;
+    if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0) return SPG_ERR_INVALID;
+    if (M->nrows > INT32_MAX || M->ncols > INT32_MAX) return SPG_ERR_INDEX_OVERFLOW;
+    if (M->dtype != SPG_F64 && M->dtype != SPG_F32) return SPG_ERR_INVALID;
+    if (!M->colptr) return SPG_ERR_INVALID;
+    if (M->nnz > 0 && (!M->rowidx || (need_values && !M->values))) return SPG_ERR_INVALID;
+    return SPG_OK;
+}
+
+spg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SPG_OK : SPG_ERR_CUDA; }
+
+}  // namespace
+
+struct spg_plan {
+    int device = 0;
+    DeviceInfo dev;
+    int64_t mA = 0, nA = 0, nB = 0, nnzA = 0, nnzB = 0;
+    int dtype = 0;
+    spg_config cfg{};
+    int64_t t_eff = 0;
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout L;
+    Ctrl host{};
+    BinOffsets off{};
+    int64_t nnzC = 0;
+    Geo num_geo[NBINS];
+    bool num_geo_ready = false;
+
+    Ctrl *ctrl() const { return reinterpret_cast<Ctrl *>(ws + L.ctrl); }
+    int64_t *op() const { return reinterpret_cast<int64_t *>(ws + L.op); }
+    int32_t *cols() const { return reinterpret_cast<int32_t *>(ws + L.cols); }
+    int64_t *tiles() const { return reinterpret_cast<int64_t *>(ws + L.tiles); }
+    unsigned char *scratch() const { return ws + L.scratch; }
+
+    BinTask task(int b) const {
+        BinTask t;
+        t.cols = cols() + off.v[b];
+        t.count = (int64_t)host.hist[b];
+        t.bin = b;
+        t.shrink = cfg.table_shrink;
+        t.m = mA;
+        t.W = ceil_div(mA, 32);
+        t.op = op();
+        t.scratch = scratch();
+        t.scratch_stride = L.scratch_stride;
+        t.ctrl = ctrl();
+        return t;
+    }
+};
+
+extern "C" {
+
+spg_status spg_config_default(spg_config *cfg) {
+    if (!cfg) return SPG_ERR_INVALID;
+    cfg->t = -1;
+    cfg->hash_cta_max = 8192;
+    cfg->cta_threads = 512;
+    cfg->validate = 1;
+    cfg->table_shrink = 0;
+    cfg->scratch_cap_bytes = (int64_t)1 << 30;
+    return SPG_OK;
+}
+
+const char *spg_status_string(spg_status s) {
+    switch (s) {
+        case SPG_OK: return "SPG_OK";
+        case SPG_ERR_INVALID: return "SPG_ERR_INVALID: bad argument or malformed CSC input";
+        case SPG_ERR_WORKSPACE: return "SPG_ERR_WORKSPACE: workspace missing or too small";
+        case SPG_ERR_TABLE_OVERFLOW: return "SPG_ERR_TABLE_OVERFLOW: a hash table ran out of slots";
+        case SPG_ERR_TIMEOUT: return "SPG_ERR_TIMEOUT: a bounded device loop hit its limit";
+        case SPG_ERR_CUDA: return "SPG_ERR_CUDA: a CUDA runtime call failed";
+        case SPG_ERR_UNSUPPORTED: return "SPG_ERR_UNSUPPORTED: shape or option not supported";
+        case SPG_ERR_INDEX_OVERFLOW: return "SPG_ERR_INDEX_OVERFLOW: a size exceeds the index types";
+    }
+    return "SPG_ERR_UNKNOWN";
+}
+
+static spg_status check_pair(const spg_csc *A, const spg_csc *B, bool values) {
+    spg_status s = check_csc(A, values);
+    if (s != SPG_OK) return s;
+    s = check_csc(B, values);
+    if (s != SPG_OK) return s;
+    if (A->ncols != B->nrows || A->dtype != B->dtype) return SPG_ERR_INVALID;
+    return SPG_OK;
+}
+
+static spg_status check_config(const spg_config &c) {
+    if (!valid_hash_max(c.hash_cta_max)) return SPG_ERR_INVALID;
+    if (c.cta_threads < 128 || c.cta_threads > 1024 || c.cta_threads % 32) return SPG_ERR_INVALID;
+    if (c.table_shrink < 0 || c.table_shrink > 30) return SPG_ERR_INVALID;
+    return SPG_OK;
+}
+
+spg_status spgemm_workspace_size(const spg_csc *A, const spg_csc *B, const spg_config *cfg, size_t *bytes) {
+    if (!bytes) return SPG_ERR_INVALID;
+    spg_status s = check_pair(A, B, false);
+    if (s != SPG_OK) return s;
+    spg_config c = normalized(cfg);
+    if ((s = check_config(c)) != SPG_OK) return s;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPG_ERR_CUDA;
+    DeviceInfo di = device_info(dev);
+    *bytes = make_layout(A->nrows, B->ncols, A->nnz, A->dtype, c, di.sms).total;
+    return SPG_OK;
+}
+
+spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config *cfg, void *workspace,
+                           size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC, spg_plan **plan_out,
+                           spg_stream stream) {
+    if (plan_out) *plan_out = nullptr;
+    if (!C_colptr || !nnzC || !plan_out) return SPG_ERR_INVALID;
+    spg_status st = check_pair(A, B, false);
+    if (st != SPG_OK) return st;
+    spg_config c = normalized(cfg);
+    if ((st = check_config(c)) != SPG_OK) return st;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return SPG_ERR_WORKSPACE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPG_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    spg_plan *P = new (std::nothrow) spg_plan();
+    if (!P) return SPG_ERR_INVALID;
+    P->device = dev;
+    P->dev = device_info(dev);
+    P->mA = A->nrows; P->nA = A->ncols; P->nB = B->ncols;
+    P->nnzA = A->nnz; P->nnzB = B->nnz;
+    P->dtype = A->dtype;
+    P->cfg = c;
+    P->t_eff = effective_t(c);
+    P->L = make_layout(P->mA, P->nB, P->nnzA, P->dtype, c, P->dev.sms);
+    if (ws_bytes < P->L.total) { delete P; return SPG_ERR_WORKSPACE; }
+    P->ws = static_cast<unsigned char *>(workspace);
+    P->ws_bytes = ws_bytes;
+    const int64_t hmax = c.hash_cta_max;
+    Ctrl *ctrl = P->ctrl();
+
+#define CK(expr)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (expr);                                      \
+        if (e_ != cudaSuccess) { delete P; return SPG_ERR_CUDA; }     \
+    } while (0)
+
+    CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    if (c.validate) {
+        const int vg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max(A->nnz, A->ncols + 1), 256), 8 * P->dev.sms));
+        k_validate<<<vg, 256, 0, s>>>(A->colptr, A->rowidx, A->nrows, A->ncols, A->nnz, 0, ctrl);
+        const int vb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max(B->nnz, B->ncols + 1), 256), 8 * P->dev.sms));
+        k_validate<<<vb, 256, 0, s>>>(B->colptr, B->rowidx, B->nrows, B->ncols, B->nnz, 1, ctrl);
+        CK(cudaGetLastError());
+        // a malformed colptr would make the walks read out of bounds: stop here
+        CK(cudaMemcpyAsync(&P->host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
+    }
+    if (P->nB > 0) {
+        const int g = (int)std::min<int64_t>(ceil_div(P->nB, 256), 16 * (int64_t)P->dev.sms);
+        k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->op(), C_colptr, ctrl);
+        CK(cudaGetLastError());
+    } else {
+        CK(cudaMemsetAsync(C_colptr, 0, sizeof(int64_t), s));
+    }
+    CK(cudaMemcpyAsync(&P->host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
+    P->off.v[0] = 0;
+    for (int b = 0; b < NBINS; ++b) {
+        // empty columns are not listed
+        const int64_t n = b == BIN_EMPTY ? 0 : (int64_t)P->host.hist[b];
+        P->off.v[b + 1] = P->off.v[b] + n;
+    }
+    if (P->nB > 0) {
+        k_bin_scatter<<<(unsigned)ceil_div(P->nB, 256), 256, 0, s>>>(P->op(), P->nB, P->t_eff, hmax, P->off,
+                                                                    P->cols(), ctrl);
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s));
+    Operands o{A->colptr, A->rowidx, nullptr, B->colptr, B->rowidx, nullptr};
+    for (int b = 1; b < NBINS; ++b) {
+        if (!P->host.hist[b]) continue;
+        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mA, c.cta_threads, P->dev.sms, P->dev.smem_optin,
+                                  (int64_t)P->host.maxop[b], c.table_shrink, P->L.scratch_ctas);
+        CK(launch_symbolic_bin(P->task(b), o, C_colptr, g, s));
+    }
+    CK(launch_inclusive_scan(C_colptr + 1, P->nB, P->tiles(), s));
+    CK(cudaMemcpyAsync(&P->nnzC, C_colptr + P->nB, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&P->host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+#undef CK
+    if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
+    for (int b = 1; b < NBINS; ++b) {
+        if (!P->host.hist[b]) continue;
+        P->num_geo[b] = numeric_geometry(b, (int64_t)P->host.hist[b], P->mA, c.cta_threads, P->dev.sms,
+                                         P->dev.smem_optin, (int64_t)P->host.maxnnz[b], P->dtype, c.table_shrink,
+                                         P->L.scratch_ctas);
+    }
+    P->num_geo_ready = true;
+    *nnzC = P->nnzC;
+    *plan_out = P;
+    return SPG_OK;
+}
+
+static spg_status check_plan_operands(const spg_plan *P, const spg_csc *A, const spg_csc *B) {
+    if (!P) return SPG_ERR_INVALID;
+    spg_status st = check_pair(A, B, true);
+    if (st != SPG_OK) return st;
+    if (A->nrows != P->mA || A->ncols != P->nA || B->ncols != P->nB || A->nnz != P->nnzA || B->nnz != P->nnzB ||
+        A->dtype != P->dtype)
+        return SPG_ERR_INVALID;
+    return SPG_OK;
+}
+
+spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const int64_t *C_colptr,
+                          int32_t *C_rowidx, void *C_values, spg_stream stream) {
+    spg_status st = check_plan_operands(P, A, B);
+    if (st != SPG_OK) return st;
+    if (!C_colptr || (P->nnzC > 0 && (!C_rowidx || !C_values))) return SPG_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ctrl *ctrl = P->ctrl();
+    if (cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s) != cudaSuccess) return SPG_ERR_CUDA;
+    Operands o{A->colptr, A->rowidx, A->values, B->colptr, B->rowidx, B->values};
+    for (int b = 1; b < NBINS; ++b) {
+        if (!P->host.hist[b]) continue;
+        cudaError_t e = launch_numeric_bin(P->task(b), o, C_colptr, C_rowidx, C_values, P->dtype, P->num_geo[b], s);
+        if (e != cudaSuccess) return SPG_ERR_CUDA;
+    }
+    return SPG_OK;
+}
+
+spg_status spgemm_backward(spg_plan *P, const spg_csc *A, const spg_csc *B, const int64_t *C_colptr,
+                           const int32_t *C_rowidx, const void *dC_values, void *dA_values, void *dB_values,
+                           spg_stream stream) {
+    spg_status st = check_plan_operands(P, A, B);
+    if (st != SPG_OK) return st;
+    (void)C_colptr; (void)C_rowidx; (void)dC_values; (void)dA_values; (void)dB_values; (void)stream;
+    return SPG_ERR_UNSUPPORTED;
+}
+
+spg_status spg_plan_check(spg_plan *P, spg_stream stream) {
+    if (!P) return SPG_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int32_t err = 0;
+    if (cudaMemcpyAsync(&err, &P->ctrl()->err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SPG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SPG_ERR_CUDA;
+    return (spg_status)err;
+}
+
+spg_status spg_plan_destroy(spg_plan *P) {
+    delete P;
+    return SPG_OK;
+}
+
+spg_status spg_plan_info(const spg_plan *P, int32_t *nbins, int64_t *bin_counts, int64_t *products,
+                         int64_t *t_effective) {
+    if (!P) return SPG_ERR_INVALID;
+    if (nbins) *nbins = NBINS;
+    if (bin_counts)
+        for (int b = 0; b < NBINS; ++b) bin_counts[b] = (int64_t)P->host.hist[b];
+    if (products) *products = (int64_t)P->host.products;
+    if (t_effective) *t_effective = P->t_eff;
+    return SPG_OK;
+}
+
+spg_status spg_plan_op_counts(const spg_plan *P, int64_t *op_out, spg_stream stream) {
+    if (!P || (!op_out && P->nB > 0)) return SPG_ERR_INVALID;
+    if (P->nB == 0) return SPG_OK;
+    return cuda_status(cudaMemcpyAsync(op_out, P->op(), (size_t)P->nB * 8, cudaMemcpyDeviceToDevice,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+spg_status spg_transpose_workspace_size(const spg_csc *M, size_t *bytes) {
+    if (!M || !bytes) return SPG_ERR_INVALID;
+    (void)M;
+    return SPG_ERR_UNSUPPORTED;
+}
+
+spg_status spg_csc_transpose(const spg_csc *M, int64_t *T_colptr, int32_t *T_rowidx, void *T_values, int64_t *perm,
+                             void *workspace, size_t ws_bytes, spg_stream stream) {
+    (void)M; (void)T_colptr; (void)T_rowidx; (void)T_values; (void)perm; (void)workspace; (void)ws_bytes;
+    (void)stream;
+    return SPG_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,328 @@
+// Device building blocks and kernel launchers of the column-wise SpGEMM.
+//
+// Every kernel walks the products of a column j of C the same way
+// (Gustavson by columns, Section 2.1): for each stored B_kj, every stored
+// A_ik gives the product A_ik * B_kj for row i.  The walk flattens the
+// products of a chunk of B entries so that consecutive lanes take
+// consecutive entries of an A column (coalesced), with the owning B entry
+// found by a binary search over the chunk's prefix sums of Z^A_k.
+#pragma once
+
+#include <algorithm>
+
+#include "spgemm_internal.cuh"
+
+namespace spg {
+
+struct BinOffsets { int64_t v[NBINS + 1]; };
+
+// ------------------------------------------------------------ group walk
+// A group of G lanes (G divides 32) walks the products of B entries
+// [p0, p1) in chunks of G entries.  f(row, product) runs once per product
+// on the lane that owns it.  All lanes of the group must call this with the
+// same arguments.
+template <int G, bool VALS, typename VT, typename F>
+__device__ __forceinline__ void group_products(unsigned mask, const int64_t *__restrict__ Acp,
+                                               const int32_t *__restrict__ Arow,
+                                               const VT *__restrict__ Aval,
+                                               const int32_t *__restrict__ Brow,
+                                               const VT *__restrict__ Bval, int64_t p0, int64_t p1,
+                                               F &&f) {
+    const int gl = threadIdx.x & (G - 1);
+    for (int64_t base = p0; base < p1; base += G) {
+        const int64_t p = base + gl;
+        int z = 0;
+        int64_t a0 = 0;
+        VT bv = VT(0);
+        if (p < p1) {
+            const int32_t k = Brow[p];
+            a0 = Acp[k];
+            z = static_cast<int>(Acp[k + 1] - a0);
+            if (VALS) bv = Bval[p];
+        }
+        const int incl = group_incl_scan<G>(mask, z);
+        const int total = __shfl_sync(mask, incl, G - 1, G);
+        const int excl = incl - z;
+        for (int q0 = 0; q0 < total; q0 += G) {
+            const int q = q0 + gl;
+            int s = 0;
+#pragma unroll
+            for (int step = G / 2; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(mask, excl, s + step, G);
+                if (ex <= q) s += step;
+            }
+            const int64_t a0s = __shfl_sync(mask, a0, s, G);
+            const int exs = __shfl_sync(mask, excl, s, G);
+            VT bvs = VT(0);
+            if (VALS) bvs = __shfl_sync(mask, bv, s, G);
+            if (q < total) {
+                const int64_t qa = a0s + (q - exs);
+                const int32_t row = Arow[qa];
+                VT prod = VT(0);
+                if (VALS) prod = Aval[qa] * bvs;
+                f(row, prod);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- CTA walk
+__device__ __forceinline__ int64_t cta_incl_scan_i64(int64_t v, int64_t *s_warp, int64_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int64_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int64_t o = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += o;
+        }
+        if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[nw - 1];
+    const int64_t r = v + (warp > 0 ? s_warp[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+// Shared scratch of the CTA walk: one B entry per thread of the chunk.
+template <typename VT>
+struct WalkSmem {
+    int64_t *excl;  // [blockDim]
+    int64_t *a0;    // [blockDim]
+    VT *bv;         // [blockDim]
+    int64_t *warp;  // [32]
+};
+
+template <typename VT>
+__host__ __device__ inline size_t walk_smem_bytes(int threads) {
+    return (size_t)threads * (16 + sizeof(VT)) + 32 * 8;
+}
+
+template <typename VT>
+__device__ __forceinline__ WalkSmem<VT> carve_walk(unsigned char *&p) {
+    WalkSmem<VT> w;
+    w.excl = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
+    w.a0 = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
+    w.warp = reinterpret_cast<int64_t *>(p); p += 32 * 8;
+    w.bv = reinterpret_cast<VT *>(p); p += (size_t)blockDim.x * sizeof(VT);
+    p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+    return w;
+}
+
+// The whole CTA walks the products of B entries [p0, p1); f(row, product)
+// per product.  Contains __syncthreads: every thread must call it.
+template <bool VALS, typename VT, typename F>
+__device__ __forceinline__ void cta_products(const int64_t *__restrict__ Acp,
+                                             const int32_t *__restrict__ Arow,
+                                             const VT *__restrict__ Aval,
+                                             const int32_t *__restrict__ Brow,
+                                             const VT *__restrict__ Bval, int64_t p0, int64_t p1,
+                                             const WalkSmem<VT> &w, F &&f) {
+    const int T = blockDim.x;
+    for (int64_t base = p0; base < p1; base += T) {
+        const int64_t p = base + threadIdx.x;
+        int64_t z = 0, a0 = 0;
+        VT bv = VT(0);
+        if (p < p1) {
+            const int32_t k = Brow[p];
+            a0 = Acp[k];
+            z = Acp[k + 1] - a0;
+            if (VALS) bv = Bval[p];
+        }
+        int64_t total;
+        const int64_t incl = cta_incl_scan_i64(z, w.warp, total);
+        w.excl[threadIdx.x] = incl - z;
+        w.a0[threadIdx.x] = a0;
+        if (VALS) w.bv[threadIdx.x] = bv;
+        __syncthreads();
+        const int nvalid = (int)((p1 - base) < T ? (p1 - base) : T);
+        int lo = 0;
+        for (int64_t q = threadIdx.x; q < total; q += T) {
+            // largest s with excl[s] <= q; owners only move forward as q grows
+            int hi = nvalid - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (w.excl[mid] <= q) lo = mid; else hi = mid - 1;
+            }
+            const int64_t qa = w.a0[lo] + (q - w.excl[lo]);
+            const int32_t row = Arow[qa];
+            VT prod = VT(0);
+            if (VALS) prod = Aval[qa] * w.bv[lo];
+            f(row, prod);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ bitmap ranking
+// Dense flags of the SPA (Algorithm 1's SPA_flags) kept as a bitmap over the
+// m rows, one uint2 per 32 rows: .x the bits, .y the number of set bits in
+// all earlier words.  After cta_bitmap_prefix, the position of row i in the
+// sorted column is rank(i) = .y + popc(.x & lanes below i).
+__device__ __forceinline__ int32_t bitmap_rank(const uint2 *bm, int32_t row) {
+    const uint2 w = bm[row >> 5];
+    return (int32_t)w.y + __popc(w.x & ((1u << (row & 31)) - 1u));
+}
+
+// Exclusive prefix of popcounts over W words into .y; returns the total.
+// Each warp owns a contiguous range of words.  Every thread must call it.
+__device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, int64_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t per = ((W + nw - 1) / nw + 31) & ~int64_t(31);
+    const int64_t w0 = ((int64_t)warp * per < W) ? (int64_t)warp * per : W;
+    const int64_t w1 = (w0 + per < W) ? w0 + per : W;
+    // pass 1: words of this warp
+    int64_t cnt = 0;
+    for (int64_t w = w0 + lane; w < w1; w += 32) cnt += __popc(bm[w].x);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+    if (lane == 0) s_warp[warp] = cnt;
+    __syncthreads();
+    int64_t off = 0, total = 0;
+    for (int i = 0; i < nw; ++i) {
+        const int64_t c = s_warp[i];
+        if (i < warp) off += c;
+        total += c;
+    }
+    // pass 2: running prefix inside the warp's range
+    for (int64_t base = w0; base < w1; base += 32) {
+        const int64_t w = base + lane;
+        const unsigned bits = w < w1 ? bm[w].x : 0u;
+        int c = __popc(bits);
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        if (w < w1) bm[w].y = (unsigned)(off + incl - c);
+        off += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncthreads();
+    return total;
+}
+
+// Visits the set bits of bm[0..W) in ascending row order, calling
+// f(row, rank) with rank = position of the row in the sorted column;
+// consecutive lanes get consecutive ranks, so writes at C[c0 + rank] are
+// coalesced.  With `clear`, the bits are reset on the way (.y is left stale).
+// Every thread must call it; bm[..].y must hold the prefix counts.
+template <typename F>
+__device__ __forceinline__ void cta_bitmap_expand(uint2 *bm, int64_t W, bool clear, F &&f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t nchunks = (W + 31) / 32;
+    for (int64_t c = warp; c < nchunks; c += nw) {
+        const int64_t w = c * 32 + lane;
+        const uint2 v = w < W ? bm[w] : make_uint2(0u, 0u);
+        if (clear && v.x) bm[w].x = 0u;
+        if (__ballot_sync(0xffffffffu, v.x != 0u) == 0u) continue;
+        const int cnt = __popc(v.x);
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const int S = __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = incl - cnt;
+        for (int o0 = 0; o0 < S; o0 += 32) {
+            const int o = o0 + lane;
+            int s = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(0xffffffffu, excl, s + step);
+                if (ex <= o) s += step;
+            }
+            unsigned b = __shfl_sync(0xffffffffu, v.x, s);
+            const int k = o - __shfl_sync(0xffffffffu, excl, s);
+            const unsigned ys = __shfl_sync(0xffffffffu, v.y, s);
+            if (o < S) {
+                for (int i = 0; i < k; ++i) b &= b - 1u;
+                const int bit = __ffs(b) - 1;
+                f((int32_t)((c * 32 + s) * 32 + bit), (int64_t)ys + k);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers
+cudaError_t launch_inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t s);
+int64_t scan_tile_count(int64_t n);
+
+__global__ void k_validate(const int64_t *cp, const int32_t *row, int64_t nrows, int64_t ncols,
+                           int64_t nnz, int which, Ctrl *ctrl);
+__global__ void k_count_bin(const int64_t *Bcp, const int32_t *Brow, const int64_t *Acp, int64_t nB,
+                            int64_t t, int64_t hmax, int64_t *op, int64_t *Ccp, Ctrl *ctrl);
+__global__ void k_bin_scatter(const int64_t *op, int64_t nB, int64_t t, int64_t hmax,
+                              BinOffsets off, int32_t *bin_cols, Ctrl *ctrl);
+
+// Geometry of one phase (symbolic / numeric / backward) of one bin.
+struct Geo {
+    int threads = 0;       // threads per CTA
+    int grid = 0;          // CTAs
+    size_t smem = 0;       // dynamic shared memory
+    int64_t slots = 0;     // table slots per CTA (CTA hash bins, global bin)
+    bool bm_global = false;  // dense flags bitmap in global scratch
+    int64_t cap = 0;       // dense bin: values kept in shared memory up to this nnz
+};
+
+// Everything a bin kernel needs, passed by value.
+struct BinTask {
+    const int32_t *cols;  // this bin's column ids
+    int64_t count;
+    int bin;
+    int shrink;           // table_shrink test knob
+    int64_t m;            // rows of A / C
+    int64_t W;            // bitmap words = ceil(m / 32)
+    const int64_t *op;    // Op_j
+    unsigned char *scratch;  // per-CTA global scratch (base)
+    size_t scratch_stride;   // bytes per CTA
+    Ctrl *ctrl;
+};
+
+struct Operands {
+    const int64_t *Acp; const int32_t *Arow; const void *Aval;
+    const int64_t *Bcp; const int32_t *Brow; const void *Bval;
+};
+
+// symbolic.cu
+cudaError_t launch_symbolic_bin(const BinTask &t, const Operands &o, int64_t *Ccp, const Geo &g,
+                                cudaStream_t s);
+Geo symbolic_geometry(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
+                      int64_t max_op, int shrink, int64_t scratch_ctas);
+// numeric.cu
+cudaError_t launch_numeric_bin(const BinTask &t, const Operands &o, const int64_t *Ccp,
+                               int32_t *Crow, void *Cval, int dtype, const Geo &g, cudaStream_t s);
+Geo numeric_geometry(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
+                     int64_t maxnnz, int dtype, int shrink, int64_t scratch_ctas);
+// backward.cu
+cudaError_t launch_backward_bin(const BinTask &t, const Operands &o, const int64_t *Ccp,
+                                const int32_t *Crow, const void *dC, void *dA, void *dB,
+                                int dtype, const Geo &g, cudaStream_t s);
+Geo backward_geometry(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
+                      int64_t maxnnz, int dtype, int shrink, int64_t scratch_ctas);
+
+// Table slots of the global-memory hash bin for a column with Op_j = op in a
+// matrix with m rows (symbolic: keys only, load <= 1/2).
+__host__ __device__ inline int64_t global_sym_slots(int64_t op, int64_t m) {
+    int64_t need = 2 * (op < m ? op : m);
+    int64_t p = 64;
+    while (p < need) p <<= 1;
+    return p;
+}
+// Table slots for a column with n outputs (numeric / backward, load <= 2/3).
+__host__ __device__ inline int64_t num_slots(int64_t n) {
+    int64_t s = (n * 3 + 1) / 2;
+    s = (s + 31) & ~int64_t(31);
+    return s < 64 ? 64 : s;
+}
+
+}  // namespace spg

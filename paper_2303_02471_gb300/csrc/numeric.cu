@@ -1,0 +1,333 @@
+// Numeric phase: values and ascending rows of every column of C = A x B.
+//
+// Per bin (Section 3.3's H-HASH(t)):
+//   * warp-group hash bins (Op_j <= 256): a group of G lanes per column
+//     accumulates into an open-addressing table (Section 3.2) in shared
+//     memory, compacts it and sorts it with a register bitonic network;
+//   * CTA hash bins (Op_j <= hash_cta_max) and the global hash bin: one CTA
+//     per column, table of ~1.5 nnz(C_j) slots (shared or global memory);
+//     the touched rows are then marked in a bitmap whose prefix counts give
+//     every row its sorted position, and the column is written in row order
+//     with one table lookup per entry;
+//   * dense bin (Op_j >= t): the SPA of Algorithm 1 -- flags as a bitmap, a
+//     first walk sets them, prefix counts turn each row into its position in
+//     the sorted column, and a second walk accumulates every product at that
+//     position (shared memory up to `cap` entries, else in place in C).
+#include "kernels.cuh"
+
+namespace spg {
+
+constexpr int kGroupThreads = 256;
+
+template <typename K>
+static void allow_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename K>
+static int occupancy(K kernel, int threads, size_t smem) {
+    int n = 0;
+    allow_smem(kernel, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) n = 1;
+    return n < 1 ? 1 : n;
+}
+
+// ------------------------------------------------- warp-group hash bins
+template <int G, int R, typename VT>
+__global__ void __launch_bounds__(kGroupThreads) k_num_group(BinTask t, Operands o, const int64_t *Ccp,
+                                                             int32_t *Crow, VT *Cval) {
+    constexpr int H = 2 * G * R;
+    constexpr int NG = kGroupThreads / G;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int grp = threadIdx.x / G;
+    int32_t *keys = reinterpret_cast<int32_t *>(smem) + grp * H;
+    VT *vals = reinterpret_cast<VT *>(smem + (size_t)NG * H * 4) + grp * H;
+    const unsigned mask = group_mask(G);
+    const int gl = threadIdx.x & (G - 1);
+    const int64_t gidx = (int64_t)blockIdx.x * NG + grp;
+    if (gidx >= t.count) return;
+    uint32_t Hj = (uint32_t)H >> t.shrink;
+    if (Hj < 1) Hj = 1;
+    const int32_t j = t.cols[gidx];
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) {
+        keys[i * G + gl] = kEmptyKey;
+        vals[i * G + gl] = VT(0);
+    }
+    __syncwarp(mask);
+    bool ovf = false;
+    group_products<G, true, VT>(mask, o.Acp, o.Arow, static_cast<const VT *>(o.Aval), o.Brow,
+                                static_cast<const VT *>(o.Bval), o.Bcp[j], o.Bcp[j + 1],
+                                [&](int32_t row, VT prod) {
+                                    bool fresh;
+                                    const int32_t slot = hash_insert(keys, Hj, row, fresh);
+                                    if (slot < 0) ovf = true;
+                                    else atomicAdd(&vals[slot], prod);
+                                });
+    __syncwarp(mask);
+    // compact the occupied slots to the front of the table
+    int32_t kk[2 * R];
+    VT vv[2 * R];
+    int pos[2 * R];
+    int n = 0;
+    const unsigned lane_base = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned below = (1u << gl) - 1u;
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) {
+        kk[i] = keys[i * G + gl];
+        vv[i] = vals[i * G + gl];
+        const bool occ = kk[i] != kEmptyKey;
+        unsigned b = __ballot_sync(mask, occ) >> lane_base;
+        if (G < 32) b &= (1u << (G & 31)) - 1u;
+        pos[i] = occ ? n + __popc(b & below) : -1;
+        n += __popc(b);
+    }
+    __syncwarp(mask);
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i)
+        if (pos[i] >= 0 && pos[i] < G * R) {
+            keys[pos[i]] = kk[i];
+            vals[pos[i]] = vv[i];
+        }
+    __syncwarp(mask);
+    int32_t key[R];
+    VT val[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * G + gl;
+        if (e < n) {
+            key[r] = keys[e];
+            val[r] = vals[e];
+        } else {
+            key[r] = 0x7fffffff;
+            val[r] = VT(0);
+        }
+    }
+    group_bitonic_sort<G, R, VT>(mask, key, val);
+    const int64_t c0 = Ccp[j];
+    const int64_t nn = Ccp[j + 1] - c0;
+    if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
+    if (nn != n || n > G * R) {
+        set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * G + gl;
+        if (e < n) {
+            Crow[c0 + e] = key[r];
+            Cval[c0 + e] = val[r];
+        }
+    }
+}
+
+// ------------------------------------------------------- CTA hash bins
+template <typename VT>
+__global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
+                                                  VT *Cval, int64_t cap, int table_global, int bm_global) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t s_col;
+    unsigned char *p = smem;
+    WalkSmem<VT> w = carve_walk<VT>(p);
+    unsigned char *g = t.scratch + (size_t)blockIdx.x * t.scratch_stride;
+    int32_t *keys;
+    VT *vals;
+    unsigned char *&tp = table_global ? g : p;
+    keys = reinterpret_cast<int32_t *>(tp);
+    tp += (size_t)cap * 4;
+    tp = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tp) + 15) & ~uintptr_t(15));
+    vals = reinterpret_cast<VT *>(tp);
+    tp += (size_t)cap * sizeof(VT);
+    tp = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tp) + 15) & ~uintptr_t(15));
+    uint2 *bm = reinterpret_cast<uint2 *>(bm_global ? g : p);
+    for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
+    const VT *Aval = static_cast<const VT *>(o.Aval);
+    const VT *Bval = static_cast<const VT *>(o.Bval);
+    for (;;) {
+        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
+        __syncthreads();
+        const int64_t ci = s_col;
+        if (ci >= t.count) break;
+        const int32_t j = t.cols[ci];
+        const int64_t c0 = Ccp[j];
+        const int64_t nn = Ccp[j + 1] - c0;
+        int64_t want = num_slots(nn);
+        if (want > cap) want = cap;
+        uint32_t H = (uint32_t)(want >> t.shrink);
+        if (H < 1) H = 1;
+        for (uint32_t s = threadIdx.x; s < H; s += blockDim.x) {
+            keys[s] = kEmptyKey;
+            vals[s] = VT(0);
+        }
+        __syncthreads();
+        bool ovf = false;
+        cta_products<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                               [&](int32_t row, VT prod) {
+                                   bool fresh;
+                                   const int32_t slot = hash_insert(keys, H, row, fresh);
+                                   if (slot < 0) ovf = true;
+                                   else atomicAdd(&vals[slot], prod);
+                               });
+        if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
+        for (uint32_t s = threadIdx.x; s < H; s += blockDim.x) {
+            const int32_t key = keys[s];
+            if (key != kEmptyKey) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
+        }
+        __syncthreads();
+        const int64_t total = cta_bitmap_prefix(bm, t.W, w.warp);
+        if (total != nn && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
+        const bool ok = total == nn;
+        cta_bitmap_expand(bm, t.W, true, [&](int32_t row, int64_t rank) {
+            const int32_t slot = hash_find(keys, H, row);
+            if (ok && slot >= 0) {
+                Crow[c0 + rank] = row;
+                Cval[c0 + rank] = vals[slot];
+            }
+        });
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ dense bin
+template <typename VT>
+__global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
+                                                    VT *Cval, int64_t cap, int bm_global) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t s_col;
+    unsigned char *p = smem;
+    WalkSmem<VT> w = carve_walk<VT>(p);
+    uint2 *bm;
+    if (bm_global) {
+        bm = reinterpret_cast<uint2 *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
+    } else {
+        bm = reinterpret_cast<uint2 *>(p);
+        p += (size_t)t.W * 8;
+    }
+    VT *s_acc = reinterpret_cast<VT *>(p);
+    for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
+    const VT *Aval = static_cast<const VT *>(o.Aval);
+    const VT *Bval = static_cast<const VT *>(o.Bval);
+    for (;;) {
+        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
+        __syncthreads();
+        const int64_t ci = s_col;
+        if (ci >= t.count) break;
+        const int32_t j = t.cols[ci];
+        const int64_t c0 = Ccp[j];
+        const int64_t nn = Ccp[j + 1] - c0;
+        // walk 1: SPA flags
+        cta_products<false, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                                [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
+        const int64_t total = cta_bitmap_prefix(bm, t.W, w.warp);
+        const bool ok = total == nn;
+        if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
+        const bool in_smem = nn <= cap;
+        VT *acc = in_smem ? s_acc : Cval + c0;
+        if (ok)
+            for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) acc[i] = VT(0);
+        __syncthreads();
+        // walk 2: accumulate every product at its row's sorted position
+        cta_products<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                               [&](int32_t row, VT prod) {
+                                   const int32_t r = bitmap_rank(bm, row);
+                                   if (ok) atomicAdd(&acc[r], prod);
+                               });
+        cta_bitmap_expand(bm, t.W, true, [&](int32_t row, int64_t rank) {
+            if (ok) {
+                Crow[c0 + rank] = row;
+                if (in_smem) Cval[c0 + rank] = s_acc[rank];
+            }
+        });
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------- launches
+constexpr size_t kBitmapSmemMax = 96 * 1024;
+
+template <typename VT>
+static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
+                              int64_t maxnnz, int shrink, int64_t scratch_ctas) {
+    (void)shrink;
+    Geo g;
+    const int64_t W = ceil_div(m, 32);
+    if (bin >= BIN_WARP0 && bin < BIN_CTA0) {
+        const int b = bin - BIN_WARP0;
+        const int G = warp_bin_G(b), R = warp_bin_R(b);
+        g.threads = kGroupThreads;
+        g.smem = (size_t)(kGroupThreads / G) * 2 * G * R * (4 + sizeof(VT));
+        g.grid = (int)ceil_div(count, kGroupThreads / G);
+        return g;
+    }
+    g.threads = threads;
+    const size_t walk = walk_smem_bytes<VT>(threads) + 16;
+    const size_t bmb = (size_t)W * 8;
+    if (bin >= BIN_CTA0 && bin <= BIN_GLOBAL) {
+        g.slots = num_slots(maxnnz);
+        const size_t tab = ((size_t)g.slots * 4 + 15) / 16 * 16 + ((size_t)g.slots * sizeof(VT) + 15) / 16 * 16;
+        const bool table_global = bin == BIN_GLOBAL || walk + tab > smem_optin;
+        g.bm_global = bmb > kBitmapSmemMax || walk + (table_global ? 0 : tab) + bmb > smem_optin;
+        g.cap = table_global ? 1 : 0;  // reused as "table in global" flag
+        g.smem = walk + (table_global ? 0 : tab) + (g.bm_global ? 0 : bmb);
+        int occ = occupancy(k_num_cta<VT>, threads, g.smem);
+        int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
+        if (table_global || g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);
+        g.grid = (int)std::max<int64_t>(1, grid);
+        return g;
+    }
+    // dense
+    g.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
+    size_t base = walk + (g.bm_global ? 0 : bmb);
+    size_t room = smem_optin > base ? smem_optin - base : 0;
+    int64_t cap = (int64_t)(room / sizeof(VT));
+    if (cap > maxnnz) cap = maxnnz;
+    g.cap = cap;
+    g.smem = base + (size_t)cap * sizeof(VT);
+    int occ = occupancy(k_num_dense<VT>, threads, g.smem);
+    int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
+    if (g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);
+    g.grid = (int)std::max<int64_t>(1, grid);
+    return g;
+}
+
+Geo numeric_geometry(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
+                     int64_t maxnnz, int dtype, int shrink, int64_t scratch_ctas) {
+    return dtype == SPG_F64
+               ? numeric_geometry_t<double>(bin, count, m, threads, sms, smem_optin, maxnnz, shrink, scratch_ctas)
+               : numeric_geometry_t<float>(bin, count, m, threads, sms, smem_optin, maxnnz, shrink, scratch_ctas);
+}
+
+template <typename VT>
+static cudaError_t launch_numeric_t(const BinTask &t, const Operands &o, const int64_t *Ccp, int32_t *Crow,
+                                    VT *Cval, const Geo &g, cudaStream_t s) {
+    if (t.count <= 0) return cudaSuccess;
+    if (t.bin >= BIN_WARP0 && t.bin < BIN_CTA0) {
+        switch (t.bin - BIN_WARP0) {
+#define NUM_CASE(b)                                                                        \
+    case b: {                                                                              \
+        auto k = k_num_group<warp_bin_G(b), warp_bin_R(b), VT>;                            \
+        allow_smem(k, g.smem);                                                             \
+        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval);                        \
+        break;                                                                             \
+    }
+            NUM_CASE(0) NUM_CASE(1) NUM_CASE(2) NUM_CASE(3) NUM_CASE(4) NUM_CASE(5)
+#undef NUM_CASE
+        }
+    } else if (t.bin <= BIN_GLOBAL) {
+        allow_smem(k_num_cta<VT>, g.smem);
+        k_num_cta<VT><<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.slots, g.cap ? 1 : 0,
+                                                        g.bm_global ? 1 : 0);
+    } else {
+        allow_smem(k_num_dense<VT>, g.smem);
+        k_num_dense<VT><<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.cap, g.bm_global ? 1 : 0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_numeric_bin(const BinTask &t, const Operands &o, const int64_t *Ccp, int32_t *Crow,
+                               void *Cval, int dtype, const Geo &g, cudaStream_t s) {
+    return dtype == SPG_F64 ? launch_numeric_t<double>(t, o, Ccp, Crow, static_cast<double *>(Cval), g, s)
+                            : launch_numeric_t<float>(t, o, Ccp, Crow, static_cast<float *>(Cval), g, s);
+}
+
+}  // namespace spg

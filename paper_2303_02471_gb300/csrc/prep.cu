@@ -1,0 +1,182 @@
+// Preprocessing kernels of the column-wise SpGEMM (arXiv 2303.02471):
+// input validation, the operation count Op_j with binning (Section 3.1's
+// "Sorting" pre-pass, done as a bucket pass), per-bin column lists, and the
+// int64 scan that turns per-column counts into C's column pointers.
+#include "kernels.cuh"
+
+namespace spg {
+
+// CSC well-formedness (Section 2.1): colptr[0] = 0, colptr[n] = nnz,
+// colptr non-decreasing, rows in [0, nrows).
+__global__ void k_validate(const int64_t *__restrict__ cp, const int32_t *__restrict__ row,
+                           int64_t nrows, int64_t ncols, int64_t nnz, int which, Ctrl *ctrl) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t j = tid; j <= ncols; j += stride) {
+        int64_t c = cp[j];
+        if ((j == 0 && c != 0) || (j == ncols && c != nnz) || (j < ncols && cp[j + 1] < c) || c < 0)
+            set_error(ctrl, SPG_ERR_INVALID, which * 2 + 0, j);
+    }
+    for (int64_t e = tid; e < nnz; e += stride) {
+        int32_t r = row[e];
+        if (r < 0 || (int64_t)r >= nrows) set_error(ctrl, SPG_ERR_INVALID, which * 2 + 1, e);
+    }
+}
+
+// Op_j = sum over stored B_kj of Z^A_k (Section 3.1), its bin, the bin
+// histogram and the total product count.  Empty columns get nnz 0 here.
+__global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__restrict__ Brow,
+                            const int64_t *__restrict__ Acp, int64_t nB, int64_t t, int64_t hmax,
+                            int64_t *__restrict__ op, int64_t *__restrict__ Ccp, Ctrl *ctrl) {
+    __shared__ unsigned long long s_hist[NBINS];
+    __shared__ unsigned long long s_max[NBINS];
+    __shared__ unsigned long long s_prod;
+    if (threadIdx.x < NBINS) {
+        s_hist[threadIdx.x] = 0;
+        s_max[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) s_prod = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long mine = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nB; j += stride) {
+        const int64_t p0 = Bcp[j], p1 = Bcp[j + 1];
+        int64_t s = 0;
+        for (int64_t p = p0; p < p1; ++p) {
+            const int32_t k = Brow[p];
+            s += Acp[k + 1] - Acp[k];
+        }
+        op[j] = s;
+        mine += (unsigned long long)s;
+        const int b = bin_of(s, t, hmax);
+        atomicAdd(&s_hist[b], 1ULL);
+        atomicMax(&s_max[b], (unsigned long long)s);
+        if (b == BIN_EMPTY) Ccp[j + 1] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) Ccp[0] = 0;
+    for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_prod, mine);
+    __syncthreads();
+    if (threadIdx.x < NBINS && s_hist[threadIdx.x]) {
+        atomicAdd(&ctrl->hist[threadIdx.x], s_hist[threadIdx.x]);
+        atomicMax(&ctrl->maxop[threadIdx.x], s_max[threadIdx.x]);
+    }
+    if (threadIdx.x == 0) atomicAdd(&ctrl->products, s_prod);
+}
+
+// Column ids into per-bin lists at off[bin] (each block reserves its slots
+// with one global atomic per bin, so columns of a bin stay roughly in
+// ascending order within a block's tile).
+__global__ void k_bin_scatter(const int64_t *__restrict__ op, int64_t nB, int64_t t, int64_t hmax,
+                              BinOffsets off, int32_t *__restrict__ bin_cols, Ctrl *ctrl) {
+    __shared__ unsigned int s_cnt[NBINS];
+    __shared__ unsigned long long s_base[NBINS];
+    if (threadIdx.x < NBINS) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int b = -1;
+    unsigned r = 0;
+    if (j < nB) {
+        b = bin_of(op[j], t, hmax);
+        if (b != BIN_EMPTY) r = atomicAdd(&s_cnt[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < NBINS && s_cnt[threadIdx.x])
+        s_base[threadIdx.x] = atomicAdd(&ctrl->fill[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+    __syncthreads();
+    if (b > BIN_EMPTY) bin_cols[off.v[b] + (int64_t)s_base[b] + r] = (int32_t)j;
+}
+
+// ----------------------------------------------------------- int64 scan
+// Inclusive scan of x[0..n) in place, in three passes over tiles of
+// kScanTile elements: tile sums, a scan of the tile sums, the tiles.
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_incl_scan_i64(int64_t v, int64_t *s_warp, int64_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int64_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int64_t o = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += o;
+        }
+        if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[nw - 1];
+    int64_t r = v + (warp > 0 ? s_warp[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tiles(const int64_t *__restrict__ x, int64_t n, int64_t *__restrict__ sums) {
+    __shared__ int64_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t e = base + (int64_t)i * kScanThreads + threadIdx.x;
+        if (e < n) s += x[e];
+    }
+    int64_t total;
+    block_incl_scan_i64(s, s_warp, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_sums(int64_t *sums, int64_t ntiles) {
+    __shared__ int64_t s_warp[32];
+    int64_t carry = 0;
+    for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+        int64_t e = base + threadIdx.x;
+        int64_t v = e < ntiles ? sums[e] : 0;
+        int64_t total;
+        int64_t incl = block_incl_scan_i64(v, s_warp, total);
+        if (e < ntiles) sums[e] = carry + incl - v;  // exclusive
+        carry += total;
+    }
+}
+
+__global__ void k_scan_apply(int64_t *__restrict__ x, int64_t n, const int64_t *__restrict__ sums) {
+    __shared__ int64_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t e = base + i;
+        v[i] = e < n ? x[e] : 0;
+        s += v[i];
+    }
+    int64_t total;
+    int64_t incl = block_incl_scan_i64(s, s_warp, total);
+    int64_t run = sums[blockIdx.x] + incl - s;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t e = base + i;
+        run += v[i];
+        if (e < n) x[e] = run;
+    }
+}
+
+cudaError_t launch_inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t ntiles = ceil_div(n, kScanTile);
+    k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, s>>>(x, n, tile_sums);
+    k_scan_sums<<<1, 1024, 0, s>>>(tile_sums, ntiles);
+    k_scan_apply<<<(unsigned)ntiles, kScanThreads, 0, s>>>(x, n, tile_sums);
+    return cudaGetLastError();
+}
+
+int64_t scan_tile_count(int64_t n) { return n <= 0 ? 1 : ceil_div(n, kScanTile); }
+
+}  // namespace spg

@@ -1,0 +1,243 @@
+"""Torch-facing calls of the GB300 SpGEMM (argument marshalling only).
+
+Torch provides device memory and the current CUDA stream; every step of the
+product runs in the kernels of libspgemm.so behind the C ABI of
+``include/spgemm.h``.  The names follow the ABI: :func:`spgemm_symbolic`,
+:func:`spgemm_numeric`, :func:`spgemm_backward`, plus :func:`spgemm` (both
+phases) and :func:`csc_transpose`.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, replace
+from typing import Optional
+
+import torch
+
+from . import _native as N
+
+
+@dataclass
+class CscMatrix:
+    """A CSC matrix in device memory (Section 2.1 of arXiv 2303.02471)."""
+
+    nrows: int
+    ncols: int
+    colptr: torch.Tensor            # int64 [ncols + 1]
+    rowidx: torch.Tensor            # int32 [nnz]
+    values: Optional[torch.Tensor]  # float64 / float32 [nnz] or None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowidx.shape[0])
+
+    @property
+    def dtype(self):
+        return self.values.dtype if self.values is not None else torch.float64
+
+    @property
+    def device(self):
+        return self.colptr.device
+
+    @staticmethod
+    def from_host(M, device="cuda", dtype=None) -> "CscMatrix":
+        """From any host object with nrows/ncols/colptr/rowidx/values (numpy)."""
+        vals = torch.as_tensor(M.values)
+        if dtype is not None:
+            vals = vals.to(dtype)
+        return CscMatrix(int(M.nrows), int(M.ncols),
+                         torch.as_tensor(M.colptr, dtype=torch.int64).to(device),
+                         torch.as_tensor(M.rowidx, dtype=torch.int32).to(device),
+                         vals.to(device))
+
+    def to_host(self):
+        from types import SimpleNamespace
+        return SimpleNamespace(nrows=self.nrows, ncols=self.ncols,
+                               colptr=self.colptr.cpu().numpy(),
+                               rowidx=self.rowidx.cpu().numpy(),
+                               values=None if self.values is None else self.values.cpu().numpy())
+
+    def with_values(self, values: torch.Tensor) -> "CscMatrix":
+        return replace(self, values=values)
+
+    def to_torch_sparse(self) -> torch.Tensor:
+        return torch.sparse_csc_tensor(self.colptr, self.rowidx.to(torch.int64), self.values,
+                                       size=(self.nrows, self.ncols))
+
+    @staticmethod
+    def from_torch_sparse(T: torch.Tensor) -> "CscMatrix":
+        T = T.to_sparse_csc()
+        return CscMatrix(T.shape[0], T.shape[1], T.ccol_indices().to(torch.int64),
+                         T.row_indices().to(torch.int32), T.values())
+
+
+@dataclass
+class Config:
+    """Mirror of spg_config; None fields keep the library defaults."""
+
+    t: Optional[int] = None            # H-HASH(t) threshold; N.INT64_MAX = infinity
+    hash_cta_max: Optional[int] = None
+    cta_threads: Optional[int] = None
+    validate: Optional[bool] = None
+    table_shrink: Optional[int] = None
+    scratch_cap_bytes: Optional[int] = None
+
+    def native(self) -> N.SpgConfig:
+        c = N.SpgConfig()
+        N.check(N.lib().spg_config_default(ctypes.byref(c)), "spg_config_default")
+        for f in ("t", "hash_cta_max", "cta_threads", "table_shrink", "scratch_cap_bytes"):
+            v = getattr(self, f)
+            if v is not None:
+                setattr(c, f, int(v))
+        if self.validate is not None:
+            c.validate = int(bool(self.validate))
+        return c
+
+
+_DT = {torch.float64: N.SPG_F64, torch.float32: N.SPG_F32}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else None
+
+
+def _csc(M: CscMatrix, dtype=None) -> N.SpgCsc:
+    dt = dtype if dtype is not None else M.dtype
+    if dt not in _DT:
+        raise TypeError(f"unsupported dtype {dt}")
+    for t, want in ((M.colptr, torch.int64), (M.rowidx, torch.int32)):
+        if t.dtype != want or not t.is_contiguous() or not t.is_cuda:
+            raise TypeError("CSC index arrays must be contiguous CUDA int64 colptr / int32 rowidx")
+    if M.values is not None and (not M.values.is_contiguous() or not M.values.is_cuda):
+        raise TypeError("CSC values must be a contiguous CUDA tensor")
+    return N.SpgCsc(M.nrows, M.ncols, M.nnz, M.colptr.data_ptr(), _ptr(M.rowidx),
+                    _ptr(M.values), _DT[dt])
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Host plan of one product plus the device workspace that holds its state."""
+
+    def __init__(self, handle: ctypes.c_void_p, workspace: torch.Tensor, A: CscMatrix,
+                 B: CscMatrix, colptr: torch.Tensor, nnz: int, config: Config):
+        self._h = handle
+        self.workspace = workspace
+        self.shape = (A.nrows, B.ncols)
+        self.dtype = A.dtype
+        self.colptr = colptr
+        self.nnz = nnz
+        self.config = config
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan destroyed")
+        return self._h
+
+    def info(self):
+        nb = ctypes.c_int32()
+        counts = (ctypes.c_int64 * 64)()
+        prod = ctypes.c_int64()
+        t = ctypes.c_int64()
+        N.check(N.lib().spg_plan_info(self.handle, ctypes.byref(nb), counts, ctypes.byref(prod),
+                                      ctypes.byref(t)), "spg_plan_info")
+        return {"bins": list(counts[:nb.value]), "products": prod.value, "t": t.value}
+
+    def op_counts(self) -> torch.Tensor:
+        out = torch.empty(self.shape[1], dtype=torch.int64, device=self.workspace.device)
+        N.check(N.lib().spg_plan_op_counts(self.handle, _ptr(out), _stream()), "spg_plan_op_counts")
+        return out
+
+    def check(self) -> None:
+        N.check(N.lib().spg_plan_check(self.handle, _stream()), "spg_plan_check")
+
+    def destroy(self) -> None:
+        if self._h is not None:
+            N.lib().spg_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def workspace_size(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None) -> int:
+    cfg = (config or Config()).native()
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().spgemm_workspace_size(ctypes.byref(_csc(A)), ctypes.byref(_csc(B, A.dtype)),
+                                          ctypes.byref(cfg), ctypes.byref(nbytes)),
+            "spgemm_workspace_size")
+    return nbytes.value
+
+
+def spgemm_symbolic(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None,
+                    workspace: Optional[torch.Tensor] = None):
+    """Column pointers of C = A B, nnz(C) and the plan (synchronises)."""
+    config = config or Config()
+    cfg = config.native()
+    cA, cB = _csc(A), _csc(B, A.dtype)
+    need = workspace_size(A, B, config)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
+    colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=A.device)
+    nnz = ctypes.c_int64()
+    h = ctypes.c_void_p()
+    N.check(N.lib().spgemm_symbolic(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(cfg),
+                                    _ptr(workspace), workspace.numel(), _ptr(colptr),
+                                    ctypes.byref(nnz), ctypes.byref(h), _stream()),
+            "spgemm_symbolic")
+    return colptr, nnz.value, Plan(h, workspace, A, B, colptr, nnz.value, config)
+
+
+def spgemm_numeric(plan: Plan, A: CscMatrix, B: CscMatrix, rowidx: Optional[torch.Tensor] = None,
+                   values: Optional[torch.Tensor] = None) -> CscMatrix:
+    """Rows (ascending) and values of C = A B into new or given buffers."""
+    if rowidx is None:
+        rowidx = torch.empty(plan.nnz, dtype=torch.int32, device=A.device)
+    if values is None:
+        values = torch.empty(plan.nnz, dtype=A.dtype, device=A.device)
+    N.check(N.lib().spgemm_numeric(plan.handle, ctypes.byref(_csc(A)), ctypes.byref(_csc(B)),
+                                   _ptr(plan.colptr), _ptr(rowidx), _ptr(values), _stream()),
+            "spgemm_numeric")
+    return CscMatrix(A.nrows, B.ncols, plan.colptr, rowidx, values)
+
+
+def spgemm(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None):
+    """C = A B (both phases).  Returns (C, plan)."""
+    _, _, plan = spgemm_symbolic(A, B, config)
+    C = spgemm_numeric(plan, A, B)
+    return C, plan
+
+
+def spgemm_backward(plan: Plan, A: CscMatrix, B: CscMatrix, C: CscMatrix, dC: torch.Tensor,
+                    need_dA: bool = True, need_dB: bool = True):
+    """(dA, dB) on the stored entries of A and B for dC on pattern(C)."""
+    dA = torch.empty(A.nnz, dtype=A.dtype, device=A.device) if need_dA else None
+    dB = torch.empty(B.nnz, dtype=A.dtype, device=A.device) if need_dB else None
+    dC = dC.contiguous()
+    N.check(N.lib().spgemm_backward(plan.handle, ctypes.byref(_csc(A)), ctypes.byref(_csc(B)),
+                                    _ptr(C.colptr), _ptr(C.rowidx), _ptr(dC), _ptr(dA), _ptr(dB),
+                                    _stream()), "spgemm_backward")
+    return dA, dB
+
+
+def csc_transpose(M: CscMatrix, with_perm: bool = True):
+    """(M^T as CscMatrix, perm) with T.values = M.values[perm]."""
+    cM = _csc(M)
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().spg_transpose_workspace_size(ctypes.byref(cM), ctypes.byref(nbytes)),
+            "spg_transpose_workspace_size")
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=M.device)
+    cp = torch.empty(M.nrows + 1, dtype=torch.int64, device=M.device)
+    row = torch.empty(M.nnz, dtype=torch.int32, device=M.device)
+    vals = torch.empty(M.nnz, dtype=M.dtype, device=M.device) if M.values is not None else None
+    perm = torch.empty(M.nnz, dtype=torch.int64, device=M.device) if with_perm else None
+    N.check(N.lib().spg_csc_transpose(ctypes.byref(cM), _ptr(cp), _ptr(row), _ptr(vals), _ptr(perm),
+                                      _ptr(ws), ws.numel(), _stream()), "spg_csc_transpose")
+    return CscMatrix(M.ncols, M.nrows, cp, row, vals), perm

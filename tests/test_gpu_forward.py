@@ -1,0 +1,211 @@
+"""Parity of the CUDA forward path (through the C ABI) with the CPU oracle."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_02471_gb300 import synth
+
+from gpu_helpers import assert_matches_oracle, upload
+
+pytestmark = pytest.mark.gpu
+
+INF = (1 << 63) - 1
+NCPU = len(os.sched_getaffinity(0))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _run(A, B, dtype=None, **cfg):
+    from paper_2303_02471_gb300 import ops
+    dA, dB = upload(A, dtype), upload(B, dtype)
+    C, plan = ops.spgemm(dA, dB, ops.Config(**cfg) if cfg else None)
+    plan.check()
+    return C, plan
+
+
+def test_fig1_example():
+    from helpers import from_dense, read_golden
+    g = read_golden("fig1.txt")
+    A, B = from_dense(g["A"]), from_dense(g["B"])
+    C, plan = _run(A, B)
+    assert np.array_equal(plan.op_counts().cpu().numpy(), g["OP"][0].astype(np.int64))
+    assert_matches_oracle(C, A, B, tau=0.0)
+
+
+@pytest.mark.parametrize("t", [0, 40, None, INF])
+def test_workload1_lap2d(t):
+    A, B = synth.workload(1)
+    C, plan = _run(A, B, t=t)
+    assert_matches_oracle(C, A, B)
+    assert C.nnz == 12676
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("seed", range(60))
+def test_fuzz(seed, dtype):
+    A, B = synth.fuzz_pair(seed, dtype=dtype)
+    C, _ = _run(A, B)
+    assert_matches_oracle(C, A, B)
+
+
+@pytest.mark.parametrize("t", [0, 3, 20, INF])
+@pytest.mark.parametrize("seed", [5, 11, 23, 42, 77])
+def test_fuzz_threshold_invariance(seed, t):
+    A, B = synth.fuzz_pair(seed)
+    C, _ = _run(A, B, t=t)
+    assert_matches_oracle(C, A, B)
+
+
+@pytest.mark.parametrize("hmax", [256, 1024, 8192])
+@pytest.mark.parametrize("t", [0, 40, None, INF])
+def test_rmat_every_bin(t, hmax):
+    """A power-law pattern with Op_j from 1 to ~10^5 crosses every bin."""
+    A = synth.rmat(13, seed=2, col_cap=600)
+    C, plan = _run(A, A, t=t, hash_cta_max=hmax)
+    assert_matches_oracle(C, A, A, nthreads=NCPU)
+    info = plan.info()
+    assert info["products"] == int(oracle.op_counts(A, A).sum())
+
+
+def test_op_counts_and_bins():
+    A = synth.rmat(12, seed=5, col_cap=300)
+    B = synth.random_z(A.ncols, 0, 12, seed=6)
+    C, plan = _run(A, B, t=40)
+    op = plan.op_counts().cpu().numpy()
+    assert np.array_equal(op, oracle.op_counts(A, B))
+    bins = plan.info()["bins"]
+    assert bins[0] == int((op == 0).sum())
+    assert bins[13] == int((op >= 40).sum())
+    assert sum(bins) == A.ncols
+
+
+def test_workload2_random_full():
+    A, B = synth.workload(2)
+    C, plan = _run(A, B)
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_workload2_random_reduced(dtype):
+    A = synth.random_z(1 << 16, 1, 8, seed=0, dtype=dtype)
+    B = synth.random_z(1 << 16, 1, 8, seed=1, dtype=dtype)
+    C, _ = _run(A, B)
+    assert_matches_oracle(C, A, B)
+
+
+def test_workload3_rmat_full():
+    """Full-size R-MAT product (2^18, ~672M products) against the oracle."""
+    A, B = synth.workload(3)
+    C, plan = _run(A, B)
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
+@pytest.mark.parametrize("t", [0, INF])
+def test_workload3_threshold_extremes_pattern(t):
+    """H-HASH(0) is all-SPA and H-HASH(inf) all-hash (Section 3.3); both give
+    the same structure as the default split on a reduced R-MAT."""
+    A = synth.rmat(15, seed=0, col_cap=2000)
+    C, _ = _run(A, A, t=t)
+    assert_matches_oracle(C, A, A, nthreads=NCPU)
+
+
+def test_identity_is_bit_exact():
+    from helpers import identity
+    A = synth.random_z(5000, 1, 9, seed=5)
+    I = identity(5000)
+    for L, R in ((A, I), (I, A)):
+        C, _ = _run(L, R)
+        G = C.to_host()
+        assert np.array_equal(G.colptr, A.colptr)
+        assert np.array_equal(G.rowidx, A.rowidx)
+        assert np.array_equal(G.values, A.values)
+
+
+def test_unsorted_input_columns():
+    rng = np.random.default_rng(3)
+    A = synth.random_pattern(rng, 3000, 2000, 0.01, shuffle=True)
+    B = synth.random_pattern(rng, 2000, 1500, 0.01, shuffle=True)
+    C, _ = _run(A, B, t=40)
+    assert_matches_oracle(C, A, B)
+
+
+def test_repeat_numeric_is_stable():
+    from paper_2303_02471_gb300 import ops
+    A = synth.rmat(12, seed=9, col_cap=400)
+    dA = upload(A)
+    _, _, plan = ops.spgemm_symbolic(dA, dA)
+    C1 = ops.spgemm_numeric(plan, dA, dA)
+    C2 = ops.spgemm_numeric(plan, dA, dA)
+    plan.check()
+    assert (C1.rowidx == C2.rowidx).all()
+    ref = oracle.spgemm(A, A)
+    assert_matches_oracle(C1, A, A, ref=ref)
+    assert_matches_oracle(C2, A, A, ref=ref)
+
+
+# ----------------------------------------------------------- errors
+def _status(fn):
+    from paper_2303_02471_gb300._native import SpgError
+    with pytest.raises(SpgError) as e:
+        fn()
+    return e.value.name
+
+
+def test_invalid_inputs_are_rejected():
+    import torch
+    from paper_2303_02471_gb300 import ops
+    A = synth.random_z(100, 1, 5, seed=1)
+    dA = upload(A)
+    bad = dA.with_values(dA.values)
+    bad_cp = dA.colptr.clone()
+    bad_cp[10] = bad_cp[11] + 3  # not monotone
+    assert _status(lambda: ops.spgemm(ops.CscMatrix(100, 100, bad_cp, dA.rowidx, dA.values), dA)) == "SPG_ERR_INVALID"
+    bad_row = dA.rowidx.clone()
+    bad_row[7] = 100  # out of range
+    assert _status(lambda: ops.spgemm(dA, ops.CscMatrix(100, 100, dA.colptr, bad_row, dA.values))) == "SPG_ERR_INVALID"
+    last = dA.colptr.clone()
+    last[-1] -= 1  # colptr[n] != nnz
+    assert _status(lambda: ops.spgemm(ops.CscMatrix(100, 100, last, dA.rowidx, dA.values), dA)) == "SPG_ERR_INVALID"
+    # shape mismatch and dtype mismatch
+    B = upload(synth.random_z(99, 1, 5, seed=2))
+    assert _status(lambda: ops.spgemm(dA, B)) == "SPG_ERR_INVALID"
+    assert _status(lambda: ops.spgemm(dA, dA.with_values(dA.values.float()))) == "SPG_ERR_INVALID"
+    del bad, torch
+
+
+def test_workspace_too_small():
+    import torch
+    from paper_2303_02471_gb300 import _native as N
+    from paper_2303_02471_gb300 import ops
+    import ctypes
+    A = upload(synth.random_z(500, 1, 5, seed=1))
+    need = ops.workspace_size(A, A)
+    ws = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    cp = torch.empty(A.ncols + 1, dtype=torch.int64, device="cuda")
+    nnz, h = ctypes.c_int64(), ctypes.c_void_p()
+    cA = ops._csc(A)
+    rc = N.lib().spgemm_symbolic(ctypes.byref(cA), ctypes.byref(cA), None, ctypes.c_void_p(ws.data_ptr()),
+                                 ws.numel(), ctypes.c_void_p(cp.data_ptr()), ctypes.byref(nnz),
+                                 ctypes.byref(h), ops._stream())
+    assert N.STATUS[rc] == "SPG_ERR_WORKSPACE"
+    assert h.value is None
+
+
+@pytest.mark.parametrize("t", [None, INF])
+def test_table_overflow_is_reported_not_hung(t):
+    A = synth.rmat(11, seed=3, col_cap=300)
+    assert _status(lambda: _run(A, A, t=t, table_shrink=4)) == "SPG_ERR_TABLE_OVERFLOW"
+
+
+def test_empty_shapes():
+    for seed in range(6):
+        A, B = synth.fuzz_pair(seed)
+        C, _ = _run(A, B)
+        assert_matches_oracle(C, A, B)
