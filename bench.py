@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU seconds of the oracle sample")
+    p.add_argument("--rmat-scale", type=int, default=18,
+                   help="log2 size of the R-MAT workload (smaller for profiler captures)")
     return p.parse_args()
 
 
@@ -122,10 +124,29 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- workloads
-def make_workload(k):
+def workload_name(args):
+    if args.workload == 3 and args.rmat_scale != 18:
+        return WORKLOADS[3].replace("2^18", f"2^{args.rmat_scale}")
+    return WORKLOADS[args.workload]
+
+
+def make_workload(k, rmat_scale=18):
     from paper_2303_02471_gb300 import synth
+    if k == 3 and rmat_scale != 18:
+        A = synth.rmat(rmat_scale, seed=0)
+        return A, A
     A, B = synth.workload(k)
     return A, B
+
+
+def bin_bytes(st, b, w):
+    """Algorithmic bytes of one bin kernel of the numeric pass: its B columns
+    (colptr pair, rows, values), the gathered A column pointers (16 B per B
+    entry), the gathered A entries (one per product), the C column pointers
+    and the C entries written once."""
+    cols = st["count"][b]
+    return (16 * cols + st["nnz_b"][b] * (4 + w + 16) + st["products"][b] * (4 + w)
+            + 16 * cols + st["nnz"][b] * (4 + w))
 
 
 def column_sample(B, frac, seed=0):
@@ -169,13 +190,13 @@ def run_reference(args, rank, world):
     unit = "GFLOP/s"
     if rank != 0:
         return None
-    A, B = make_workload(args.workload)
+    A, B = make_workload(args.workload, args.rmat_scale)
     base = cpu_baseline(A, B, min(args.cpu_seconds, 20.0), unit)
     line = {"impl": "reference", "metric": "SpGEMM GFLOP/s (2 x intermediate products / s)",
             "value": base["value"], "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]},
+            "config": {"workload": workload_name(args)},
             "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -189,7 +210,7 @@ def run_ours(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    A_h, B_h = make_workload(args.workload)
+    A_h, B_h = make_workload(args.workload, args.rmat_scale)
     w = 8
     A = ops.CscMatrix.from_host(A_h, device=dev)
     B = A if B_h is A_h else ops.CscMatrix.from_host(B_h, device=dev)
@@ -212,28 +233,36 @@ def run_ours(args, rank, world):
         return h, nnz.value
 
     h, nnz = symbolic()
-    info = ops.Plan(h, ws, A, B, colptr, nnz, cfg).info()
+    first = ops.Plan(h, ws, A, B, colptr, nnz, cfg)
+    info = first.info()
+    st = first.bin_stats()
+    st["count"] = info["bins"]
     products = info["products"]
+    lc = first.launch_count()
+    launches_per_step = lc["symbolic"] + lc["numeric"]
+    first.destroy()
     rowidx = torch.empty(nnz, dtype=torch.int32, device=dev)
     values = torch.empty(nnz, dtype=torch.float64, device=dev)
-    nonempty = sum(1 for b in info["bins"][1:] if b)
-    launches_per_step = 2 + 1 + 1 + nonempty + 3 + nonempty
 
-    def numeric(hh):
-        N.check(lib.spgemm_numeric(hh, ctypes.byref(cA), ctypes.byref(cB),
+    def numeric(plan):
+        N.check(lib.spgemm_numeric(plan.handle, ctypes.byref(cA), ctypes.byref(cB),
                                    ctypes.c_void_p(colptr.data_ptr()),
                                    ctypes.c_void_p(rowidx.data_ptr()),
                                    ctypes.c_void_p(values.data_ptr()), sp), "spgemm_numeric")
 
-    lib.spg_plan_destroy(h)
+    def plan_of(hh, n):
+        return ops.Plan(hh, ws, A, B, colptr, n, cfg)
+
     for _ in range(args.warmup):
-        hh, _ = symbolic()
-        numeric(hh)
-        lib.spg_plan_destroy(hh)
+        plan = plan_of(*symbolic())
+        numeric(plan)
+        plan.check()
+        plan.destroy()
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bin_ms = []
     clocks = ClockSampler()
     if world > 1:
         torch.distributed.barrier()
@@ -242,14 +271,14 @@ def run_ours(args, rank, world):
     for i in range(args.steps):
         flush.fill_(i & 0xff)  # evict A and B from L2 between steps
         ev[i][0].record(stream)
-        hh, _ = symbolic()
+        plan = plan_of(*symbolic())
+        plan.set_timing(True)
         ev[i][1].record(stream)
-        numeric(hh)
+        numeric(plan)
         ev[i][2].record(stream)
-        stream.synchronize()
-        st = lib.spg_plan_check(hh, sp)
-        lib.spg_plan_destroy(hh)
-        N.check(st, "spg_plan_check")
+        plan.check()
+        bin_ms.append(plan.bin_times())
+        plan.destroy()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -263,15 +292,28 @@ def run_ours(args, rank, world):
         ms = float(t.item())
     value = world * 2.0 * products / (ms * 1e-3) / 1e9
 
-    # roofline of the binned numeric pass
+    # roofline: the dominant kernel (the bin kernel with the largest time) and
+    # the whole binned numeric pass
     peak, peak_kind = peaks()
+    bms = np.mean(np.array(bin_ms), axis=0)
+    top = int(np.argmax(bms))
+    top_bytes = bin_bytes(st, top, w)
+    top_ach = top_bytes / (bms[top] * 1e-3) / 1e9
     alg = algorithmic_bytes(A_h, B_h, products, nnz, w)
     num_avg = float(np.mean(num_ms))
     achieved = alg / (num_avg * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
-            "kernel": "numeric pass (all bin kernels of spgemm_numeric)",
-            "algorithmic_bytes": int(alg), "ms": round(num_avg, 4), "peak_kind": peak_kind}
+    names = ["empty"] + [f"hash_group_op<={o}" for o in (8, 16, 32, 64, 128, 256)] + \
+        [f"hash_cta_op<={o}" for o in (512, 1024, 2048, 4096, 8192)] + ["hash_global", "dense_spa"]
+    roof = {"bound": "hbm", "achieved": round(top_ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(top_ach / peak, 4), "traffic": None,
+            "kernel": f"numeric bin {top} ({names[top]})", "ms": round(float(bms[top]), 4),
+            "algorithmic_bytes": int(top_bytes), "peak_kind": peak_kind,
+            "numeric_pass": {"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
+                             "ms": round(num_avg, 4), "algorithmic_bytes": int(alg)}}
+    per_bin = {names[b]: {"ms": round(float(bms[b]), 4), "cols": st["count"][b],
+                          "products": st["products"][b], "nnz": st["nnz"][b],
+                          "GBps": round(bin_bytes(st, b, w) / (bms[b] * 1e-3) / 1e9, 1)}
+               for b in range(1, len(bms)) if st["count"][b]}
 
     # end to end through host buffers
     e2e = None
@@ -287,12 +329,12 @@ def run_ours(args, rank, world):
                 "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOADS[args.workload], "products": int(products),
+                "config": {"workload": workload_name(args), "products": int(products),
                            "nnz_C": int(nnz), "l2": "512 MiB buffer written between timed steps",
                            "parallelism": f"replicas x{world}"},
                 "phases_ms": {"symbolic": round(float(np.mean([a.elapsed_time(b) for a, b, c in ev])), 4),
                               "numeric": round(num_avg, 4)},
-                "roofline": roof, "cpu_baseline": base, "e2e": e2e,
+                "roofline": roof, "numeric_bins": per_bin, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk}
     return line

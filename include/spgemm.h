@@ -208,6 +208,27 @@ spg_status spg_plan_info(const spg_plan *plan, int32_t *nbins,
                          int64_t *bin_counts, int64_t *products,
                          int64_t *t_effective);
 
+/* Per-bin statistics of the plan, host arrays of spg_plan_info's nbins
+ * entries (any may be NULL): sum of Op_j, sum of nnz(C_j), largest Op_j,
+ * largest nnz(C_j) and sum of nnz(B_j) over the bin's columns.  No device
+ * work. */
+spg_status spg_plan_bin_stats(const spg_plan *plan, int64_t *bin_products,
+                              int64_t *bin_nnz, int64_t *bin_max_op,
+                              int64_t *bin_max_nnz, int64_t *bin_nnz_b);
+
+/* Kernels one spgemm_symbolic call launched for this plan, and the kernels
+ * one spgemm_numeric / spgemm_backward call launches (host, no device work). */
+spg_status spg_plan_launch_count(const spg_plan *plan, int64_t *symbolic,
+                                 int64_t *numeric, int64_t *backward);
+
+/* Enable (nonzero) or disable event timing of every bin kernel in later
+ * spgemm_numeric calls of this plan (CUDA events, no device memory). */
+spg_status spg_plan_set_timing(spg_plan *plan, int32_t enable);
+
+/* Milliseconds each bin kernel of the last timed spgemm_numeric call took
+ * (host float[nbins]; 0 for bins without columns).  Waits for those events. */
+spg_status spg_plan_bin_times(spg_plan *plan, float *ms);
+
 /* Copy Op_j (int64[B->ncols], Section 3.1) from the plan's workspace into
  * the device buffer `op_out` on `stream` (asynchronous). */
 spg_status spg_plan_op_counts(const spg_plan *plan, int64_t *op_out,

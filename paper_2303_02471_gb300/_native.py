@@ -52,6 +52,10 @@ SIGNATURES = {
     "spg_plan_destroy": (i32, [vp]),
     "spg_plan_info": (i32, [vp, ctypes.POINTER(i32), vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
     "spg_plan_op_counts": (i32, [vp, vp, vp]),
+    "spg_plan_bin_stats": (i32, [vp, vp, vp, vp, vp, vp]),
+    "spg_plan_launch_count": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+    "spg_plan_set_timing": (i32, [vp, i32]),
+    "spg_plan_bin_times": (i32, [vp, vp]),
     "spg_transpose_workspace_size": (i32, [vp, ctypes.POINTER(ctypes.c_size_t)]),
     "spg_csc_transpose": (i32, [vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
 }

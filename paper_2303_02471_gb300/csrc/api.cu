@@ -117,6 +117,22 @@ struct spg_plan {
     int64_t nnzC = 0;
     Geo num_geo[NBINS];
     bool num_geo_ready = false;
+    bool timing = false;
+    bool timed = false;
+    cudaEvent_t ev0[NBINS] = {}, ev1[NBINS] = {};
+    int64_t sym_launches = 0;
+
+    ~spg_plan() {
+        for (int b = 0; b < NBINS; ++b) {
+            if (ev0[b]) cudaEventDestroy(ev0[b]);
+            if (ev1[b]) cudaEventDestroy(ev1[b]);
+        }
+    }
+    int64_t nonempty_bins() const {
+        int64_t n = 0;
+        for (int b = 1; b < NBINS; ++b) n += host.hist[b] ? 1 : 0;
+        return n;
+    }
 
     Ctrl *ctrl() const { return reinterpret_cast<Ctrl *>(ws + L.ctrl); }
     int64_t *op() const { return reinterpret_cast<int64_t *>(ws + L.op); }
@@ -286,6 +302,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
                                          P->L.scratch_ctas);
     }
     P->num_geo_ready = true;
+    P->sym_launches = (c.validate ? 2 : 0) + (P->nB > 0 ? 5 : 0) + P->nonempty_bins();
     *nnzC = P->nnzC;
     *plan_out = P;
     return SPG_OK;
@@ -312,9 +329,12 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
     Operands o{A->colptr, A->rowidx, A->values, B->colptr, B->rowidx, B->values};
     for (int b = 1; b < NBINS; ++b) {
         if (!P->host.hist[b]) continue;
+        if (P->timing && cudaEventRecord(P->ev0[b], s) != cudaSuccess) return SPG_ERR_CUDA;
         cudaError_t e = launch_numeric_bin(P->task(b), o, C_colptr, C_rowidx, C_values, P->dtype, P->num_geo[b], s);
         if (e != cudaSuccess) return SPG_ERR_CUDA;
+        if (P->timing && cudaEventRecord(P->ev1[b], s) != cudaSuccess) return SPG_ERR_CUDA;
     }
+    P->timed = P->timing;
     return SPG_OK;
 }
 
@@ -350,6 +370,50 @@ spg_status spg_plan_info(const spg_plan *P, int32_t *nbins, int64_t *bin_counts,
         for (int b = 0; b < NBINS; ++b) bin_counts[b] = (int64_t)P->host.hist[b];
     if (products) *products = (int64_t)P->host.products;
     if (t_effective) *t_effective = P->t_eff;
+    return SPG_OK;
+}
+
+spg_status spg_plan_bin_stats(const spg_plan *P, int64_t *bin_products, int64_t *bin_nnz, int64_t *bin_max_op,
+                              int64_t *bin_max_nnz, int64_t *bin_nnz_b) {
+    if (!P) return SPG_ERR_INVALID;
+    for (int b = 0; b < NBINS; ++b) {
+        if (bin_products) bin_products[b] = (int64_t)P->host.binprod[b];
+        if (bin_nnz) bin_nnz[b] = (int64_t)P->host.binnnz[b];
+        if (bin_max_op) bin_max_op[b] = (int64_t)P->host.maxop[b];
+        if (bin_max_nnz) bin_max_nnz[b] = (int64_t)P->host.maxnnz[b];
+        if (bin_nnz_b) bin_nnz_b[b] = (int64_t)P->host.binnnzb[b];
+    }
+    return SPG_OK;
+}
+
+spg_status spg_plan_launch_count(const spg_plan *P, int64_t *symbolic, int64_t *numeric, int64_t *backward) {
+    if (!P) return SPG_ERR_INVALID;
+    if (symbolic) *symbolic = P->sym_launches;
+    if (numeric) *numeric = P->nonempty_bins();
+    if (backward) *backward = P->nonempty_bins();
+    return SPG_OK;
+}
+
+spg_status spg_plan_set_timing(spg_plan *P, int32_t enable) {
+    if (!P) return SPG_ERR_INVALID;
+    if (enable) {
+        for (int b = 0; b < NBINS; ++b) {
+            if (!P->ev0[b] && cudaEventCreate(&P->ev0[b]) != cudaSuccess) return SPG_ERR_CUDA;
+            if (!P->ev1[b] && cudaEventCreate(&P->ev1[b]) != cudaSuccess) return SPG_ERR_CUDA;
+        }
+    }
+    P->timing = enable != 0;
+    return SPG_OK;
+}
+
+spg_status spg_plan_bin_times(spg_plan *P, float *ms) {
+    if (!P || !ms) return SPG_ERR_INVALID;
+    for (int b = 0; b < NBINS; ++b) {
+        ms[b] = 0.f;
+        if (!P->timed || b == 0 || !P->host.hist[b]) continue;
+        if (cudaEventSynchronize(P->ev1[b]) != cudaSuccess) return SPG_ERR_CUDA;
+        if (cudaEventElapsedTime(&ms[b], P->ev0[b], P->ev1[b]) != cudaSuccess) return SPG_ERR_CUDA;
+    }
     return SPG_OK;
 }
 

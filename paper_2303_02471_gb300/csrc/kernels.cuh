@@ -16,6 +16,9 @@ namespace spg {
 
 struct BinOffsets { int64_t v[NBINS + 1]; };
 
+// Products a lane of a group walk gathers before it consumes them.
+constexpr int kGroupBatch = 2;
+
 // ------------------------------------------------------------ group walk
 // A group of G lanes (G divides 32) walks the products of B entries
 // [p0, p1) in chunks of G entries.  f(row, product) runs once per product
@@ -43,24 +46,37 @@ __device__ __forceinline__ void group_products(unsigned mask, const int64_t *__r
         const int incl = group_incl_scan<G>(mask, z);
         const int total = __shfl_sync(mask, incl, G - 1, G);
         const int excl = incl - z;
-        for (int q0 = 0; q0 < total; q0 += G) {
-            const int q = q0 + gl;
-            int s = 0;
+        for (int q0 = 0; q0 < total; q0 += G * kGroupBatch) {
+            int32_t rows[kGroupBatch];
+            VT av[kGroupBatch], bvs[kGroupBatch];
 #pragma unroll
-            for (int step = G / 2; step > 0; step >>= 1) {
-                const int ex = __shfl_sync(mask, excl, s + step, G);
-                if (ex <= q) s += step;
+            for (int u = 0; u < kGroupBatch; ++u) {
+                const int q = q0 + u * G + gl;
+                rows[u] = -1;
+                if (q0 + u * G < total) {  // uniform over the group
+                    int s = 0;
+#pragma unroll
+                    for (int step = G / 2; step > 0; step >>= 1) {
+                        const int ex = __shfl_sync(mask, excl, s + step, G);
+                        if (ex <= q) s += step;
+                    }
+                    const int64_t a0s = __shfl_sync(mask, a0, s, G);
+                    const int exs = __shfl_sync(mask, excl, s, G);
+                    if (VALS) bvs[u] = __shfl_sync(mask, bv, s, G);
+                    if (q < total) {
+                        const int64_t qa = a0s + (q - exs);
+                        rows[u] = Arow[qa];
+                        if (VALS) av[u] = Aval[qa];
+                    }
+                }
             }
-            const int64_t a0s = __shfl_sync(mask, a0, s, G);
-            const int exs = __shfl_sync(mask, excl, s, G);
-            VT bvs = VT(0);
-            if (VALS) bvs = __shfl_sync(mask, bv, s, G);
-            if (q < total) {
-                const int64_t qa = a0s + (q - exs);
-                const int32_t row = Arow[qa];
-                VT prod = VT(0);
-                if (VALS) prod = Aval[qa] * bvs;
-                f(row, prod);
+#pragma unroll
+            for (int u = 0; u < kGroupBatch; ++u) {
+                if (rows[u] >= 0) {
+                    VT prod = VT(0);
+                    if (VALS) prod = av[u] * bvs[u];
+                    f(rows[u], prod);
+                }
             }
         }
     }
@@ -91,6 +107,9 @@ __device__ __forceinline__ int64_t cta_incl_scan_i64(int64_t v, int64_t *s_warp,
     __syncthreads();
     return r;
 }
+
+// Products a thread of the CTA walk gathers before it consumes them.
+constexpr int kWalkBatch = 4;
 
 // Shared scratch of the CTA walk: one B entry per thread of the chunk.
 template <typename VT>
@@ -145,18 +164,38 @@ __device__ __forceinline__ void cta_products(const int64_t *__restrict__ Acp,
         __syncthreads();
         const int nvalid = (int)((p1 - base) < T ? (p1 - base) : T);
         int lo = 0;
-        for (int64_t q = threadIdx.x; q < total; q += T) {
-            // largest s with excl[s] <= q; owners only move forward as q grows
-            int hi = nvalid - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (w.excl[mid] <= q) lo = mid; else hi = mid - 1;
+        // kWalkBatch products per thread are gathered before any is used, so
+        // their L2/HBM latencies overlap.
+        for (int64_t qb = threadIdx.x; qb < total; qb += (int64_t)T * kWalkBatch) {
+            int32_t rows[kWalkBatch];
+            VT av[kWalkBatch], bvv[kWalkBatch];
+#pragma unroll
+            for (int u = 0; u < kWalkBatch; ++u) {
+                const int64_t q = qb + (int64_t)u * T;
+                rows[u] = -1;
+                if (q < total) {
+                    // largest s with excl[s] <= q; owners only move forward as q grows
+                    int hi = nvalid - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (w.excl[mid] <= q) lo = mid; else hi = mid - 1;
+                    }
+                    const int64_t qa = w.a0[lo] + (q - w.excl[lo]);
+                    rows[u] = Arow[qa];
+                    if (VALS) {
+                        av[u] = Aval[qa];
+                        bvv[u] = w.bv[lo];
+                    }
+                }
             }
-            const int64_t qa = w.a0[lo] + (q - w.excl[lo]);
-            const int32_t row = Arow[qa];
-            VT prod = VT(0);
-            if (VALS) prod = Aval[qa] * w.bv[lo];
-            f(row, prod);
+#pragma unroll
+            for (int u = 0; u < kWalkBatch; ++u) {
+                if (rows[u] >= 0) {
+                    VT prod = VT(0);
+                    if (VALS) prod = av[u] * bvv[u];
+                    f(rows[u], prod);
+                }
+            }
         }
         __syncthreads();
     }

@@ -30,10 +30,14 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
                             int64_t *__restrict__ op, int64_t *__restrict__ Ccp, Ctrl *ctrl) {
     __shared__ unsigned long long s_hist[NBINS];
     __shared__ unsigned long long s_max[NBINS];
+    __shared__ unsigned long long s_binprod[NBINS];
+    __shared__ unsigned long long s_binb[NBINS];
     __shared__ unsigned long long s_prod;
     if (threadIdx.x < NBINS) {
         s_hist[threadIdx.x] = 0;
         s_max[threadIdx.x] = 0;
+        s_binprod[threadIdx.x] = 0;
+        s_binb[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) s_prod = 0;
     __syncthreads();
@@ -51,6 +55,8 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
         const int b = bin_of(s, t, hmax);
         atomicAdd(&s_hist[b], 1ULL);
         atomicMax(&s_max[b], (unsigned long long)s);
+        if (s) atomicAdd(&s_binprod[b], (unsigned long long)s);
+        if (p1 > p0) atomicAdd(&s_binb[b], (unsigned long long)(p1 - p0));
         if (b == BIN_EMPTY) Ccp[j + 1] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) Ccp[0] = 0;
@@ -60,6 +66,8 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
     if (threadIdx.x < NBINS && s_hist[threadIdx.x]) {
         atomicAdd(&ctrl->hist[threadIdx.x], s_hist[threadIdx.x]);
         atomicMax(&ctrl->maxop[threadIdx.x], s_max[threadIdx.x]);
+        atomicAdd(&ctrl->binprod[threadIdx.x], s_binprod[threadIdx.x]);
+        atomicAdd(&ctrl->binnnzb[threadIdx.x], s_binb[threadIdx.x]);
     }
     if (threadIdx.x == 0) atomicAdd(&ctrl->products, s_prod);
 }

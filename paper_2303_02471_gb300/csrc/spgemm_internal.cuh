@@ -59,6 +59,9 @@ struct Ctrl {
     unsigned long long maxnnz[NBINS];   // largest nnz(C_j) per bin
     unsigned long long work[NBINS];     // dynamic work counters (CTA kernels)
     unsigned long long maxop[NBINS];    // largest Op_j per bin
+    unsigned long long binprod[NBINS];  // sum of Op_j per bin
+    unsigned long long binnnz[NBINS];   // sum of nnz(C_j) per bin
+    unsigned long long binnnzb[NBINS];  // sum of nnz(B_j) per bin
     unsigned long long products;        // sum_j Op_j
     unsigned long long pad[3];
 };

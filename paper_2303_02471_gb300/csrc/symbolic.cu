@@ -18,9 +18,9 @@ template <int G, int R>
 __global__ void __launch_bounds__(kGroupThreads) k_sym_group(BinTask t, Operands o, int64_t *Ccp) {
     constexpr int H = 2 * G * R;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long s_max;
+    __shared__ unsigned long long s_max, s_sum;
     int32_t *keys = reinterpret_cast<int32_t *>(smem) + (threadIdx.x / G) * H;
-    if (threadIdx.x == 0) s_max = 0;
+    if (threadIdx.x == 0) s_max = s_sum = 0;
     __syncthreads();
     const unsigned mask = group_mask(G);
     const int gl = threadIdx.x & (G - 1);
@@ -45,10 +45,14 @@ __global__ void __launch_bounds__(kGroupThreads) k_sym_group(BinTask t, Operands
         if (gl == 0) {
             Ccp[j + 1] = cnt;
             atomicMax(&s_max, (unsigned long long)cnt);
+            atomicAdd(&s_sum, (unsigned long long)cnt);
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && s_max) atomicMax(&t.ctrl->maxnnz[t.bin], s_max);
+    if (threadIdx.x == 0 && s_max) {
+        atomicMax(&t.ctrl->maxnnz[t.bin], s_max);
+        atomicAdd(&t.ctrl->binnnz[t.bin], s_sum);
+    }
 }
 
 // ------------------------------------------------------- CTA hash bins
@@ -58,12 +62,12 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
                                                   int use_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
-    __shared__ unsigned long long s_cnt, s_max;
+    __shared__ unsigned long long s_cnt, s_max, s_sum;
     unsigned char *p = smem;
     WalkSmem<float> w = carve_walk<float>(p);
     int32_t *keys = use_global ? reinterpret_cast<int32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride)
                                : reinterpret_cast<int32_t *>(p);
-    if (threadIdx.x == 0) s_max = 0;
+    if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
@@ -95,10 +99,14 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
         if (threadIdx.x == 0) {
             Ccp[j + 1] = (int64_t)s_cnt;
             if (s_cnt > s_max) s_max = s_cnt;
+            s_sum += s_cnt;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && s_max) atomicMax(&t.ctrl->maxnnz[t.bin], s_max);
+    if (threadIdx.x == 0 && s_max) {
+        atomicMax(&t.ctrl->maxnnz[t.bin], s_max);
+        atomicAdd(&t.ctrl->binnnz[t.bin], s_sum);
+    }
 }
 
 // ------------------------------------------------------------ dense bin
@@ -107,13 +115,13 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
 __global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64_t *Ccp, int use_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
-    __shared__ unsigned long long s_cnt, s_max;
+    __shared__ unsigned long long s_cnt, s_max, s_sum;
     unsigned char *p = smem;
     WalkSmem<float> w = carve_walk<float>(p);
     uint32_t *bm = use_global ? reinterpret_cast<uint32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride)
                               : reinterpret_cast<uint32_t *>(p);
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = 0u;
-    if (threadIdx.x == 0) s_max = 0;
+    if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
@@ -142,10 +150,14 @@ __global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64
         if (threadIdx.x == 0) {
             Ccp[j + 1] = (int64_t)s_cnt;
             if (s_cnt > s_max) s_max = s_cnt;
+            s_sum += s_cnt;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && s_max) atomicMax(&t.ctrl->maxnnz[t.bin], s_max);
+    if (threadIdx.x == 0 && s_max) {
+        atomicMax(&t.ctrl->maxnnz[t.bin], s_max);
+        atomicAdd(&t.ctrl->binnnz[t.bin], s_sum);
+    }
 }
 
 // ------------------------------------------------------------- launches

@@ -147,6 +147,27 @@ class Plan:
                                       ctypes.byref(t)), "spg_plan_info")
         return {"bins": list(counts[:nb.value]), "products": prod.value, "t": t.value}
 
+    def bin_stats(self):
+        arrs = [(ctypes.c_int64 * 64)() for _ in range(5)]
+        N.check(N.lib().spg_plan_bin_stats(self.handle, *arrs), "spg_plan_bin_stats")
+        nb = len(self.info()["bins"])
+        keys = ("products", "nnz", "max_op", "max_nnz", "nnz_b")
+        return {k: list(a[:nb]) for k, a in zip(keys, arrs)}
+
+    def launch_count(self):
+        s, n, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        N.check(N.lib().spg_plan_launch_count(self.handle, ctypes.byref(s), ctypes.byref(n),
+                                              ctypes.byref(b)), "spg_plan_launch_count")
+        return {"symbolic": s.value, "numeric": n.value, "backward": b.value}
+
+    def set_timing(self, enable: bool = True) -> None:
+        N.check(N.lib().spg_plan_set_timing(self.handle, int(bool(enable))), "spg_plan_set_timing")
+
+    def bin_times(self):
+        ms = (ctypes.c_float * 64)()
+        N.check(N.lib().spg_plan_bin_times(self.handle, ms), "spg_plan_bin_times")
+        return list(ms[:len(self.info()["bins"])])
+
     def op_counts(self) -> torch.Tensor:
         out = torch.empty(self.shape[1], dtype=torch.int64, device=self.workspace.device)
         N.check(N.lib().spg_plan_op_counts(self.handle, _ptr(out), _stream()), "spg_plan_op_counts")
