@@ -68,10 +68,11 @@ Layout make_layout(int64_t m, int64_t nB, int64_t nnzA, int dtype, const spg_con
     // per-CTA global scratch: a bitmap (uint2 per 32 rows) plus, for hash
     // tables that do not fit shared memory, keys and values
     const int64_t reach = std::min<int64_t>(std::max<int64_t>(nnzA, 1), std::max<int64_t>(m, 1));
-    size_t tab = (size_t)num_slots(std::min<int64_t>(hmax, reach)) * (4 + w) + 32;
+    // hash table keys + values + word list of the extraction (numeric)
+    size_t tab = (size_t)num_slots(std::min<int64_t>(hmax, reach)) * (8 + w) + 64;
     if (effective_t(c) > hmax + 1) {
         const size_t sym = (size_t)global_sym_slots(reach, m) * 4;
-        const size_t num = (size_t)num_slots(reach) * (4 + w) + 32;
+        const size_t num = (size_t)num_slots(reach) * (8 + w) + 64;
         tab = std::max(tab, std::max(sym, num));
     }
     L.scratch_stride = align256((size_t)W * 8) + align256(tab);
@@ -162,7 +163,7 @@ spg_status spg_config_default(spg_config *cfg) {
     if (!cfg) return SPG_ERR_INVALID;
     cfg->t = -1;
     cfg->hash_cta_max = 8192;
-    cfg->cta_threads = 512;
+    cfg->cta_threads = 1024;
     cfg->validate = 1;
     cfg->table_shrink = 0;
     cfg->scratch_cap_bytes = (int64_t)1 << 30;

@@ -82,72 +82,32 @@ __device__ __forceinline__ void group_products(unsigned mask, const int64_t *__r
     }
 }
 
-// ------------------------------------------------------------- CTA walk
-__device__ __forceinline__ int64_t cta_incl_scan_i64(int64_t v, int64_t *s_warp, int64_t &total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int64_t o = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += o;
-    }
-    if (lane == 31) s_warp[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        int64_t w = lane < nw ? s_warp[lane] : 0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            int64_t o = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += o;
-        }
-        if (lane < nw) s_warp[lane] = w;
-    }
-    __syncthreads();
-    total = s_warp[nw - 1];
-    const int64_t r = v + (warp > 0 ? s_warp[warp - 1] : 0);
-    __syncthreads();
-    return r;
-}
-
-// Products a thread of the CTA walk gathers before it consumes them.
+// Products a thread of a walk gathers before it consumes them.
 constexpr int kWalkBatch = 4;
 
-// Shared scratch of the CTA walk: one B entry per thread of the chunk.
-template <typename VT>
-struct WalkSmem {
-    int64_t *excl;  // [blockDim]
-    int64_t *a0;    // [blockDim]
-    VT *bv;         // [blockDim]
-    int64_t *warp;  // [32]
-};
-
-template <typename VT>
-__host__ __device__ inline size_t walk_smem_bytes(int threads) {
-    return (size_t)threads * (16 + sizeof(VT)) + 32 * 8;
-}
-
-template <typename VT>
-__device__ __forceinline__ WalkSmem<VT> carve_walk(unsigned char *&p) {
-    WalkSmem<VT> w;
-    w.excl = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
-    w.a0 = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
-    w.warp = reinterpret_cast<int64_t *>(p); p += 32 * 8;
-    w.bv = reinterpret_cast<VT *>(p); p += (size_t)blockDim.x * sizeof(VT);
-    p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
-    return w;
-}
-
-// The whole CTA walks the products of B entries [p0, p1); f(row, product)
-// per product.  Contains __syncthreads: every thread must call it.
+// ------------------------------------------------------------ warp walk
+// Every warp of the CTA takes chunks of 32 B entries of [p0, p1) from a
+// shared counter (*s_next, zeroed by the caller before a barrier) and walks
+// their products: the chunk's Z^A_k are prefix-summed with shuffles, each
+// lane takes the products q, q + 32, ... of the flattened chunk and finds
+// its B entry by a 5-step binary search over the lanes' prefix sums.
+// kWalkBatch windows of 32 products are gathered before they are consumed.
+// No barrier inside: warps run independently until the caller's barrier.
 template <bool VALS, typename VT, typename F>
-__device__ __forceinline__ void cta_products(const int64_t *__restrict__ Acp,
-                                             const int32_t *__restrict__ Arow,
-                                             const VT *__restrict__ Aval,
-                                             const int32_t *__restrict__ Brow,
-                                             const VT *__restrict__ Bval, int64_t p0, int64_t p1,
-                                             const WalkSmem<VT> &w, F &&f) {
-    const int T = blockDim.x;
-    for (int64_t base = p0; base < p1; base += T) {
-        const int64_t p = base + threadIdx.x;
+__device__ __forceinline__ void warp_walk(const int64_t *__restrict__ Acp,
+                                          const int32_t *__restrict__ Arow,
+                                          const VT *__restrict__ Aval,
+                                          const int32_t *__restrict__ Brow,
+                                          const VT *__restrict__ Bval, int64_t p0, int64_t p1,
+                                          int *s_next, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (p1 - p0 + 31) >> 5;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(s_next, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const int64_t p = p0 + ((int64_t)c << 5) + lane;
         int64_t z = 0, a0 = 0;
         VT bv = VT(0);
         if (p < p1) {
@@ -156,35 +116,35 @@ __device__ __forceinline__ void cta_products(const int64_t *__restrict__ Acp,
             z = Acp[k + 1] - a0;
             if (VALS) bv = Bval[p];
         }
-        int64_t total;
-        const int64_t incl = cta_incl_scan_i64(z, w.warp, total);
-        w.excl[threadIdx.x] = incl - z;
-        w.a0[threadIdx.x] = a0;
-        if (VALS) w.bv[threadIdx.x] = bv;
-        __syncthreads();
-        const int nvalid = (int)((p1 - base) < T ? (p1 - base) : T);
-        int lo = 0;
-        // kWalkBatch products per thread are gathered before any is used, so
-        // their L2/HBM latencies overlap.
-        for (int64_t qb = threadIdx.x; qb < total; qb += (int64_t)T * kWalkBatch) {
+        int64_t incl = z;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const int64_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const int64_t excl = incl - z;
+        for (int64_t q0 = 0; q0 < total; q0 += 32 * kWalkBatch) {
             int32_t rows[kWalkBatch];
-            VT av[kWalkBatch], bvv[kWalkBatch];
+            VT av[kWalkBatch], bvs[kWalkBatch];
 #pragma unroll
             for (int u = 0; u < kWalkBatch; ++u) {
-                const int64_t q = qb + (int64_t)u * T;
                 rows[u] = -1;
-                if (q < total) {
-                    // largest s with excl[s] <= q; owners only move forward as q grows
-                    int hi = nvalid - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (w.excl[mid] <= q) lo = mid; else hi = mid - 1;
+                const int64_t q = q0 + 32 * u + lane;
+                if (q0 + 32 * u < total) {  // uniform over the warp
+                    int s = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int64_t ex = __shfl_sync(0xffffffffu, excl, s + step);
+                        if (ex <= q) s += step;
                     }
-                    const int64_t qa = w.a0[lo] + (q - w.excl[lo]);
-                    rows[u] = Arow[qa];
-                    if (VALS) {
-                        av[u] = Aval[qa];
-                        bvv[u] = w.bv[lo];
+                    const int64_t a0s = __shfl_sync(0xffffffffu, a0, s);
+                    const int64_t exs = __shfl_sync(0xffffffffu, excl, s);
+                    if (VALS) bvs[u] = __shfl_sync(0xffffffffu, bv, s);
+                    if (q < total) {
+                        const int64_t qa = a0s + (q - exs);
+                        rows[u] = Arow[qa];
+                        if (VALS) av[u] = Aval[qa];
                     }
                 }
             }
@@ -192,13 +152,125 @@ __device__ __forceinline__ void cta_products(const int64_t *__restrict__ Acp,
             for (int u = 0; u < kWalkBatch; ++u) {
                 if (rows[u] >= 0) {
                     VT prod = VT(0);
-                    if (VALS) prod = av[u] * bvv[u];
+                    if (VALS) prod = av[u] * bvs[u];
                     f(rows[u], prod);
                 }
             }
         }
-        __syncthreads();
     }
+}
+
+// ------------------------------------------------- two-level row bitmap
+// For extracting a hash table's rows in ascending order in O(m / 1024 + n)
+// per column: L0 has one bit per row, L1 one bit per non-zero L0 word.
+// After marking, cta_list_words writes the indices of the non-zero L0 words
+// in ascending order to `wlist` and returns their number; cta_expand_words
+// then visits the rows in ascending order with their ranks and clears both
+// levels.  Every thread must call both (they contain barriers).
+__device__ __forceinline__ void mark_row(uint32_t *L0, uint32_t *L1, int32_t row) {
+    const uint32_t bit = 1u << (row & 31);
+    const uint32_t old = atomicOr(&L0[row >> 5], bit);
+    if (old == 0u) atomicOr(&L1[row >> 10], 1u << ((row >> 5) & 31));
+}
+
+__device__ __forceinline__ int64_t cta_list_words(uint32_t *L1, int64_t W1, int32_t *wlist, int64_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // each warp owns a contiguous range of L1 words
+    const int64_t per = ((W1 + nw - 1) / nw + 31) & ~int64_t(31);
+    const int64_t w0 = (int64_t)warp * per < W1 ? (int64_t)warp * per : W1;
+    const int64_t w1 = w0 + per < W1 ? w0 + per : W1;
+    int64_t cnt = 0;
+    for (int64_t w = w0 + lane; w < w1; w += 32) cnt += __popc(L1[w]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+    if (lane == 0) s_warp[warp] = cnt;
+    __syncthreads();
+    int64_t off = 0, total = 0;
+    for (int i = 0; i < nw; ++i) {
+        const int64_t c = s_warp[i];
+        if (i < warp) off += c;
+        total += c;
+    }
+    for (int64_t base = w0; base < w1; base += 32) {
+        const int64_t w = base + lane;
+        uint32_t bits = w < w1 ? L1[w] : 0u;
+        const int c = __popc(bits);
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        int64_t pos = off + incl - c;
+        if (w < w1) {
+            L1[w] = 0u;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                wlist[pos++] = (int32_t)(w * 32 + b);
+            }
+        }
+        off += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncthreads();
+    return total;
+}
+
+// Visits the rows of the K listed L0 words in ascending order: f(row, rank).
+// Warps own contiguous ranges of the list; lanes expand consecutive words so
+// consecutive lanes get consecutive ranks (coalesced writes).  Clears L0.
+template <typename F>
+__device__ __forceinline__ void cta_expand_words(uint32_t *L0, const int32_t *wlist, int64_t K, int64_t *s_warp,
+                                                 F &&f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t per = ((K + nw - 1) / nw + 31) & ~int64_t(31);
+    const int64_t k0 = (int64_t)warp * per < K ? (int64_t)warp * per : K;
+    const int64_t k1 = k0 + per < K ? k0 + per : K;
+    int64_t cnt = 0;
+    for (int64_t i = k0 + lane; i < k1; i += 32) cnt += __popc(L0[wlist[i]]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+    if (lane == 0) s_warp[warp] = cnt;
+    __syncthreads();
+    int64_t off = 0;
+    for (int i = 0; i < warp; ++i) off += s_warp[i];
+    for (int64_t base = k0; base < k1; base += 32) {
+        const int64_t i = base + lane;
+        int32_t word = 0;
+        uint32_t v = 0u;
+        if (i < k1) {
+            word = wlist[i];
+            v = L0[word];
+            L0[word] = 0u;
+        }
+        const int cntl = __popc(v);
+        int incl = cntl;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const int S = __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = incl - cntl;
+        for (int o0 = 0; o0 < S; o0 += 32) {
+            const int o = o0 + lane;
+            int s = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(0xffffffffu, excl, s + step);
+                if (ex <= o) s += step;
+            }
+            uint32_t b = __shfl_sync(0xffffffffu, v, s);
+            const int kk = o - __shfl_sync(0xffffffffu, excl, s);
+            const int32_t ws = __shfl_sync(0xffffffffu, word, s);
+            if (o < S) {
+                for (int t = 0; t < kk; ++t) b &= b - 1u;
+                f(ws * 32 + (__ffs(b) - 1), off + o);
+            }
+        }
+        off += S;
+    }
+    __syncthreads();
 }
 
 // ------------------------------------------------------ bitmap ranking

@@ -122,29 +122,55 @@ __global__ void __launch_bounds__(kGroupThreads) k_num_group(BinTask t, Operands
 }
 
 // ------------------------------------------------------- CTA hash bins
+__host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
+
 template <typename VT>
 __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
                                                   VT *Cval, int64_t cap, int table_global, int bm_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
-    unsigned char *p = smem;
-    WalkSmem<VT> w = carve_walk<VT>(p);
-    unsigned char *g = t.scratch + (size_t)blockIdx.x * t.scratch_stride;
+    __shared__ int s_next;
+    __shared__ unsigned s_occ;
+    __shared__ int64_t s_warp[32];
+    const int64_t W1 = (t.W + 31) / 32;
+    unsigned char *sp = smem;
+    unsigned char *gp = t.scratch + (size_t)blockIdx.x * t.scratch_stride;
     int32_t *keys;
     VT *vals;
-    unsigned char *&tp = table_global ? g : p;
-    keys = reinterpret_cast<int32_t *>(tp);
-    tp += (size_t)cap * 4;
-    tp = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tp) + 15) & ~uintptr_t(15));
-    vals = reinterpret_cast<VT *>(tp);
-    tp += (size_t)cap * sizeof(VT);
-    tp = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tp) + 15) & ~uintptr_t(15));
-    uint2 *bm = reinterpret_cast<uint2 *>(bm_global ? g : p);
-    for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
+    // the table and the word list scale with the table size: both live in
+    // shared memory, or both in the CTA's global scratch
+    int32_t *wlist;
+    if (table_global) {
+        keys = reinterpret_cast<int32_t *>(gp);
+        vals = reinterpret_cast<VT *>(gp + al16((size_t)cap * 4));
+        gp += al16((size_t)cap * 4) + al16((size_t)cap * sizeof(VT));
+        wlist = reinterpret_cast<int32_t *>(gp);
+        gp += al16((size_t)cap * 4);
+    } else {
+        keys = reinterpret_cast<int32_t *>(sp);
+        vals = reinterpret_cast<VT *>(sp + al16((size_t)cap * 4));
+        sp += al16((size_t)cap * 4) + al16((size_t)cap * sizeof(VT));
+        wlist = reinterpret_cast<int32_t *>(sp);
+        sp += al16((size_t)cap * 4);
+    }
+    uint32_t *L0;
+    if (bm_global) {
+        L0 = reinterpret_cast<uint32_t *>(gp);
+    } else {
+        L0 = reinterpret_cast<uint32_t *>(sp);
+        sp += al16((size_t)t.W * 4);
+    }
+    uint32_t *L1 = reinterpret_cast<uint32_t *>(sp);
+    for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) L0[i] = 0u;
+    for (int64_t i = threadIdx.x; i < W1; i += blockDim.x) L1[i] = 0u;
     const VT *Aval = static_cast<const VT *>(o.Aval);
     const VT *Bval = static_cast<const VT *>(o.Bval);
     for (;;) {
-        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
+        if (threadIdx.x == 0) {
+            s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
+            s_next = 0;
+            s_occ = 0;
+        }
         __syncthreads();
         const int64_t ci = s_col;
         if (ci >= t.count) break;
@@ -161,30 +187,37 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
         }
         __syncthreads();
         bool ovf = false;
-        cta_products<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                               [&](int32_t row, VT prod) {
-                                   bool fresh;
-                                   const int32_t slot = hash_insert(keys, H, row, fresh);
-                                   if (slot < 0) ovf = true;
-                                   else atomicAdd(&vals[slot], prod);
-                               });
+        warp_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], &s_next,
+                            [&](int32_t row, VT prod) {
+                                bool fresh;
+                                const int32_t slot = hash_insert(keys, H, row, fresh);
+                                if (slot < 0) ovf = true;
+                                else atomicAdd(&vals[slot], prod);
+                            });
         if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
+        __syncthreads();
+        unsigned occ = 0;
         for (uint32_t s = threadIdx.x; s < H; s += blockDim.x) {
             const int32_t key = keys[s];
-            if (key != kEmptyKey) atomicOr(&bm[key >> 5].x, 1u << (key & 31));
+            if (key != kEmptyKey) {
+                mark_row(L0, L1, key);
+                ++occ;
+            }
         }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) occ += __shfl_xor_sync(0xffffffffu, occ, d);
+        if ((threadIdx.x & 31) == 0 && occ) atomicAdd(&s_occ, occ);
         __syncthreads();
-        const int64_t total = cta_bitmap_prefix(bm, t.W, w.warp);
-        if (total != nn && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
-        const bool ok = total == nn;
-        cta_bitmap_expand(bm, t.W, true, [&](int32_t row, int64_t rank) {
+        const bool ok = (int64_t)s_occ == nn;
+        if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
+        const int64_t K = cta_list_words(L1, W1, wlist, s_warp);
+        cta_expand_words(L0, wlist, K, s_warp, [&](int32_t row, int64_t rank) {
             const int32_t slot = hash_find(keys, H, row);
             if (ok && slot >= 0) {
                 Crow[c0 + rank] = row;
                 Cval[c0 + rank] = vals[slot];
             }
         });
-        __syncthreads();
     }
 }
 
@@ -194,8 +227,9 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
                                                     VT *Cval, int64_t cap, int bm_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
+    __shared__ int s_next;
+    __shared__ int64_t s_warp[32];
     unsigned char *p = smem;
-    WalkSmem<VT> w = carve_walk<VT>(p);
     uint2 *bm;
     if (bm_global) {
         bm = reinterpret_cast<uint2 *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
@@ -208,7 +242,10 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
     const VT *Aval = static_cast<const VT *>(o.Aval);
     const VT *Bval = static_cast<const VT *>(o.Bval);
     for (;;) {
-        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
+        if (threadIdx.x == 0) {
+            s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
+            s_next = 0;
+        }
         __syncthreads();
         const int64_t ci = s_col;
         if (ci >= t.count) break;
@@ -216,22 +253,25 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
         const int64_t c0 = Ccp[j];
         const int64_t nn = Ccp[j + 1] - c0;
         // walk 1: SPA flags
-        cta_products<false, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                                [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
-        const int64_t total = cta_bitmap_prefix(bm, t.W, w.warp);
+        warp_walk<false, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], &s_next,
+                             [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
+        __syncthreads();
+        const int64_t total = cta_bitmap_prefix(bm, t.W, s_warp);
         const bool ok = total == nn;
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
         const bool in_smem = nn <= cap;
         VT *acc = in_smem ? s_acc : Cval + c0;
         if (ok)
             for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) acc[i] = VT(0);
+        if (threadIdx.x == 0) s_next = 0;
         __syncthreads();
         // walk 2: accumulate every product at its row's sorted position
-        cta_products<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                               [&](int32_t row, VT prod) {
-                                   const int32_t r = bitmap_rank(bm, row);
-                                   if (ok) atomicAdd(&acc[r], prod);
-                               });
+        warp_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], &s_next,
+                            [&](int32_t row, VT prod) {
+                                const int32_t r = bitmap_rank(bm, row);
+                                if (ok) atomicAdd(&acc[r], prod);
+                            });
+        __syncthreads();
         cta_bitmap_expand(bm, t.W, true, [&](int32_t row, int64_t rank) {
             if (ok) {
                 Crow[c0 + rank] = row;
@@ -245,12 +285,21 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
 // ------------------------------------------------------------- launches
 constexpr size_t kBitmapSmemMax = 96 * 1024;
 
+// Threads per CTA of the CTA-level bins: small columns share an SM among
+// several CTAs, the largest get a whole SM.
+inline int cta_bin_threads(int bin, int cfg_threads) {
+    if (bin == BIN_CTA0 || bin == BIN_CTA0 + 1) return 256;
+    if (bin == BIN_CTA0 + 2 || bin == BIN_CTA0 + 3) return 512;
+    return cfg_threads;
+}
+
 template <typename VT>
 static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
                               int64_t maxnnz, int shrink, int64_t scratch_ctas) {
     (void)shrink;
     Geo g;
     const int64_t W = ceil_div(m, 32);
+    const int64_t W1 = ceil_div(W, 32);
     if (bin >= BIN_WARP0 && bin < BIN_CTA0) {
         const int b = bin - BIN_WARP0;
         const int G = warp_bin_G(b), R = warp_bin_R(b);
@@ -259,31 +308,34 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
         g.grid = (int)ceil_div(count, kGroupThreads / G);
         return g;
     }
-    g.threads = threads;
-    const size_t walk = walk_smem_bytes<VT>(threads) + 16;
-    const size_t bmb = (size_t)W * 8;
+    g.threads = cta_bin_threads(bin, threads);
     if (bin >= BIN_CTA0 && bin <= BIN_GLOBAL) {
         g.slots = num_slots(maxnnz);
-        const size_t tab = ((size_t)g.slots * 4 + 15) / 16 * 16 + ((size_t)g.slots * sizeof(VT) + 15) / 16 * 16;
-        const bool table_global = bin == BIN_GLOBAL || walk + tab > smem_optin;
-        g.bm_global = bmb > kBitmapSmemMax || walk + (table_global ? 0 : tab) + bmb > smem_optin;
+        // table (keys, values) and word list; L1 always in shared memory
+        const size_t tab = al16((size_t)g.slots * 4) + al16((size_t)g.slots * sizeof(VT)) +
+                           al16((size_t)g.slots * 4);
+        const size_t fixed = al16((size_t)W1 * 4);
+        const size_t l0 = al16((size_t)W * 4);
+        const bool table_global = bin == BIN_GLOBAL || fixed + tab > smem_optin;
+        g.bm_global = l0 > kBitmapSmemMax || fixed + (table_global ? 0 : tab) + l0 > smem_optin;
         g.cap = table_global ? 1 : 0;  // reused as "table in global" flag
-        g.smem = walk + (table_global ? 0 : tab) + (g.bm_global ? 0 : bmb);
-        int occ = occupancy(k_num_cta<VT>, threads, g.smem);
+        g.smem = fixed + (table_global ? 0 : tab) + (g.bm_global ? 0 : l0);
+        int occ = occupancy(k_num_cta<VT>, g.threads, g.smem);
         int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
         if (table_global || g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);
         g.grid = (int)std::max<int64_t>(1, grid);
         return g;
     }
     // dense
-    g.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
-    size_t base = walk + (g.bm_global ? 0 : bmb);
+    const size_t bmb = (size_t)W * 8;
+    g.bm_global = bmb > kBitmapSmemMax || bmb > smem_optin;
+    size_t base = g.bm_global ? 0 : bmb;
     size_t room = smem_optin > base ? smem_optin - base : 0;
     int64_t cap = (int64_t)(room / sizeof(VT));
     if (cap > maxnnz) cap = maxnnz;
     g.cap = cap;
     g.smem = base + (size_t)cap * sizeof(VT);
-    int occ = occupancy(k_num_dense<VT>, threads, g.smem);
+    int occ = occupancy(k_num_dense<VT>, g.threads, g.smem);
     int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
     if (g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);
     g.grid = (int)std::max<int64_t>(1, grid);

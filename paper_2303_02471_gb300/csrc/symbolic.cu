@@ -62,16 +62,16 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
                                                   int use_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
+    __shared__ int s_next;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
-    unsigned char *p = smem;
-    WalkSmem<float> w = carve_walk<float>(p);
     int32_t *keys = use_global ? reinterpret_cast<int32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride)
-                               : reinterpret_cast<int32_t *>(p);
+                               : reinterpret_cast<int32_t *>(smem);
     if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
             s_cnt = 0;
+            s_next = 0;
         }
         __syncthreads();
         const int64_t ci = s_col;
@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
         __syncthreads();
         unsigned cnt = 0;
         bool ovf = false;
-        cta_products<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
-                                   [&](int32_t row, float) {
-                                       bool fresh;
-                                       if (hash_insert(keys, H, row, fresh) < 0) ovf = true;
-                                       cnt += fresh;
-                                   });
+        warp_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], &s_next,
+                                [&](int32_t row, float) {
+                                    bool fresh;
+                                    if (hash_insert(keys, H, row, fresh) < 0) ovf = true;
+                                    cnt += fresh;
+                                });
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
         if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, (unsigned long long)cnt);
@@ -115,34 +115,31 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
 __global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64_t *Ccp, int use_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
+    __shared__ int s_next;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
-    unsigned char *p = smem;
-    WalkSmem<float> w = carve_walk<float>(p);
     uint32_t *bm = use_global ? reinterpret_cast<uint32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride)
-                              : reinterpret_cast<uint32_t *>(p);
+                              : reinterpret_cast<uint32_t *>(smem);
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = 0u;
     if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
             s_cnt = 0;
+            s_next = 0;
         }
         __syncthreads();
         const int64_t ci = s_col;
         if (ci >= t.count) break;
         const int32_t j = t.cols[ci];
-        cta_products<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
-                                   [&](int32_t row, float) {
-                                       atomicOr(&bm[row >> 5], 1u << (row & 31));
-                                   });
+        // a row is new when its flag bit was still clear (Algorithm 1's counter)
         unsigned long long cnt = 0;
-        for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) {
-            const uint32_t b = bm[i];
-            if (b) {
-                cnt += __popc(b);
-                bm[i] = 0u;
-            }
-        }
+        warp_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], &s_next,
+                                [&](int32_t row, float) {
+                                    const uint32_t bit = 1u << (row & 31);
+                                    cnt += (atomicOr(&bm[row >> 5], bit) & bit) ? 0 : 1;
+                                });
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = 0u;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
         if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
@@ -191,7 +188,7 @@ Geo symbolic_geometry(int bin, int64_t count, int64_t m, int threads, int sms, s
         return g;
     }
     g.threads = threads;
-    const size_t walk = walk_smem_bytes<float>(threads) + 16;
+    const size_t walk = 0;
     if (bin >= BIN_CTA0 && bin < BIN_GLOBAL) {
         g.slots = global_sym_slots(cta_bin_opmax(bin - BIN_CTA0), m);
         g.smem = walk + (size_t)g.slots * 4;
