@@ -85,29 +85,73 @@ __device__ __forceinline__ void group_products(unsigned mask, const int64_t *__r
 // Products a thread of a walk gathers before it consumes them.
 constexpr int kWalkBatch = 4;
 
-// ------------------------------------------------------------ warp walk
-// Every warp of the CTA takes chunks of 32 B entries of [p0, p1) from a
-// shared counter (*s_next, zeroed by the caller before a barrier) and walks
-// their products: the chunk's Z^A_k are prefix-summed with shuffles, each
-// lane takes the products q, q + 32, ... of the flattened chunk and finds
-// its B entry by a 5-step binary search over the lanes' prefix sums.
-// kWalkBatch windows of 32 products are gathered before they are consumed.
-// No barrier inside: warps run independently until the caller's barrier.
+// ------------------------------------------------------------- CTA walk
+__device__ __forceinline__ int64_t cta_incl_scan_i64(int64_t v, int64_t *s_warp, int64_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t x = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += o;
+        }
+        if (lane < nw) s_warp[lane] = x;
+    }
+    __syncthreads();
+    total = s_warp[nw - 1];
+    return v + (warp > 0 ? s_warp[warp - 1] : 0);
+}
+
+// Shared scratch of the CTA walk: one B entry per thread of a chunk.
+template <typename VT>
+struct WalkSmem {
+    int64_t *excl;  // [blockDim] products before this entry in the chunk
+    int64_t *a0;    // [blockDim] start of A column k
+    VT *bv;         // [blockDim] B_kj
+    int64_t *warp;  // [32]
+};
+
+template <typename VT>
+__host__ __device__ inline size_t walk_smem_bytes(int threads) {
+    return (size_t)threads * (16 + sizeof(VT)) + 32 * 8 + 16;
+}
+
+template <typename VT>
+__device__ __forceinline__ WalkSmem<VT> carve_walk(unsigned char *&p) {
+    WalkSmem<VT> w;
+    w.excl = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
+    w.a0 = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
+    w.warp = reinterpret_cast<int64_t *>(p); p += 32 * 8;
+    w.bv = reinterpret_cast<VT *>(p); p += (size_t)blockDim.x * sizeof(VT);
+    p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+    return w;
+}
+
+// The whole CTA walks the products of B entries [p0, p1).  Per chunk of
+// blockDim entries: one block scan of Z^A_k, then the chunk's products are
+// cut into windows of 32 (one product per lane, consecutive lanes on
+// consecutive entries of an A column: coalesced) and every warp takes an
+// equal contiguous share of the windows, so the work is balanced over
+// products, not over B entries.  A lane finds the B entry of its product by
+// binary search over the chunk's prefix sums in shared memory; kWalkBatch
+// windows are searched and gathered before any product is consumed.
+// f(row, product) per product.  Contains barriers: every thread calls it.
 template <bool VALS, typename VT, typename F>
-__device__ __forceinline__ void warp_walk(const int64_t *__restrict__ Acp,
-                                          const int32_t *__restrict__ Arow,
-                                          const VT *__restrict__ Aval,
-                                          const int32_t *__restrict__ Brow,
-                                          const VT *__restrict__ Bval, int64_t p0, int64_t p1,
-                                          int *s_next, F &&f) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nchunks = (p1 - p0 + 31) >> 5;
-    for (;;) {
-        int c = 0;
-        if (lane == 0) c = atomicAdd(s_next, 1);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= nchunks) break;
-        const int64_t p = p0 + ((int64_t)c << 5) + lane;
+__device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const int32_t *__restrict__ Arow,
+                                         const VT *__restrict__ Aval, const int32_t *__restrict__ Brow,
+                                         const VT *__restrict__ Bval, int64_t p0, int64_t p1,
+                                         const WalkSmem<VT> &w, F &&f) {
+    const int T = blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+    for (int64_t base = p0; base < p1; base += T) {
+        const int64_t p = base + threadIdx.x;
         int64_t z = 0, a0 = 0;
         VT bv = VT(0);
         if (p < p1) {
@@ -116,35 +160,36 @@ __device__ __forceinline__ void warp_walk(const int64_t *__restrict__ Acp,
             z = Acp[k + 1] - a0;
             if (VALS) bv = Bval[p];
         }
-        int64_t incl = z;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int64_t o = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += o;
-        }
-        const int64_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const int64_t excl = incl - z;
-        for (int64_t q0 = 0; q0 < total; q0 += 32 * kWalkBatch) {
+        int64_t total;
+        const int64_t incl = cta_incl_scan_i64(z, w.warp, total);
+        w.excl[threadIdx.x] = incl - z;
+        w.a0[threadIdx.x] = a0;
+        if (VALS) w.bv[threadIdx.x] = bv;
+        __syncthreads();
+        const int nvalid = (int)((p1 - base) < T ? (p1 - base) : T);
+        const int64_t nwin = (total + 31) >> 5;
+        const int64_t win0 = nwin * warp / nw, win1 = nwin * (warp + 1) / nw;
+        int lo = 0;
+        for (int64_t win = win0; win < win1; win += kWalkBatch) {
             int32_t rows[kWalkBatch];
             VT av[kWalkBatch], bvs[kWalkBatch];
+            const int start = lo;
 #pragma unroll
             for (int u = 0; u < kWalkBatch; ++u) {
                 rows[u] = -1;
-                const int64_t q = q0 + 32 * u + lane;
-                if (q0 + 32 * u < total) {  // uniform over the warp
-                    int s = 0;
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1) {
-                        const int64_t ex = __shfl_sync(0xffffffffu, excl, s + step);
-                        if (ex <= q) s += step;
+                const int64_t q = ((win + u) << 5) + lane;
+                if (win + u < win1 && q < total) {
+                    int l = start, hi = nvalid - 1;
+                    while (l < hi) {
+                        const int mid = (l + hi + 1) >> 1;
+                        if (w.excl[mid] <= q) l = mid; else hi = mid - 1;
                     }
-                    const int64_t a0s = __shfl_sync(0xffffffffu, a0, s);
-                    const int64_t exs = __shfl_sync(0xffffffffu, excl, s);
-                    if (VALS) bvs[u] = __shfl_sync(0xffffffffu, bv, s);
-                    if (q < total) {
-                        const int64_t qa = a0s + (q - exs);
-                        rows[u] = Arow[qa];
-                        if (VALS) av[u] = Aval[qa];
+                    lo = l;
+                    const int64_t qa = w.a0[l] + (q - w.excl[l]);
+                    rows[u] = Arow[qa];
+                    if (VALS) {
+                        av[u] = Aval[qa];
+                        bvs[u] = w.bv[l];
                     }
                 }
             }
@@ -157,6 +202,7 @@ __device__ __forceinline__ void warp_walk(const int64_t *__restrict__ Acp,
                 }
             }
         }
+        __syncthreads();
     }
 }
 

@@ -129,11 +129,11 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
                                                   VT *Cval, int64_t cap, int table_global, int bm_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
-    __shared__ int s_next;
     __shared__ unsigned s_occ;
     __shared__ int64_t s_warp[32];
     const int64_t W1 = (t.W + 31) / 32;
     unsigned char *sp = smem;
+    const WalkSmem<VT> w = carve_walk<VT>(sp);
     unsigned char *gp = t.scratch + (size_t)blockIdx.x * t.scratch_stride;
     int32_t *keys;
     VT *vals;
@@ -168,7 +168,6 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
     for (;;) {
         if (threadIdx.x == 0) {
             s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
-            s_next = 0;
             s_occ = 0;
         }
         __syncthreads();
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
         }
         __syncthreads();
         bool ovf = false;
-        warp_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], &s_next,
+        cta_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
                             [&](int32_t row, VT prod) {
                                 bool fresh;
                                 const int32_t slot = hash_insert(keys, H, row, fresh);
@@ -195,7 +194,6 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
                                 else atomicAdd(&vals[slot], prod);
                             });
         if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
-        __syncthreads();
         unsigned occ = 0;
         for (uint32_t s = threadIdx.x; s < H; s += blockDim.x) {
             const int32_t key = keys[s];
@@ -227,9 +225,9 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
                                                     VT *Cval, int64_t cap, int bm_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
-    __shared__ int s_next;
     __shared__ int64_t s_warp[32];
     unsigned char *p = smem;
+    const WalkSmem<VT> w = carve_walk<VT>(p);
     uint2 *bm;
     if (bm_global) {
         bm = reinterpret_cast<uint2 *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
@@ -242,10 +240,7 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
     const VT *Aval = static_cast<const VT *>(o.Aval);
     const VT *Bval = static_cast<const VT *>(o.Bval);
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
-            s_next = 0;
-        }
+        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
         __syncthreads();
         const int64_t ci = s_col;
         if (ci >= t.count) break;
@@ -253,9 +248,8 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
         const int64_t c0 = Ccp[j];
         const int64_t nn = Ccp[j + 1] - c0;
         // walk 1: SPA flags
-        warp_walk<false, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], &s_next,
+        cta_walk<false, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
                              [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
-        __syncthreads();
         const int64_t total = cta_bitmap_prefix(bm, t.W, s_warp);
         const bool ok = total == nn;
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
@@ -263,15 +257,13 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
         VT *acc = in_smem ? s_acc : Cval + c0;
         if (ok)
             for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) acc[i] = VT(0);
-        if (threadIdx.x == 0) s_next = 0;
         __syncthreads();
         // walk 2: accumulate every product at its row's sorted position
-        warp_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], &s_next,
+        cta_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
                             [&](int32_t row, VT prod) {
                                 const int32_t r = bitmap_rank(bm, row);
                                 if (ok) atomicAdd(&acc[r], prod);
                             });
-        __syncthreads();
         cta_bitmap_expand(bm, t.W, true, [&](int32_t row, int64_t rank) {
             if (ok) {
                 Crow[c0 + rank] = row;
@@ -314,7 +306,7 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
         // table (keys, values) and word list; L1 always in shared memory
         const size_t tab = al16((size_t)g.slots * 4) + al16((size_t)g.slots * sizeof(VT)) +
                            al16((size_t)g.slots * 4);
-        const size_t fixed = al16((size_t)W1 * 4);
+        const size_t fixed = al16((size_t)W1 * 4) + walk_smem_bytes<VT>(g.threads);
         const size_t l0 = al16((size_t)W * 4);
         const bool table_global = bin == BIN_GLOBAL || fixed + tab > smem_optin;
         g.bm_global = l0 > kBitmapSmemMax || fixed + (table_global ? 0 : tab) + l0 > smem_optin;
@@ -328,8 +320,9 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
     }
     // dense
     const size_t bmb = (size_t)W * 8;
-    g.bm_global = bmb > kBitmapSmemMax || bmb > smem_optin;
-    size_t base = g.bm_global ? 0 : bmb;
+    const size_t walk = walk_smem_bytes<VT>(g.threads);
+    g.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
+    size_t base = walk + (g.bm_global ? 0 : bmb);
     size_t room = smem_optin > base ? smem_optin - base : 0;
     int64_t cap = (int64_t)(room / sizeof(VT));
     if (cap > maxnnz) cap = maxnnz;

@@ -62,16 +62,16 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
                                                   int use_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
-    __shared__ int s_next;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
+    unsigned char *p = smem;
+    const WalkSmem<float> w = carve_walk<float>(p);
     int32_t *keys = use_global ? reinterpret_cast<int32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride)
-                               : reinterpret_cast<int32_t *>(smem);
+                               : reinterpret_cast<int32_t *>(p);
     if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
             s_cnt = 0;
-            s_next = 0;
         }
         __syncthreads();
         const int64_t ci = s_col;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
         __syncthreads();
         unsigned cnt = 0;
         bool ovf = false;
-        warp_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], &s_next,
+        cta_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
                                 [&](int32_t row, float) {
                                     bool fresh;
                                     if (hash_insert(keys, H, row, fresh) < 0) ovf = true;
@@ -115,17 +115,17 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
 __global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64_t *Ccp, int use_global) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
-    __shared__ int s_next;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
+    unsigned char *p = smem;
+    const WalkSmem<float> w = carve_walk<float>(p);
     uint32_t *bm = use_global ? reinterpret_cast<uint32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride)
-                              : reinterpret_cast<uint32_t *>(smem);
+                              : reinterpret_cast<uint32_t *>(p);
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = 0u;
     if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
             s_cnt = 0;
-            s_next = 0;
         }
         __syncthreads();
         const int64_t ci = s_col;
@@ -133,12 +133,11 @@ __global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64
         const int32_t j = t.cols[ci];
         // a row is new when its flag bit was still clear (Algorithm 1's counter)
         unsigned long long cnt = 0;
-        warp_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], &s_next,
+        cta_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
                                 [&](int32_t row, float) {
                                     const uint32_t bit = 1u << (row & 31);
                                     cnt += (atomicOr(&bm[row >> 5], bit) & bit) ? 0 : 1;
                                 });
-        __syncthreads();
         for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = 0u;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
@@ -188,7 +187,7 @@ Geo symbolic_geometry(int bin, int64_t count, int64_t m, int threads, int sms, s
         return g;
     }
     g.threads = threads;
-    const size_t walk = 0;
+    const size_t walk = walk_smem_bytes<float>(threads);
     if (bin >= BIN_CTA0 && bin < BIN_GLOBAL) {
         g.slots = global_sym_slots(cta_bin_opmax(bin - BIN_CTA0), m);
         g.smem = walk + (size_t)g.slots * 4;
