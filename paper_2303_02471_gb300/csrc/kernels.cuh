@@ -86,41 +86,63 @@ __device__ __forceinline__ void group_products(unsigned mask, const int64_t *__r
 constexpr int kWalkBatch = 4;
 
 // ------------------------------------------------------------- CTA walk
-__device__ __forceinline__ int64_t cta_incl_scan_i64(int64_t v, int64_t *s_warp, int64_t &total) {
+// Inclusive block scan of (v, c) pairs; totals returned.  Two barriers.
+__device__ __forceinline__ void cta_incl_scan_pair(int64_t &v, int &c, int64_t *s_warp, int *s_warpc,
+                                                   int64_t &total, int &ctotal) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int64_t o = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += o;
+        const int oc = __shfl_up_sync(0xffffffffu, c, d);
+        if (lane >= d) {
+            v += o;
+            c += oc;
+        }
     }
-    if (lane == 31) s_warp[warp] = v;
+    if (lane == 31) {
+        s_warp[warp] = v;
+        s_warpc[warp] = c;
+    }
     __syncthreads();
     if (warp == 0) {
         int64_t x = lane < nw ? s_warp[lane] : 0;
+        int xc = lane < nw ? s_warpc[lane] : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int64_t o = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += o;
+            const int oc = __shfl_up_sync(0xffffffffu, xc, d);
+            if (lane >= d) {
+                x += o;
+                xc += oc;
+            }
         }
-        if (lane < nw) s_warp[lane] = x;
+        if (lane < nw) {
+            s_warp[lane] = x;
+            s_warpc[lane] = xc;
+        }
     }
     __syncthreads();
     total = s_warp[nw - 1];
-    return v + (warp > 0 ? s_warp[warp - 1] : 0);
+    ctotal = s_warpc[nw - 1];
+    if (warp > 0) {
+        v += s_warp[warp - 1];
+        c += s_warpc[warp - 1];
+    }
 }
 
-// Shared scratch of the CTA walk: one B entry per thread of a chunk.
+// Shared scratch of the CTA walk: the non-empty B entries of a chunk.
 template <typename VT>
 struct WalkSmem {
     int64_t *excl;  // [blockDim] products before this entry in the chunk
     int64_t *a0;    // [blockDim] start of A column k
     VT *bv;         // [blockDim] B_kj
     int64_t *warp;  // [32]
+    int *warpc;     // [32]
 };
 
 template <typename VT>
 __host__ __device__ inline size_t walk_smem_bytes(int threads) {
-    return (size_t)threads * (16 + sizeof(VT)) + 32 * 8 + 16;
+    return (size_t)threads * (16 + sizeof(VT)) + 32 * 12 + 32;
 }
 
 template <typename VT>
@@ -129,20 +151,25 @@ __device__ __forceinline__ WalkSmem<VT> carve_walk(unsigned char *&p) {
     w.excl = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
     w.a0 = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
     w.warp = reinterpret_cast<int64_t *>(p); p += 32 * 8;
+    w.warpc = reinterpret_cast<int *>(p); p += 32 * 4;
     w.bv = reinterpret_cast<VT *>(p); p += (size_t)blockDim.x * sizeof(VT);
     p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     return w;
 }
 
 // The whole CTA walks the products of B entries [p0, p1).  Per chunk of
-// blockDim entries: one block scan of Z^A_k, then the chunk's products are
-// cut into windows of 32 (one product per lane, consecutive lanes on
-// consecutive entries of an A column: coalesced) and every warp takes an
-// equal contiguous share of the windows, so the work is balanced over
-// products, not over B entries.  A lane finds the B entry of its product by
-// binary search over the chunk's prefix sums in shared memory; kWalkBatch
-// windows are searched and gathered before any product is consumed.
-// f(row, product) per product.  Contains barriers: every thread calls it.
+// blockDim entries, one block scan gives every non-empty entry (Z^A_k > 0)
+// its compacted slot and the number of products before it.  The chunk's
+// products are cut into windows of 32 (one per lane; consecutive lanes on
+// consecutive entries of an A column, so gathers coalesce) and every warp
+// takes an equal contiguous share of the windows: the work is balanced over
+// products, not B entries.  Owners need no per-lane search: with s the entry
+// holding the window's first product, entries s+1..s+32 are loaded one per
+// lane, the offsets of those that start inside the window are OR-reduced
+// into a bit mask, and lane l's owner is s + popc(mask & bits 1..l); the
+// mask also gives s for the next window.  kWalkBatch windows are gathered
+// before any product is consumed.  f(row, product) per product.  Contains
+// barriers: every thread must call it.
 template <bool VALS, typename VT, typename F>
 __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const int32_t *__restrict__ Arow,
                                          const VT *__restrict__ Aval, const int32_t *__restrict__ Brow,
@@ -150,6 +177,7 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                                          const WalkSmem<VT> &w, F &&f) {
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
     for (int64_t base = p0; base < p1; base += T) {
         const int64_t p = base + threadIdx.x;
         int64_t z = 0, a0 = 0;
@@ -160,45 +188,57 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
             z = Acp[k + 1] - a0;
             if (VALS) bv = Bval[p];
         }
-        int64_t total;
-        const int64_t incl = cta_incl_scan_i64(z, w.warp, total);
-        w.excl[threadIdx.x] = incl - z;
-        w.a0[threadIdx.x] = a0;
-        if (VALS) w.bv[threadIdx.x] = bv;
+        int64_t incl = z, total;
+        int cnt = z > 0 ? 1 : 0, nz;
+        cta_incl_scan_pair(incl, cnt, w.warp, w.warpc, total, nz);
+        if (z > 0) {
+            w.excl[cnt - 1] = incl - z;
+            w.a0[cnt - 1] = a0;
+            if (VALS) w.bv[cnt - 1] = bv;
+        }
         __syncthreads();
-        const int nvalid = (int)((p1 - base) < T ? (p1 - base) : T);
         const int64_t nwin = (total + 31) >> 5;
         const int64_t win0 = nwin * warp / nw, win1 = nwin * (warp + 1) / nw;
-        int lo = 0;
-        for (int64_t win = win0; win < win1; win += kWalkBatch) {
-            int32_t rows[kWalkBatch];
-            VT av[kWalkBatch], bvs[kWalkBatch];
-            const int start = lo;
+        if (win0 < win1) {
+            // entry holding product 32 * win0: largest s with excl[s] <= q
+            const int64_t qs = win0 << 5;
+            int s = 0, hi = nz - 1;
+            while (s < hi) {
+                const int mid = (s + hi + 1) >> 1;
+                if (w.excl[mid] <= qs) s = mid; else hi = mid - 1;
+            }
+            for (int64_t win = win0; win < win1; win += kWalkBatch) {
+                int32_t rows[kWalkBatch];
+                VT av[kWalkBatch], bvs[kWalkBatch];
 #pragma unroll
-            for (int u = 0; u < kWalkBatch; ++u) {
-                rows[u] = -1;
-                const int64_t q = ((win + u) << 5) + lane;
-                if (win + u < win1 && q < total) {
-                    int l = start, hi = nvalid - 1;
-                    while (l < hi) {
-                        const int mid = (l + hi + 1) >> 1;
-                        if (w.excl[mid] <= q) l = mid; else hi = mid - 1;
-                    }
-                    lo = l;
-                    const int64_t qa = w.a0[l] + (q - w.excl[l]);
-                    rows[u] = Arow[qa];
-                    if (VALS) {
-                        av[u] = Aval[qa];
-                        bvs[u] = w.bv[l];
+                for (int u = 0; u < kWalkBatch; ++u) {
+                    rows[u] = -1;
+                    if (win + u < win1) {  // uniform over the warp
+                        const int64_t qf = (win + u) << 5;
+                        const int cand = s + 1 + lane;
+                        const int64_t pos = cand < nz ? w.excl[cand] - qf : 64;
+                        const unsigned bits =
+                            __reduce_or_sync(0xffffffffu, pos < 32 ? (1u << (int)pos) : 0u);
+                        const int own = s + __popc(bits & upto);
+                        const int64_t q = qf + lane;
+                        if (q < total) {
+                            const int64_t qa = w.a0[own] + (q - w.excl[own]);
+                            rows[u] = Arow[qa];
+                            if (VALS) {
+                                av[u] = Aval[qa];
+                                bvs[u] = w.bv[own];
+                            }
+                        }
+                        s += __popc(bits) + (__ballot_sync(0xffffffffu, pos == 32) ? 1 : 0);
                     }
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < kWalkBatch; ++u) {
-                if (rows[u] >= 0) {
-                    VT prod = VT(0);
-                    if (VALS) prod = av[u] * bvs[u];
-                    f(rows[u], prod);
+                for (int u = 0; u < kWalkBatch; ++u) {
+                    if (rows[u] >= 0) {
+                        VT prod = VT(0);
+                        if (VALS) prod = av[u] * bvs[u];
+                        f(rows[u], prod);
+                    }
                 }
             }
         }
