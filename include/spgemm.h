@@ -135,7 +135,8 @@ spg_status spgemm_workspace_size(const spg_csc *A, const spg_csc *B,
  * Synchronises `stream` (it reads the bin histogram and nnz(C) back to the
  * host).  Errors: SPG_ERR_INVALID (shapes, dtypes, NULL pointers, or a
  * malformed input when cfg->validate), SPG_ERR_WORKSPACE, SPG_ERR_INDEX_OVERFLOW
- * (a dimension beyond int32 rows), SPG_ERR_TABLE_OVERFLOW, SPG_ERR_CUDA.
+ * (a dimension beyond int32 rows), SPG_ERR_UNSUPPORTED (a column with
+ * Op_j >= 2^31 products), SPG_ERR_TABLE_OVERFLOW, SPG_ERR_CUDA.
  */
 spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B,
                            const spg_config *cfg, void *workspace,

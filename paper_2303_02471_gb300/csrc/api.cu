@@ -271,6 +271,9 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     CK(cudaMemcpyAsync(&P->host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
+    // the walks index a column's products with 32-bit offsets
+    for (int b = 0; b < NBINS; ++b)
+        if (P->host.maxop[b] >= (1ULL << 31)) { delete P; return SPG_ERR_UNSUPPORTED; }
     P->off.v[0] = 0;
     for (int b = 0; b < NBINS; ++b) {
         // empty columns are not listed

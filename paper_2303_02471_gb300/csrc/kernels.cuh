@@ -86,90 +86,104 @@ __device__ __forceinline__ void group_products(unsigned mask, const int64_t *__r
 constexpr int kWalkBatch = 4;
 
 // ------------------------------------------------------------- CTA walk
-// Inclusive block scan of (v, c) pairs; totals returned.  Two barriers.
-__device__ __forceinline__ void cta_incl_scan_pair(int64_t &v, int &c, int64_t *s_warp, int *s_warpc,
-                                                   int64_t &total, int &ctotal) {
+// Entries whose A column has at least this many entries are walked one
+// 32-product window at a time with a single owner per window.
+constexpr int kLongEntry = 32;
+
+// Inclusive block scan of four int32 counters packed as two int64 lanes
+// (each half < 2^31); totals returned.  Two barriers.
+__device__ __forceinline__ void cta_incl_scan4(int (&v)[4], int64_t *s_warp, int (&tot)[4]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t x = (int64_t)v[0] | ((int64_t)v[1] << 32);
+    int64_t y = (int64_t)v[2] | ((int64_t)v[3] << 32);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const int64_t o = __shfl_up_sync(0xffffffffu, v, d);
-        const int oc = __shfl_up_sync(0xffffffffu, c, d);
+        const int64_t ox = __shfl_up_sync(0xffffffffu, x, d);
+        const int64_t oy = __shfl_up_sync(0xffffffffu, y, d);
         if (lane >= d) {
-            v += o;
-            c += oc;
+            x += ox;
+            y += oy;
         }
     }
     if (lane == 31) {
-        s_warp[warp] = v;
-        s_warpc[warp] = c;
+        s_warp[warp] = x;
+        s_warp[32 + warp] = y;
     }
     __syncthreads();
     if (warp == 0) {
-        int64_t x = lane < nw ? s_warp[lane] : 0;
-        int xc = lane < nw ? s_warpc[lane] : 0;
+        int64_t a = lane < nw ? s_warp[lane] : 0, b = lane < nw ? s_warp[32 + lane] : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int64_t o = __shfl_up_sync(0xffffffffu, x, d);
-            const int oc = __shfl_up_sync(0xffffffffu, xc, d);
+            const int64_t oa = __shfl_up_sync(0xffffffffu, a, d);
+            const int64_t ob = __shfl_up_sync(0xffffffffu, b, d);
             if (lane >= d) {
-                x += o;
-                xc += oc;
+                a += oa;
+                b += ob;
             }
         }
         if (lane < nw) {
-            s_warp[lane] = x;
-            s_warpc[lane] = xc;
+            s_warp[lane] = a;
+            s_warp[32 + lane] = b;
         }
     }
     __syncthreads();
-    total = s_warp[nw - 1];
-    ctotal = s_warpc[nw - 1];
+    const int64_t tx = s_warp[nw - 1], ty = s_warp[32 + nw - 1];
     if (warp > 0) {
-        v += s_warp[warp - 1];
-        c += s_warpc[warp - 1];
+        x += s_warp[warp - 1];
+        y += s_warp[32 + warp - 1];
     }
+    v[0] = (int)(x & 0xffffffff); v[1] = (int)(x >> 32);
+    v[2] = (int)(y & 0xffffffff); v[3] = (int)(y >> 32);
+    tot[0] = (int)(tx & 0xffffffff); tot[1] = (int)(tx >> 32);
+    tot[2] = (int)(ty & 0xffffffff); tot[3] = (int)(ty >> 32);
 }
 
-// Shared scratch of the CTA walk: the non-empty B entries of a chunk.
+// Shared scratch of the CTA walk: the non-empty B entries of a chunk, long
+// entries first, then short ones.
 template <typename VT>
 struct WalkSmem {
-    int64_t *excl;  // [blockDim] products before this entry in the chunk
+    int *key;       // [blockDim] long: windows before it; short: products before it
+    int *z;         // [blockDim] Z^A_k
     int64_t *a0;    // [blockDim] start of A column k
     VT *bv;         // [blockDim] B_kj
-    int64_t *warp;  // [32]
-    int *warpc;     // [32]
+    int64_t *warp;  // [64]
 };
 
 template <typename VT>
 __host__ __device__ inline size_t walk_smem_bytes(int threads) {
-    return (size_t)threads * (16 + sizeof(VT)) + 32 * 12 + 32;
+    return (size_t)threads * (16 + sizeof(VT)) + 64 * 8 + 32;
 }
 
 template <typename VT>
 __device__ __forceinline__ WalkSmem<VT> carve_walk(unsigned char *&p) {
     WalkSmem<VT> w;
-    w.excl = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
     w.a0 = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
-    w.warp = reinterpret_cast<int64_t *>(p); p += 32 * 8;
-    w.warpc = reinterpret_cast<int *>(p); p += 32 * 4;
+    w.warp = reinterpret_cast<int64_t *>(p); p += 64 * 8;
+    w.key = reinterpret_cast<int *>(p); p += (size_t)blockDim.x * 4;
+    w.z = reinterpret_cast<int *>(p); p += (size_t)blockDim.x * 4;
+    p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     w.bv = reinterpret_cast<VT *>(p); p += (size_t)blockDim.x * sizeof(VT);
     p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     return w;
 }
 
-// The whole CTA walks the products of B entries [p0, p1).  Per chunk of
-// blockDim entries, one block scan gives every non-empty entry (Z^A_k > 0)
-// its compacted slot and the number of products before it.  The chunk's
-// products are cut into windows of 32 (one per lane; consecutive lanes on
-// consecutive entries of an A column, so gathers coalesce) and every warp
-// takes an equal contiguous share of the windows: the work is balanced over
-// products, not B entries.  Owners need no per-lane search: with s the entry
-// holding the window's first product, entries s+1..s+32 are loaded one per
-// lane, the offsets of those that start inside the window are OR-reduced
-// into a bit mask, and lane l's owner is s + popc(mask & bits 1..l); the
-// mask also gives s for the next window.  kWalkBatch windows are gathered
-// before any product is consumed.  f(row, product) per product.  Contains
-// barriers: every thread must call it.
+// The whole CTA walks the products of B entries [p0, p1) of one column
+// (whose Op_j must be below 2^31).  Per chunk of blockDim entries, one block
+// scan sorts the non-empty entries into long ones (Z^A_k >= kLongEntry) and
+// short ones.  The work is cut into windows of 32 products, one per lane,
+// with consecutive lanes on consecutive entries of an A column (coalesced):
+//   * a long entry contributes ceil(Z^A_k / 32) windows of its own; the
+//     window's owner is the same for all lanes and advances with a uniform
+//     shared-memory scan;
+//   * short entries are concatenated into windows that can span several
+//     entries; with s the entry of the window's first product, entries
+//     s+1..s+32 are loaded one per lane, the offsets of those that start in
+//     the window are OR-reduced into a mask and lane l's owner is
+//     s + popc(mask & bits 1..l).
+// Every warp takes an equal contiguous share of the chunk's windows (balanced
+// over products, not B entries); kWalkBatch windows are gathered before any
+// product is consumed.  f(row, product) per product.  Contains barriers:
+// every thread of the CTA must call it.
 template <bool VALS, typename VT, typename F>
 __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const int32_t *__restrict__ Arow,
                                          const VT *__restrict__ Aval, const int32_t *__restrict__ Brow,
@@ -180,56 +194,68 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
     const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
     for (int64_t base = p0; base < p1; base += T) {
         const int64_t p = base + threadIdx.x;
-        int64_t z = 0, a0 = 0;
+        int z = 0;
+        int64_t a0 = 0;
         VT bv = VT(0);
         if (p < p1) {
             const int32_t k = Brow[p];
             a0 = Acp[k];
-            z = Acp[k + 1] - a0;
+            z = (int)(Acp[k + 1] - a0);
             if (VALS) bv = Bval[p];
         }
-        int64_t incl = z, total;
-        int cnt = z > 0 ? 1 : 0, nz;
-        cta_incl_scan_pair(incl, cnt, w.warp, w.warpc, total, nz);
-        if (z > 0) {
-            w.excl[cnt - 1] = incl - z;
-            w.a0[cnt - 1] = a0;
-            if (VALS) w.bv[cnt - 1] = bv;
+        const bool lng = z >= kLongEntry;
+        // counters: long windows, long entries, short products, short entries
+        int v[4] = {lng ? (z + 31) >> 5 : 0, lng ? 1 : 0, lng ? 0 : z, (!lng && z > 0) ? 1 : 0};
+        const int mine[4] = {v[0], v[1], v[2], v[3]};
+        int tot[4];
+        cta_incl_scan4(v, w.warp, tot);
+        const int nl = tot[1];
+        if (lng) {
+            const int i = v[1] - 1;
+            w.key[i] = v[0] - mine[0];
+            w.z[i] = z;
+            w.a0[i] = a0;
+            if (VALS) w.bv[i] = bv;
+        } else if (z > 0) {
+            const int i = nl + v[3] - 1;
+            w.key[i] = v[2] - mine[2];
+            w.z[i] = z;
+            w.a0[i] = a0;
+            if (VALS) w.bv[i] = bv;
         }
         __syncthreads();
-        const int64_t nwin = (total + 31) >> 5;
-        const int64_t win0 = nwin * warp / nw, win1 = nwin * (warp + 1) / nw;
-        if (win0 < win1) {
-            // entry holding product 32 * win0: largest s with excl[s] <= q
-            const int64_t qs = win0 << 5;
-            int s = 0, hi = nz - 1;
-            while (s < hi) {
-                const int mid = (s + hi + 1) >> 1;
-                if (w.excl[mid] <= qs) s = mid; else hi = mid - 1;
+        const int WL = tot[0], nsh = tot[3], ZS = tot[2];
+        const int WS = (ZS + 31) >> 5;
+        const int64_t nwin = (int64_t)WL + WS;
+        const int win0 = (int)(nwin * warp / nw), win1 = (int)(nwin * (warp + 1) / nw);
+        // ---- long entries: windows [win0, min(win1, WL))
+        {
+            const int e1 = win1 < WL ? win1 : WL;
+            int li = 0;
+            if (win0 < e1) {
+                int hi = nl - 1;
+                while (li < hi) {
+                    const int mid = (li + hi + 1) >> 1;
+                    if (w.key[mid] <= win0) li = mid; else hi = mid - 1;
+                }
             }
-            for (int64_t win = win0; win < win1; win += kWalkBatch) {
+            for (int win = win0; win < e1; win += kWalkBatch) {
                 int32_t rows[kWalkBatch];
                 VT av[kWalkBatch], bvs[kWalkBatch];
 #pragma unroll
                 for (int u = 0; u < kWalkBatch; ++u) {
                     rows[u] = -1;
-                    if (win + u < win1) {  // uniform over the warp
-                        const int64_t qf = (win + u) << 5;
-                        const int cand = s + 1 + lane;
-                        const int64_t pos = cand < nz ? w.excl[cand] - qf : 64;
-                        const unsigned bits =
-                            __reduce_or_sync(0xffffffffu, pos < 32 ? (1u << (int)pos) : 0u);
-                        const int own = s + __popc(bits & upto);
-                        const int64_t q = qf + lane;
-                        if (q < total) {
-                            const int64_t qa = w.a0[own] + (q - w.excl[own]);
+                    if (win + u < e1) {
+                        while (li + 1 < nl && w.key[li + 1] <= win + u) ++li;
+                        const int idx = ((win + u - w.key[li]) << 5) + lane;
+                        if (idx < w.z[li]) {
+                            const int64_t qa = w.a0[li] + idx;
                             rows[u] = Arow[qa];
                             if (VALS) {
                                 av[u] = Aval[qa];
-                                bvs[u] = w.bv[own];
+                                bvs[u] = w.bv[li];
                             }
                         }
-                        s += __popc(bits) + (__ballot_sync(0xffffffffu, pos == 32) ? 1 : 0);
                     }
                 }
 #pragma unroll
@@ -238,6 +264,54 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                         VT prod = VT(0);
                         if (VALS) prod = av[u] * bvs[u];
                         f(rows[u], prod);
+                    }
+                }
+            }
+        }
+        // ---- short entries: windows [max(win0, WL), win1) of the concatenation
+        {
+            const int s0w = (win0 > WL ? win0 : WL) - WL, s1w = win1 - WL;
+            if (s0w < s1w) {
+                const int *sk = w.key + nl;
+                const int64_t *sa = w.a0 + nl;
+                const VT *sb = w.bv + nl;
+                const int qs = s0w << 5;
+                int s = 0, hi = nsh - 1;
+                while (s < hi) {
+                    const int mid = (s + hi + 1) >> 1;
+                    if (sk[mid] <= qs) s = mid; else hi = mid - 1;
+                }
+                for (int win = s0w; win < s1w; win += kWalkBatch) {
+                    int32_t rows[kWalkBatch];
+                    VT av[kWalkBatch], bvs[kWalkBatch];
+#pragma unroll
+                    for (int u = 0; u < kWalkBatch; ++u) {
+                        rows[u] = -1;
+                        if (win + u < s1w) {  // uniform over the warp
+                            const int qf = (win + u) << 5;
+                            const int cand = s + 1 + lane;
+                            const int pos = cand < nsh ? sk[cand] - qf : 64;
+                            const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? (1u << pos) : 0u);
+                            const int own = s + __popc(bits & upto);
+                            const int q = qf + lane;
+                            if (q < ZS) {
+                                const int64_t qa = sa[own] + (q - sk[own]);
+                                rows[u] = Arow[qa];
+                                if (VALS) {
+                                    av[u] = Aval[qa];
+                                    bvs[u] = sb[own];
+                                }
+                            }
+                            s += __popc(bits) + (__ballot_sync(0xffffffffu, pos == 32) ? 1 : 0);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kWalkBatch; ++u) {
+                        if (rows[u] >= 0) {
+                            VT prod = VT(0);
+                            if (VALS) prod = av[u] * bvs[u];
+                            f(rows[u], prod);
+                        }
                     }
                 }
             }
