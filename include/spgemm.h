@@ -94,6 +94,11 @@ typedef struct {
     /* Cap on the bytes of per-CTA global scratch (global hash tables and
      * bitmaps); the number of CTAs that use such scratch shrinks to fit. */
     int64_t scratch_cap_bytes;
+    /* Bytes of workspace that keep the SPA flag bitmaps (m bits per column)
+     * the symbolic phase builds for dense-SPA columns, so that the numeric
+     * phase reuses them instead of walking the column's products twice.
+     * Columns beyond the budget rebuild their flags.  0 disables. */
+    int64_t dense_cache_bytes;
 } spg_config;
 
 typedef struct spg_plan spg_plan;

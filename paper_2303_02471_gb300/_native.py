@@ -29,7 +29,7 @@ class SpgCsc(ctypes.Structure):
 
 class SpgConfig(ctypes.Structure):
     _fields_ = [("t", i64), ("hash_cta_max", i32), ("cta_threads", i32), ("validate", i32),
-                ("table_shrink", i32), ("scratch_cap_bytes", i64)]
+                ("table_shrink", i32), ("scratch_cap_bytes", i64), ("dense_cache_bytes", i64)]
 
 
 class SpgError(RuntimeError):

@@ -37,9 +37,10 @@ DeviceInfo device_info(int dev) {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t ctrl = 0, op = 0, cols = 0, tiles = 0, scratch = 0, total = 0;
+    size_t ctrl = 0, op = 0, cols = 0, tiles = 0, scratch = 0, cache = 0, total = 0;
     size_t scratch_stride = 0;
     int64_t scratch_ctas = 0;
+    int64_t cache_cols = 0;
 };
 
 spg_config normalized(const spg_config *cfg) {
@@ -85,6 +86,12 @@ Layout make_layout(int64_t m, int64_t nB, int64_t nnzA, int dtype, const spg_con
     L.scratch_ctas = ctas;
     L.scratch = off;
     off = align256(off + (size_t)ctas * L.scratch_stride);
+    // SPA flag bitmaps of dense columns, kept from the symbolic phase
+    L.cache = off;
+    if (c.dense_cache_bytes > 0 && W > 0) {
+        L.cache_cols = std::min<int64_t>(nB, c.dense_cache_bytes / (W * 4));
+        off = align256(off + (size_t)L.cache_cols * (size_t)W * 4);
+    }
     L.total = off;
     return L;
 }
@@ -153,6 +160,8 @@ struct spg_plan {
         t.scratch = scratch();
         t.scratch_stride = L.scratch_stride;
         t.ctrl = ctrl();
+        t.flag_cache = b == BIN_DENSE ? reinterpret_cast<uint32_t *>(ws + L.cache) : nullptr;
+        t.cache_cols = b == BIN_DENSE ? L.cache_cols : 0;
         return t;
     }
 };
@@ -167,6 +176,7 @@ spg_status spg_config_default(spg_config *cfg) {
     cfg->validate = 1;
     cfg->table_shrink = 0;
     cfg->scratch_cap_bytes = (int64_t)1 << 30;
+    cfg->dense_cache_bytes = (int64_t)1 << 30;
     return SPG_OK;
 }
 
@@ -197,6 +207,7 @@ static spg_status check_config(const spg_config &c) {
     if (!valid_hash_max(c.hash_cta_max)) return SPG_ERR_INVALID;
     if (c.cta_threads < 128 || c.cta_threads > 1024 || c.cta_threads % 32) return SPG_ERR_INVALID;
     if (c.table_shrink < 0 || c.table_shrink > 30) return SPG_ERR_INVALID;
+    if (c.dense_cache_bytes < 0 || c.scratch_cap_bytes < 0) return SPG_ERR_INVALID;
     return SPG_OK;
 }
 

@@ -320,6 +320,23 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
     }
 }
 
+// ------------------------------------------------------ bit selection
+// Position of the k-th (0-based) set bit of b, for k < popc(b): a binary
+// search over the halves of the word by their population counts.
+__device__ __forceinline__ int select_bit(uint32_t b, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int width = 16; width > 0; width >>= 1) {
+        const int c = __popc(b & ((1u << width) - 1u));
+        if (k >= c) {
+            k -= c;
+            b >>= width;
+            pos += width;
+        }
+    }
+    return pos;
+}
+
 // ------------------------------------------------- two-level row bitmap
 // For extracting a hash table's rows in ascending order in O(m / 1024 + n)
 // per column: L0 has one bit per row, L1 one bit per non-zero L0 word.
@@ -423,10 +440,7 @@ __device__ __forceinline__ void cta_expand_words(uint32_t *L0, const int32_t *wl
             uint32_t b = __shfl_sync(0xffffffffu, v, s);
             const int kk = o - __shfl_sync(0xffffffffu, excl, s);
             const int32_t ws = __shfl_sync(0xffffffffu, word, s);
-            if (o < S) {
-                for (int t = 0; t < kk; ++t) b &= b - 1u;
-                f(ws * 32 + (__ffs(b) - 1), off + o);
-            }
+            if (o < S) f(ws * 32 + select_bit(b, kk), off + o);
         }
         off += S;
     }
@@ -515,11 +529,7 @@ __device__ __forceinline__ void cta_bitmap_expand(uint2 *bm, int64_t W, bool cle
             unsigned b = __shfl_sync(0xffffffffu, v.x, s);
             const int k = o - __shfl_sync(0xffffffffu, excl, s);
             const unsigned ys = __shfl_sync(0xffffffffu, v.y, s);
-            if (o < S) {
-                for (int i = 0; i < k; ++i) b &= b - 1u;
-                const int bit = __ffs(b) - 1;
-                f((int32_t)((c * 32 + s) * 32 + bit), (int64_t)ys + k);
-            }
+            if (o < S) f((int32_t)((c * 32 + s) * 32 + select_bit(b, k)), (int64_t)ys + k);
         }
     }
 }
@@ -557,6 +567,8 @@ struct BinTask {
     unsigned char *scratch;  // per-CTA global scratch (base)
     size_t scratch_stride;   // bytes per CTA
     Ctrl *ctrl;
+    uint32_t *flag_cache;    // dense bin: W words per listed column, for the
+    int64_t cache_cols;      //   first cache_cols columns of the bin's list
 };
 
 struct Operands {

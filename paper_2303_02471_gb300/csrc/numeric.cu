@@ -247,9 +247,16 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
         const int32_t j = t.cols[ci];
         const int64_t c0 = Ccp[j];
         const int64_t nn = Ccp[j + 1] - c0;
-        // walk 1: SPA flags
-        cta_walk<false, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                             [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
+        if (ci < t.cache_cols) {
+            // SPA flags kept by the symbolic phase
+            const uint32_t *keep = t.flag_cache + (size_t)ci * t.W;
+            for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i].x = keep[i];
+            __syncthreads();
+        } else {
+            // walk 1: SPA flags
+            cta_walk<false, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                                [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
+        }
         const int64_t total = cta_bitmap_prefix(bm, t.W, s_warp);
         const bool ok = total == nn;
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);

@@ -138,7 +138,12 @@ __global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64
                                     const uint32_t bit = 1u << (row & 31);
                                     cnt += (atomicOr(&bm[row >> 5], bit) & bit) ? 0 : 1;
                                 });
-        for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = 0u;
+        // keep the flags for the numeric phase when the column has a cache slot
+        uint32_t *keep = ci < t.cache_cols ? t.flag_cache + (size_t)ci * t.W : nullptr;
+        for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) {
+            if (keep) keep[i] = bm[i];
+            bm[i] = 0u;
+        }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
         if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);

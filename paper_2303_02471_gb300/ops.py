@@ -81,11 +81,13 @@ class Config:
     validate: Optional[bool] = None
     table_shrink: Optional[int] = None
     scratch_cap_bytes: Optional[int] = None
+    dense_cache_bytes: Optional[int] = None
 
     def native(self) -> N.SpgConfig:
         c = N.SpgConfig()
         N.check(N.lib().spg_config_default(ctypes.byref(c)), "spg_config_default")
-        for f in ("t", "hash_cta_max", "cta_threads", "table_shrink", "scratch_cap_bytes"):
+        for f in ("t", "hash_cta_max", "cta_threads", "table_shrink", "scratch_cap_bytes",
+                  "dense_cache_bytes"):
             v = getattr(self, f)
             if v is not None:
                 setattr(c, f, int(v))

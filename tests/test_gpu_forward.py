@@ -74,6 +74,16 @@ def test_rmat_every_bin(t, hmax):
     assert info["products"] == int(oracle.op_counts(A, A).sum())
 
 
+@pytest.mark.parametrize("cache", [0, 3 * 4 * 256, None])
+def test_dense_flag_cache_budgets(cache):
+    """Dense columns with and without flags kept from the symbolic phase
+    (no cache, a cache for only the first few columns, the default)."""
+    A = synth.rmat(13, seed=4, col_cap=600)
+    C, plan = _run(A, A, t=0, dense_cache_bytes=cache)
+    assert plan.info()["bins"][13] > 3
+    assert_matches_oracle(C, A, A, nthreads=NCPU)
+
+
 def test_op_counts_and_bins():
     A = synth.rmat(12, seed=5, col_cap=300)
     B = synth.random_z(A.ncols, 0, 12, seed=6)
