@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU seconds of the oracle sample")
+    p.add_argument("--t", type=int, default=None,
+                   help="H-HASH(t) threshold (default: the library's)")
+    p.add_argument("--dense-cache", type=int, default=None,
+                   help="bytes of workspace for dense-column SPA flags kept between phases")
     p.add_argument("--rmat-scale", type=int, default=18,
                    help="log2 size of the R-MAT workload (smaller for profiler captures)")
     return p.parse_args()
@@ -214,7 +218,7 @@ def run_ours(args, rank, world):
     w = 8
     A = ops.CscMatrix.from_host(A_h, device=dev)
     B = A if B_h is A_h else ops.CscMatrix.from_host(B_h, device=dev)
-    cfg = ops.Config()
+    cfg = ops.Config(t=args.t, dense_cache_bytes=args.dense_cache)
     ncfg = cfg.native()
     lib = N.lib()
     stream = torch.cuda.current_stream()
@@ -318,7 +322,7 @@ def run_ours(args, rank, world):
     # end to end through host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, A_h, B_h, products, lib, ncfg, dev, stream, world)
+        e2e = run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world)
 
     line = None
     if rank == 0:
@@ -329,7 +333,7 @@ def run_ours(args, rank, world):
                 "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name(args), "products": int(products),
+                "config": {"workload": workload_name(args), "t": info["t"], "products": int(products),
                            "nnz_C": int(nnz), "l2": "512 MiB buffer written between timed steps",
                            "parallelism": f"replicas x{world}"},
                 "phases_ms": {"symbolic": round(float(np.mean([a.elapsed_time(b) for a, b, c in ev])), 4),
@@ -340,7 +344,7 @@ def run_ours(args, rank, world):
     return line
 
 
-def run_e2e(args, A_h, B_h, products, lib, ncfg, dev, stream, world):
+def run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world):
     """Same metric with host inputs and outputs: pinned host CSC in, H2D copy,
     both phases, D2H copy of C, every step."""
     import torch
@@ -357,7 +361,7 @@ def run_e2e(args, A_h, B_h, products, lib, ncfg, dev, stream, world):
     A = ops.CscMatrix(A_h.nrows, A_h.ncols, *dA)
     B = ops.CscMatrix(B_h.nrows, B_h.ncols, *dB)
     cA, cB = ops._csc(A), ops._csc(B)
-    ws = torch.empty(ops.workspace_size(A, B), dtype=torch.uint8, device=dev)
+    ws = torch.empty(ops.workspace_size(A, B, cfg), dtype=torch.uint8, device=dev)
     colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=dev)
     sp = ctypes.c_void_p(stream.cuda_stream)
     h2d = sum(x.numel() * x.element_size() for x in hA) + (0 if same else sum(x.numel() * x.element_size() for x in hB))
