@@ -155,7 +155,7 @@ __host__ __device__ inline size_t walk_smem_bytes(int threads) {
 }
 
 template <typename VT>
-__device__ __forceinline__ WalkSmem<VT> carve_walk(unsigned char *&p) {
+__device__ __forceinline__ WalkSmem<VT> carve_walk(unsigned char *p) {
     WalkSmem<VT> w;
     w.a0 = reinterpret_cast<int64_t *>(p); p += (size_t)blockDim.x * 8;
     w.warp = reinterpret_cast<int64_t *>(p); p += 64 * 8;

@@ -124,43 +124,30 @@ __global__ void __launch_bounds__(kGroupThreads) k_num_group(BinTask t, Operands
 // ------------------------------------------------------- CTA hash bins
 __host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
 
-template <typename VT>
+// Placement of the table (TSM) and of the row bitmap (BSM) is a template
+// parameter: pointers derived straight from the shared-memory array let the
+// compiler use shared-space loads and atomics instead of generic ones.
+template <typename VT, bool TSM, bool BSM>
 __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
-                                                  VT *Cval, int64_t cap, int table_global, int bm_global) {
+                                                  VT *Cval, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ unsigned s_occ;
     __shared__ int64_t s_warp[32];
     const int64_t W1 = (t.W + 31) / 32;
-    unsigned char *sp = smem;
-    const WalkSmem<VT> w = carve_walk<VT>(sp);
+    const WalkSmem<VT> w = carve_walk<VT>(smem);
+    const size_t o_walk = walk_smem_bytes<VT>(blockDim.x);
+    const size_t tab = al16((size_t)cap * 4) + al16((size_t)cap * sizeof(VT)) + al16((size_t)cap * 4);
     unsigned char *gp = t.scratch + (size_t)blockIdx.x * t.scratch_stride;
-    int32_t *keys;
-    VT *vals;
     // the table and the word list scale with the table size: both live in
     // shared memory, or both in the CTA's global scratch
-    int32_t *wlist;
-    if (table_global) {
-        keys = reinterpret_cast<int32_t *>(gp);
-        vals = reinterpret_cast<VT *>(gp + al16((size_t)cap * 4));
-        gp += al16((size_t)cap * 4) + al16((size_t)cap * sizeof(VT));
-        wlist = reinterpret_cast<int32_t *>(gp);
-        gp += al16((size_t)cap * 4);
-    } else {
-        keys = reinterpret_cast<int32_t *>(sp);
-        vals = reinterpret_cast<VT *>(sp + al16((size_t)cap * 4));
-        sp += al16((size_t)cap * 4) + al16((size_t)cap * sizeof(VT));
-        wlist = reinterpret_cast<int32_t *>(sp);
-        sp += al16((size_t)cap * 4);
-    }
-    uint32_t *L0;
-    if (bm_global) {
-        L0 = reinterpret_cast<uint32_t *>(gp);
-    } else {
-        L0 = reinterpret_cast<uint32_t *>(sp);
-        sp += al16((size_t)t.W * 4);
-    }
-    uint32_t *L1 = reinterpret_cast<uint32_t *>(sp);
+    unsigned char *tb = TSM ? smem + o_walk : gp;
+    int32_t *keys = reinterpret_cast<int32_t *>(tb);
+    VT *vals = reinterpret_cast<VT *>(tb + al16((size_t)cap * 4));
+    int32_t *wlist = reinterpret_cast<int32_t *>(tb + al16((size_t)cap * 4) + al16((size_t)cap * sizeof(VT)));
+    const size_t o_l0 = o_walk + (TSM ? tab : 0);
+    uint32_t *L0 = BSM ? reinterpret_cast<uint32_t *>(smem + o_l0) : reinterpret_cast<uint32_t *>(gp + (TSM ? 0 : tab));
+    uint32_t *L1 = reinterpret_cast<uint32_t *>(smem + o_l0 + (BSM ? al16((size_t)t.W * 4) : 0));
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) L0[i] = 0u;
     for (int64_t i = threadIdx.x; i < W1; i += blockDim.x) L1[i] = 0u;
     const VT *Aval = static_cast<const VT *>(o.Aval);
@@ -220,22 +207,17 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
 }
 
 // ------------------------------------------------------------ dense bin
-template <typename VT>
+template <typename VT, bool BSM>
 __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
-                                                    VT *Cval, int64_t cap, int bm_global) {
+                                                    VT *Cval, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ int64_t s_warp[32];
-    unsigned char *p = smem;
-    const WalkSmem<VT> w = carve_walk<VT>(p);
-    uint2 *bm;
-    if (bm_global) {
-        bm = reinterpret_cast<uint2 *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
-    } else {
-        bm = reinterpret_cast<uint2 *>(p);
-        p += (size_t)t.W * 8;
-    }
-    VT *s_acc = reinterpret_cast<VT *>(p);
+    const WalkSmem<VT> w = carve_walk<VT>(smem);
+    const size_t o_walk = walk_smem_bytes<VT>(blockDim.x);
+    uint2 *bm = BSM ? reinterpret_cast<uint2 *>(smem + o_walk)
+                    : reinterpret_cast<uint2 *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
+    VT *s_acc = reinterpret_cast<VT *>(smem + o_walk + (BSM ? (size_t)t.W * 8 : 0));
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
     const VT *Aval = static_cast<const VT *>(o.Aval);
     const VT *Bval = static_cast<const VT *>(o.Bval);
@@ -261,16 +243,28 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
         const bool ok = total == nn;
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
         const bool in_smem = nn <= cap;
-        VT *acc = in_smem ? s_acc : Cval + c0;
-        if (ok)
-            for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) acc[i] = VT(0);
-        __syncthreads();
-        // walk 2: accumulate every product at its row's sorted position
-        cta_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                            [&](int32_t row, VT prod) {
-                                const int32_t r = bitmap_rank(bm, row);
-                                if (ok) atomicAdd(&acc[r], prod);
-                            });
+        // walk 2: accumulate every product at its row's sorted position, in
+        // shared memory when the column fits, else in place in C
+        if (in_smem) {
+            if (ok)
+                for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) s_acc[i] = VT(0);
+            __syncthreads();
+            cta_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                                [&](int32_t row, VT prod) {
+                                    const int32_t r = bitmap_rank(bm, row);
+                                    if (ok) atomicAdd(&s_acc[r], prod);
+                                });
+        } else {
+            VT *gacc = Cval + c0;
+            if (ok)
+                for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) gacc[i] = VT(0);
+            __syncthreads();
+            cta_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                                [&](int32_t row, VT prod) {
+                                    const int32_t r = bitmap_rank(bm, row);
+                                    if (ok) atomicAdd(&gacc[r], prod);
+                                });
+        }
         cta_bitmap_expand(bm, t.W, true, [&](int32_t row, int64_t rank) {
             if (ok) {
                 Crow[c0 + rank] = row;
@@ -319,7 +313,7 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
         g.bm_global = l0 > kBitmapSmemMax || fixed + (table_global ? 0 : tab) + l0 > smem_optin;
         g.cap = table_global ? 1 : 0;  // reused as "table in global" flag
         g.smem = fixed + (table_global ? 0 : tab) + (g.bm_global ? 0 : l0);
-        int occ = occupancy(k_num_cta<VT>, g.threads, g.smem);
+        int occ = occupancy(k_num_cta<VT, true, true>, g.threads, g.smem);
         int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
         if (table_global || g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);
         g.grid = (int)std::max<int64_t>(1, grid);
@@ -335,7 +329,7 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
     if (cap > maxnnz) cap = maxnnz;
     g.cap = cap;
     g.smem = base + (size_t)cap * sizeof(VT);
-    int occ = occupancy(k_num_dense<VT>, g.threads, g.smem);
+    int occ = occupancy(k_num_dense<VT, true>, g.threads, g.smem);
     int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
     if (g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);
     g.grid = (int)std::max<int64_t>(1, grid);
@@ -366,12 +360,15 @@ static cudaError_t launch_numeric_t(const BinTask &t, const Operands &o, const i
 #undef NUM_CASE
         }
     } else if (t.bin <= BIN_GLOBAL) {
-        allow_smem(k_num_cta<VT>, g.smem);
-        k_num_cta<VT><<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.slots, g.cap ? 1 : 0,
-                                                        g.bm_global ? 1 : 0);
+        const bool tsm = g.cap == 0, bsm = !g.bm_global;
+        auto k = tsm ? (bsm ? k_num_cta<VT, true, true> : k_num_cta<VT, true, false>)
+                     : (bsm ? k_num_cta<VT, false, true> : k_num_cta<VT, false, false>);
+        allow_smem(k, g.smem);
+        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.slots);
     } else {
-        allow_smem(k_num_dense<VT>, g.smem);
-        k_num_dense<VT><<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.cap, g.bm_global ? 1 : 0);
+        auto k = g.bm_global ? k_num_dense<VT, false> : k_num_dense<VT, true>;
+        allow_smem(k, g.smem);
+        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.cap);
     }
     return cudaGetLastError();
 }

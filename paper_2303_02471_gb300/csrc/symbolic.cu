@@ -58,15 +58,14 @@ __global__ void __launch_bounds__(kGroupThreads) k_sym_group(BinTask t, Operands
 // ------------------------------------------------------- CTA hash bins
 // One CTA per column (dynamic work counter); table of pow2 >= 2 Op_j keys in
 // shared memory, or in the CTA's global scratch for the global bin.
-__global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t *Ccp, int64_t cap_slots,
-                                                  int use_global) {
+template <bool KSM>
+__global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t *Ccp, int64_t cap_slots) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
-    unsigned char *p = smem;
-    const WalkSmem<float> w = carve_walk<float>(p);
-    int32_t *keys = use_global ? reinterpret_cast<int32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride)
-                               : reinterpret_cast<int32_t *>(p);
+    const WalkSmem<float> w = carve_walk<float>(smem);
+    int32_t *keys = KSM ? reinterpret_cast<int32_t *>(smem + walk_smem_bytes<float>(blockDim.x))
+                        : reinterpret_cast<int32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
     if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -112,14 +111,14 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
 // ------------------------------------------------------------ dense bin
 // SPA flags as a bitmap of m bits (shared memory, or global scratch when m
 // is large); nnz(C_j) is the number of set bits.
-__global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64_t *Ccp, int use_global) {
+template <bool BSM>
+__global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64_t *Ccp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
-    unsigned char *p = smem;
-    const WalkSmem<float> w = carve_walk<float>(p);
-    uint32_t *bm = use_global ? reinterpret_cast<uint32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride)
-                              : reinterpret_cast<uint32_t *>(p);
+    const WalkSmem<float> w = carve_walk<float>(smem);
+    uint32_t *bm = BSM ? reinterpret_cast<uint32_t *>(smem + walk_smem_bytes<float>(blockDim.x))
+                       : reinterpret_cast<uint32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = 0u;
     if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
@@ -196,18 +195,18 @@ Geo symbolic_geometry(int bin, int64_t count, int64_t m, int threads, int sms, s
     if (bin >= BIN_CTA0 && bin < BIN_GLOBAL) {
         g.slots = global_sym_slots(cta_bin_opmax(bin - BIN_CTA0), m);
         g.smem = walk + (size_t)g.slots * 4;
-        int occ = occupancy(k_sym_cta, threads, g.smem);
+        int occ = occupancy(k_sym_cta<true>, threads, g.smem);
         g.grid = (int)std::min<int64_t>(count, (int64_t)occ * sms);
     } else if (bin == BIN_GLOBAL) {
         g.slots = global_sym_slots(max_op, m);
         g.smem = walk;
-        int occ = occupancy(k_sym_cta, threads, g.smem);
+        int occ = occupancy(k_sym_cta<true>, threads, g.smem);
         g.grid = (int)std::min<int64_t>(std::min<int64_t>(count, (int64_t)occ * sms), scratch_ctas);
     } else {  // dense
         const size_t bmb = (size_t)W * 4;
         g.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
         g.smem = walk + (g.bm_global ? 0 : bmb);
-        int occ = occupancy(k_sym_dense, threads, g.smem);
+        int occ = occupancy(k_sym_dense<true>, threads, g.smem);
         int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
         if (g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);
         g.grid = (int)grid;
@@ -232,11 +231,13 @@ cudaError_t launch_symbolic_bin(const BinTask &t, const Operands &o, int64_t *Cc
 #undef SYM_CASE
         }
     } else if (t.bin < BIN_DENSE) {
-        allow_smem(k_sym_cta, g.smem);
-        k_sym_cta<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, g.slots, t.bin == BIN_GLOBAL ? 1 : 0);
+        auto k = t.bin == BIN_GLOBAL ? k_sym_cta<false> : k_sym_cta<true>;
+        allow_smem(k, g.smem);
+        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, g.slots);
     } else {
-        allow_smem(k_sym_dense, g.smem);
-        k_sym_dense<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, g.bm_global ? 1 : 0);
+        auto k = g.bm_global ? k_sym_dense<false> : k_sym_dense<true>;
+        allow_smem(k, g.smem);
+        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp);
     }
     return cudaGetLastError();
 }
