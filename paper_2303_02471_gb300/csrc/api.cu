@@ -50,7 +50,16 @@ spg_config normalized(const spg_config *cfg) {
     return c;
 }
 
-int64_t effective_t(const spg_config &c) { return c.t < 0 ? (int64_t)c.hash_cta_max + 1 : c.t; }
+// Default threshold: the dense SPA pays O(m / 32) words per column (flag
+// bitmap prefix and sorted extraction), so a column goes dense once its
+// product count reaches m / 128, within [257, hash_cta_max + 1].
+int64_t effective_t(const spg_config &c, int64_t m) {
+    if (c.t >= 0) return c.t;
+    int64_t t = (m + 127) / 128;
+    if (t > (int64_t)c.hash_cta_max + 1) t = (int64_t)c.hash_cta_max + 1;
+    if (t < 257) t = 257;
+    return t;
+}
 
 bool valid_hash_max(int32_t h) {
     return h == 256 || h == 512 || h == 1024 || h == 2048 || h == 4096 || h == 8192;
@@ -71,7 +80,7 @@ Layout make_layout(int64_t m, int64_t nB, int64_t nnzA, int dtype, const spg_con
     const int64_t reach = std::min<int64_t>(std::max<int64_t>(nnzA, 1), std::max<int64_t>(m, 1));
     // hash table keys + values + word list of the extraction (numeric)
     size_t tab = (size_t)num_slots(std::min<int64_t>(hmax, reach)) * (8 + w) + 64;
-    if (effective_t(c) > hmax + 1) {
+    if (effective_t(c, m) > hmax + 1) {
         const size_t sym = (size_t)global_sym_slots(reach, m) * 4;
         const size_t num = (size_t)num_slots(reach) * (8 + w) + 64;
         tab = std::max(tab, std::max(sym, num));
@@ -246,7 +255,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     P->nnzA = A->nnz; P->nnzB = B->nnz;
     P->dtype = A->dtype;
     P->cfg = c;
-    P->t_eff = effective_t(c);
+    P->t_eff = effective_t(c, A->nrows);
     P->L = make_layout(P->mA, P->nB, P->nnzA, P->dtype, c, P->dev.sms);
     if (ws_bytes < P->L.total) { delete P; return SPG_ERR_WORKSPACE; }
     P->ws = static_cast<unsigned char *>(workspace);
