@@ -245,10 +245,11 @@ spg_status spg_plan_op_counts(const spg_plan *plan, int64_t *op_out,
  * becomes column k.  Pure data movement; the Galerkin product P^T (A P) of
  * the differentiable workload needs P^T as a CSC operand.
  *
- * M            device CSC (values may be NULL: then T_values is not written).
+ * M            device CSC (values may be NULL: then T_values is not written);
+ *              rows outside [0, M->nrows) are dropped.
  * T_colptr     device int64[M->nrows + 1], written.
  * T_rowidx     device int32[M->nnz], written; rows inside each output column
- *              are in ascending order.
+ *              are in ascending order (deterministic).
  * T_values     device values[M->nnz] (M's dtype) or NULL.
  * perm         device int64[M->nnz] or NULL: T_values[e] = M.values[perm[e]].
  * workspace    device buffer of spg_transpose_workspace_size bytes.
@@ -259,6 +260,17 @@ spg_status spg_csc_transpose(const spg_csc *M, int64_t *T_colptr,
                              int32_t *T_rowidx, void *T_values, int64_t *perm,
                              void *workspace, size_t ws_bytes,
                              spg_stream stream);
+
+/*
+ * Permute a value array on the device: dst[i] = src[idx[i]] (scatter = 0) or
+ * dst[idx[i]] = src[i] (scatter = 1), i < n.  With the permutation of
+ * spg_csc_transpose this moves values (or their gradients) between M and
+ * M^T.  idx must be a permutation of [0, n) for scatter.  Asynchronous.
+ * Errors: SPG_ERR_INVALID, SPG_ERR_CUDA.
+ */
+spg_status spg_permute_values(const void *src, const int64_t *idx, void *dst,
+                              int64_t n, int32_t dtype, int32_t scatter,
+                              spg_stream stream);
 
 #ifdef __cplusplus
 }

@@ -58,6 +58,7 @@ SIGNATURES = {
     "spg_plan_bin_times": (i32, [vp, vp]),
     "spg_transpose_workspace_size": (i32, [vp, ctypes.POINTER(ctypes.c_size_t)]),
     "spg_csc_transpose": (i32, [vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+    "spg_permute_values": (i32, [vp, vp, vp, i64, i32, i32, vp]),
 }
 
 _lib = None

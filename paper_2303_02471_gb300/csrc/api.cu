@@ -134,6 +134,8 @@ struct spg_plan {
     int64_t nnzC = 0;
     Geo num_geo[NBINS];
     bool num_geo_ready = false;
+    Geo bwd_geo[NBINS];
+    bool bwd_geo_ready = false;
     bool timing = false;
     bool timed = false;
     cudaEvent_t ev0[NBINS] = {}, ev1[NBINS] = {};
@@ -367,8 +369,33 @@ spg_status spgemm_backward(spg_plan *P, const spg_csc *A, const spg_csc *B, cons
                            spg_stream stream) {
     spg_status st = check_plan_operands(P, A, B);
     if (st != SPG_OK) return st;
-    (void)C_colptr; (void)C_rowidx; (void)dC_values; (void)dA_values; (void)dB_values; (void)stream;
-    return SPG_ERR_UNSUPPORTED;
+    if (!C_colptr || (P->nnzC > 0 && (!C_rowidx || !dC_values))) return SPG_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t w = P->dtype == SPG_F64 ? 8 : 4;
+    if (dA_values && P->nnzA > 0 && cudaMemsetAsync(dA_values, 0, (size_t)P->nnzA * w, s) != cudaSuccess)
+        return SPG_ERR_CUDA;
+    if (dB_values && P->nnzB > 0 && cudaMemsetAsync(dB_values, 0, (size_t)P->nnzB * w, s) != cudaSuccess)
+        return SPG_ERR_CUDA;
+    if (!dA_values && !dB_values) return SPG_OK;
+    Ctrl *ctrl = P->ctrl();
+    if (cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s) != cudaSuccess) return SPG_ERR_CUDA;
+    if (!P->bwd_geo_ready) {
+        for (int b = 1; b < NBINS; ++b) {
+            if (!P->host.hist[b]) continue;
+            P->bwd_geo[b] = backward_geometry(b, (int64_t)P->host.hist[b], P->mA, P->cfg.cta_threads, P->dev.sms,
+                                              P->dev.smem_optin, (int64_t)P->host.maxnnz[b], P->dtype,
+                                              P->cfg.table_shrink, P->L.scratch_ctas);
+        }
+        P->bwd_geo_ready = true;
+    }
+    Operands o{A->colptr, A->rowidx, A->values, B->colptr, B->rowidx, B->values};
+    for (int b = 1; b < NBINS; ++b) {
+        if (!P->host.hist[b]) continue;
+        cudaError_t e = launch_backward_bin(P->task(b), o, C_colptr, C_rowidx, dC_values, dA_values, dB_values,
+                                            P->dtype, P->bwd_geo[b], s);
+        if (e != cudaSuccess) return SPG_ERR_CUDA;
+    }
+    return SPG_OK;
 }
 
 spg_status spg_plan_check(spg_plan *P, spg_stream stream) {
@@ -446,19 +473,6 @@ spg_status spg_plan_op_counts(const spg_plan *P, int64_t *op_out, spg_stream str
     if (P->nB == 0) return SPG_OK;
     return cuda_status(cudaMemcpyAsync(op_out, P->op(), (size_t)P->nB * 8, cudaMemcpyDeviceToDevice,
                                        reinterpret_cast<cudaStream_t>(stream)));
-}
-
-spg_status spg_transpose_workspace_size(const spg_csc *M, size_t *bytes) {
-    if (!M || !bytes) return SPG_ERR_INVALID;
-    (void)M;
-    return SPG_ERR_UNSUPPORTED;
-}
-
-spg_status spg_csc_transpose(const spg_csc *M, int64_t *T_colptr, int32_t *T_rowidx, void *T_values, int64_t *perm,
-                             void *workspace, size_t ws_bytes, spg_stream stream) {
-    (void)M; (void)T_colptr; (void)T_rowidx; (void)T_values; (void)perm; (void)workspace; (void)ws_bytes;
-    (void)stream;
-    return SPG_ERR_UNSUPPORTED;
 }
 
 }  // extern "C"

@@ -1,0 +1,179 @@
+"""Backward (masked products), transpose and autograd of the CUDA path,
+against the CPU oracle and FP64 finite differences."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_02471_gb300 import synth
+
+from gpu_helpers import upload
+
+pytestmark = pytest.mark.gpu
+
+INF = (1 << 63) - 1
+NCPU = len(os.sched_getaffinity(0))
+TAU = {np.dtype(np.float64): 1e-12, np.dtype(np.float32): 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _check_backward(A, B, dtype=np.float64, seed=0, **cfg):
+    """GPU dA, dB vs the oracle; tolerance tau * (sum of |terms|), the sums
+    taken by the oracle on absolute values."""
+    import torch
+    from paper_2303_02471_gb300 import ops
+    dA_, dB_ = upload(A, dtype), upload(B, dtype)
+    C, plan = ops.spgemm(dA_, dB_, ops.Config(**cfg) if cfg else None)
+    Ch = C.to_host()
+    rng = np.random.default_rng(seed)
+    dc = rng.standard_normal(C.nnz).astype(dtype)
+    gA, gB = ops.spgemm_backward(plan, dA_, dB_, C, torch.as_tensor(dc, device="cuda"))
+    plan.check()
+    # the oracle widens float32 inputs and always accumulates in float64
+    rA, rB = oracle.backward(A, B, Ch, dc)
+    sA, sB = oracle.backward(A.with_values(np.abs(A.values)), B.with_values(np.abs(B.values)), Ch, np.abs(dc))
+    tau = TAU[np.dtype(dtype)]
+    for got, want, scale, name in ((gA, rA, sA, "dA"), (gB, rB, sB, "dB")):
+        g = got.cpu().numpy().astype(np.float64)
+        bad = np.abs(g - want) > tau * scale + (0 if dtype == np.float64 else 1e-30)
+        assert not bad.any(), f"{name}: {int(bad.sum())} entries off, worst {np.max(np.abs(g - want) - tau * scale)}"
+    return C, plan
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("seed", range(30))
+def test_backward_fuzz(seed, dtype):
+    A, B = synth.fuzz_pair(seed, dtype=dtype)
+    _check_backward(A, B, dtype, seed)
+
+
+@pytest.mark.parametrize("t", [0, 40, None, INF])
+def test_backward_rmat_every_bin(t):
+    A = synth.rmat(13, seed=2, col_cap=600)
+    B = synth.rmat(13, seed=3, col_cap=600)
+    _check_backward(A, B, t=t, hash_cta_max=1024)
+
+
+def test_backward_only_one_side():
+    import torch
+    from paper_2303_02471_gb300 import ops
+    A = synth.random_z(3000, 1, 8, seed=1)
+    B = synth.random_z(3000, 1, 8, seed=2)
+    dA_, dB_ = upload(A), upload(B)
+    C, plan = ops.spgemm(dA_, dB_)
+    dc = torch.ones(C.nnz, dtype=torch.float64, device="cuda")
+    gA, gB = ops.spgemm_backward(plan, dA_, dB_, C, dc, need_dA=False)
+    assert gA is None and gB is not None
+    rA, rB = oracle.backward(A, B, C.to_host(), np.ones(C.nnz))
+    assert np.allclose(gB.cpu().numpy(), rB, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------- transpose
+@pytest.mark.parametrize("case", ["fuzz", "rmat", "long_rows", "empty"])
+def test_transpose_matches_oracle(case):
+    from paper_2303_02471_gb300 import ops
+    rng = np.random.default_rng(4)
+    if case == "fuzz":
+        M = synth.random_pattern(rng, 300, 200, 0.05, shuffle=True)
+    elif case == "rmat":
+        M = synth.rmat(12, seed=1, col_cap=300)
+    elif case == "long_rows":  # rows of 600 and 20000 entries: shared and global sorts
+        M = synth.random_pattern(rng, 3, 20000, 1.0)
+        M2 = synth.random_pattern(rng, 5, 600, 1.0)
+        T2, p2 = ops.csc_transpose(upload(M2))
+        R2, q2 = oracle.transpose(M2)
+        assert np.array_equal(T2.rowidx.cpu().numpy(), R2.rowidx)
+        assert np.array_equal(p2.cpu().numpy(), q2)
+    else:
+        M = synth.random_pattern(rng, 7, 0, 0.5)
+    T, perm = ops.csc_transpose(upload(M))
+    R, q = oracle.transpose(M)
+    Th = T.to_host()
+    assert np.array_equal(Th.colptr, R.colptr)
+    assert np.array_equal(Th.rowidx, R.rowidx)
+    assert np.array_equal(Th.values, R.values)
+    assert np.array_equal(perm.cpu().numpy(), q)
+
+
+# ----------------------------------------------------------------- autograd
+def test_autograd_matches_oracle():
+    import torch
+    from paper_2303_02471_gb300 import autograd as ag
+    A = synth.rmat(11, seed=5, col_cap=200)
+    B = synth.random_z(A.ncols, 1, 7, seed=6)
+    dA_, dB_ = upload(A), upload(B)
+    a = dA_.values.clone().requires_grad_(True)
+    b = dB_.values.clone().requires_grad_(True)
+    C = ag.spgemm(dA_.with_values(a), dB_.with_values(b))
+    w = torch.as_tensor(np.random.default_rng(7).standard_normal(C.nnz), device="cuda")
+    (C.values * w).sum().backward()
+    rA, rB = oracle.backward(A, B, C.to_host(), w.cpu().numpy())
+    assert np.allclose(a.grad.cpu().numpy(), rA, rtol=1e-11, atol=1e-12)
+    assert np.allclose(b.grad.cpu().numpy(), rB, rtol=1e-11, atol=1e-12)
+
+
+def _galerkin_problem(g):
+    A = synth.lap3d(g)
+    P = synth.prolongation(g, seed=0)
+    M0, _ = oracle.spgemm(A, P)
+    Pt0, _ = oracle.transpose(P)
+    C0, _ = oracle.spgemm(Pt0, M0)
+    T = C0.values * synth.perturbation(C0.rowidx.shape[0], seed=1)
+    rng = np.random.default_rng(3)
+    Pv = P.values * (1 + 0.05 * rng.uniform(-1, 1, P.values.shape[0]))
+    return A, P, T, Pv
+
+
+@pytest.mark.parametrize("g", [8, 40])
+def test_galerkin_gradient_vs_oracle(g):
+    import torch
+    from paper_2303_02471_gb300 import autograd as ag
+    A, P, T, Pv = _galerkin_problem(g)
+    dA_ = upload(A)
+    dP = upload(P.with_values(Pv))
+    p = dP.values.clone().requires_grad_(True)
+    C = ag.galerkin(dA_, dP.with_values(p))
+    Tt = torch.as_tensor(T, device="cuda")
+    loss = ((C.values - Tt) ** 2).sum()
+    loss.backward()
+    L, Cr, _, gP = oracle.galerkin(A, P.with_values(Pv), T_values=T)
+    assert np.array_equal(C.rowidx.cpu().numpy(), Cr.rowidx)
+    assert abs(loss.item() - L) <= 1e-10 * max(1.0, abs(L))
+    assert np.allclose(p.grad.cpu().numpy(), gP, rtol=1e-9, atol=1e-9 * np.abs(gP).max())
+
+
+def test_galerkin_finite_differences_workload5():
+    """FP64 central differences of L = ||P^T A P - T||^2 on 64 seeded entries
+    of P at the full 40^3 size (L is a quartic polynomial in each entry)."""
+    import torch
+    from paper_2303_02471_gb300 import autograd as ag
+    A, P, T, Pv = _galerkin_problem(40)
+    dA_ = upload(A)
+    dP = upload(P.with_values(Pv))
+    Tt = torch.as_tensor(T, device="cuda")
+
+    def loss_of(vals):
+        C = ag.galerkin(dA_, dP.with_values(vals))
+        return ((C.values - Tt) ** 2).sum()
+
+    p = dP.values.clone().requires_grad_(True)
+    loss_of(p).backward()
+    grad = p.grad.cpu().numpy()
+    rng = np.random.default_rng(11)
+    idx = rng.choice(Pv.shape[0], 64, replace=False)
+    with torch.no_grad():
+        for i in idx:
+            h = 1e-6 * max(1.0, abs(Pv[i]))
+            vp = dP.values.clone()
+            vm = dP.values.clone()
+            vp[i] += h
+            vm[i] -= h
+            fd = (loss_of(vp).item() - loss_of(vm).item()) / (2 * h)
+            assert abs(fd - grad[i]) <= 1e-6 * max(1.0, abs(grad[i])), (int(i), fd, grad[i])
