@@ -55,7 +55,7 @@ class CscMatrix:
         return SimpleNamespace(nrows=self.nrows, ncols=self.ncols,
                                colptr=self.colptr.cpu().numpy(),
                                rowidx=self.rowidx.cpu().numpy(),
-                               values=None if self.values is None else self.values.cpu().numpy())
+                               values=None if self.values is None else self.values.detach().cpu().numpy())
 
     def with_values(self, values: torch.Tensor) -> "CscMatrix":
         return replace(self, values=values)
