@@ -261,6 +261,69 @@ spg_status spg_csc_transpose(const spg_csc *M, int64_t *T_colptr,
                              void *workspace, size_t ws_bytes,
                              spg_stream stream);
 
+/* ------------------------------------------------------------- batched
+ * nb independent products C_i = A_i x B_i (uneven sizes, each pair with its
+ * own dtype).  The columns of all products are binned together by Op_j and
+ * each phase runs as one persistent kernel whose blocks take work items
+ * (one column of a CTA-level bin, or a tile of columns of a warp-group bin)
+ * heaviest first.  The paper has no batched form; the per-column work is the
+ * method of the single product (H-HASH(t), Section 3.3).  In the batched
+ * kernels t is at most hash_cta_max + 1 (no global-memory hash tables), and
+ * every product's bitmaps must fit shared memory (m_i up to ~2^20 rows);
+ * otherwise the calls return SPG_ERR_UNSUPPORTED.
+ *
+ * A, B         host arrays of nb spg_csc (device pointers inside).
+ * C_colptr     device int64[sum_i (B[i].ncols + 1)], concatenated: product
+ *              i's column pointers start at sum_{i' < i} (B[i'].ncols + 1).
+ */
+typedef struct spg_bplan spg_bplan;
+
+/* Workspace bytes of a batch (shapes only; no device work). */
+spg_status spgemm_batched_workspace_size(int32_t nb, const spg_csc *A,
+                                         const spg_csc *B,
+                                         const spg_config *cfg, size_t *bytes);
+
+/* Symbolic phase of the whole batch: validation (cfg->validate), Op_j and
+ * bins over all columns, one persistent kernel for nnz(C_i[:, j]), a
+ * segmented scan into C_colptr.  nnzC: host int64[nb].  Synchronises. */
+spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A,
+                                   const spg_csc *B, const spg_config *cfg,
+                                   void *workspace, size_t ws_bytes,
+                                   int64_t *C_colptr, int64_t *nnzC,
+                                   spg_bplan **plan, spg_stream stream);
+
+/* Numeric phase of the whole batch in ONE persistent kernel launch.
+ * C_rowidx, C_values: host arrays of nb device pointers (nnzC[i] entries).
+ * use_graph: nonzero captures the launch (with its counter reset) into a CUDA
+ * graph on the first call and replays it while the pointers stay the same
+ * (re-captured when they change); the stream must then not be the legacy
+ * default stream.  Asynchronous. */
+spg_status spgemm_batched_numeric(spg_bplan *plan, const spg_csc *A,
+                                  const spg_csc *B, const int64_t *C_colptr,
+                                  int32_t *const *C_rowidx,
+                                  void *const *C_values, int32_t use_graph,
+                                  spg_stream stream);
+
+/* Backward of every product (as spgemm_backward) in one persistent launch.
+ * dA_values / dB_values: host arrays of nb device pointers or NULL arrays;
+ * an individual NULL pointer skips that gradient.  Asynchronous. */
+spg_status spgemm_batched_backward(spg_bplan *plan, const spg_csc *A,
+                                   const spg_csc *B, const int64_t *C_colptr,
+                                   const int32_t *const *C_rowidx,
+                                   const void *const *dC_values,
+                                   void *const *dA_values,
+                                   void *const *dB_values, spg_stream stream);
+
+/* Synchronise and report the first kernel-side error of the batch. */
+spg_status spg_bplan_check(spg_bplan *plan, spg_stream stream);
+
+/* Host statistics: columns per bin (int64[nbins]), total products, and the
+ * kernels launched by the symbolic, numeric and backward calls (int64[3]). */
+spg_status spg_bplan_info(const spg_bplan *plan, int64_t *bin_counts,
+                          int64_t *products, int64_t *launches);
+
+spg_status spg_bplan_destroy(spg_bplan *plan);
+
 /*
  * Permute a value array on the device: dst[i] = src[idx[i]] (scatter = 0) or
  * dst[idx[i]] = src[i] (scatter = 1), i < n.  With the permutation of

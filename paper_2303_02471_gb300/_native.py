@@ -59,6 +59,13 @@ SIGNATURES = {
     "spg_transpose_workspace_size": (i32, [vp, ctypes.POINTER(ctypes.c_size_t)]),
     "spg_csc_transpose": (i32, [vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     "spg_permute_values": (i32, [vp, vp, vp, i64, i32, i32, vp]),
+    "spgemm_batched_workspace_size": (i32, [i32, vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "spgemm_batched_symbolic": (i32, [i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(vp), vp]),
+    "spgemm_batched_numeric": (i32, [vp, vp, vp, vp, vp, vp, i32, vp]),
+    "spgemm_batched_backward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "spg_bplan_check": (i32, [vp, vp]),
+    "spg_bplan_info": (i32, [vp, vp, ctypes.POINTER(i64), vp]),
+    "spg_bplan_destroy": (i32, [vp]),
 }
 
 _lib = None

@@ -1,0 +1,111 @@
+"""Autotuner of the batched form: picks the H-HASH threshold t, the largest
+shared-memory hash table (hash_cta_max) and the threads per CTA of the
+persistent kernels by timing candidate configurations on the batch itself.
+
+The paper fixes t = 40 for its vector unit and studies t, b_min and b_max by
+hand (Section 5.4); here the choice is measured on the GPU and cached per GPU
+model and batch signature (JSON under $XDG_CACHE_HOME/spgemm_gb300 or the
+path given).
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import json
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import ops
+from .ops import Config
+
+INF = (1 << 63) - 1
+DEFAULT_GRID = {
+    "t": [257, 513, 1025, 2049, None],
+    "hash_cta_max": [2048, 8192],
+    "cta_threads": [256, 512],
+}
+
+
+def _cache_path(path: Optional[str]) -> str:
+    if path:
+        return path
+    base = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(base, "spgemm_gb300", "autotune.json")
+
+
+def signature(As, Bs) -> str:
+    """GPU model, batch size, dtype mix and log2 histograms of the sizes."""
+    dev = torch.cuda.get_device_name(As[0].device) if As else "none"
+    n = np.array([B.ncols for B in Bs], dtype=np.int64)
+    z = np.array([B.nnz / max(1, B.ncols) for B in Bs])
+    f64 = sum(1 for A in As if A.dtype == torch.float64)
+    h = (np.bincount(np.log2(np.maximum(n, 1)).astype(int), minlength=32).tolist(),
+         np.bincount(np.log2(np.maximum(z, 1)).astype(int), minlength=16).tolist())
+    key = json.dumps([dev, len(As), f64, h])
+    return hashlib.sha1(key.encode()).hexdigest()
+
+
+def _time(As, Bs, cfg: Config, repeats: int) -> float:
+    plan = ops.spgemm_batched_symbolic(As, Bs, cfg)
+    ops.spgemm_batched_numeric(plan, As, Bs)
+    plan.check()
+    stream = torch.cuda.current_stream()
+    best = float("inf")
+    for _ in range(repeats):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        p = ops.spgemm_batched_symbolic(As, Bs, cfg)
+        e1.record(stream)
+        ops.spgemm_batched_numeric(p, As, Bs)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e2))
+        p.destroy()
+    plan.destroy()
+    return best
+
+
+def tune(As, Bs, grid: Optional[dict] = None, repeats: int = 2, cache: Optional[str] = None,
+         refresh: bool = False):
+    """Best Config for the batch (cached).  Returns (config, report)."""
+    path = _cache_path(cache)
+    key = signature(As, Bs)
+    table = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if key in table and not refresh:
+        return Config(**table[key]["config"]), table[key]
+    grid = grid or DEFAULT_GRID
+    results = []
+    for t, hmax, thr in itertools.product(grid["t"], grid["hash_cta_max"], grid["cta_threads"]):
+        cfg = Config(t=t, hash_cta_max=hmax, cta_threads=thr)
+        try:
+            ms = _time(As, Bs, cfg, repeats)
+        except RuntimeError as e:  # a shape the candidate does not support
+            ms = float("inf")
+            err = str(e)
+        else:
+            err = None
+        results.append({"config": {"t": t, "hash_cta_max": hmax, "cta_threads": thr}, "ms": ms, "error": err})
+    ok = [r for r in results if np.isfinite(r["ms"])]
+    if not ok:
+        raise RuntimeError("no candidate configuration ran")
+    best = min(ok, key=lambda r: r["ms"])
+    entry = {"config": best["config"], "ms": best["ms"], "candidates": results}
+    table[key] = entry
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return Config(**best["config"]), entry

@@ -13,7 +13,7 @@
 //     first walk sets them, prefix counts turn each row into its position in
 //     the sorted column, and a second walk accumulates every product at that
 //     position (shared memory up to `cap` entries, else in place in C).
-#include "kernels.cuh"
+#include "columns.cuh"
 
 namespace spg {
 
@@ -42,88 +42,20 @@ __global__ void __launch_bounds__(kGroupThreads) k_num_group(BinTask t, Operands
     const int grp = threadIdx.x / G;
     int32_t *keys = reinterpret_cast<int32_t *>(smem) + grp * H;
     VT *vals = reinterpret_cast<VT *>(smem + (size_t)NG * H * 4) + grp * H;
-    const unsigned mask = group_mask(G);
-    const int gl = threadIdx.x & (G - 1);
     const int64_t gidx = (int64_t)blockIdx.x * NG + grp;
     if (gidx >= t.count) return;
     uint32_t Hj = (uint32_t)H >> t.shrink;
     if (Hj < 1) Hj = 1;
     const int32_t j = t.cols[gidx];
-#pragma unroll
-    for (int i = 0; i < 2 * R; ++i) {
-        keys[i * G + gl] = kEmptyKey;
-        vals[i * G + gl] = VT(0);
-    }
-    __syncwarp(mask);
-    bool ovf = false;
-    group_products<G, true, VT>(mask, o.Acp, o.Arow, static_cast<const VT *>(o.Aval), o.Brow,
-                                static_cast<const VT *>(o.Bval), o.Bcp[j], o.Bcp[j + 1],
-                                [&](int32_t row, VT prod) {
-                                    bool fresh;
-                                    const int32_t slot = hash_insert(keys, Hj, row, fresh);
-                                    if (slot < 0) ovf = true;
-                                    else atomicAdd(&vals[slot], prod);
-                                });
-    __syncwarp(mask);
-    // compact the occupied slots to the front of the table
-    int32_t kk[2 * R];
-    VT vv[2 * R];
-    int pos[2 * R];
-    int n = 0;
-    const unsigned lane_base = (threadIdx.x & 31) & ~(G - 1);
-    const unsigned below = (1u << gl) - 1u;
-#pragma unroll
-    for (int i = 0; i < 2 * R; ++i) {
-        kk[i] = keys[i * G + gl];
-        vv[i] = vals[i * G + gl];
-        const bool occ = kk[i] != kEmptyKey;
-        unsigned b = __ballot_sync(mask, occ) >> lane_base;
-        if (G < 32) b &= (1u << (G & 31)) - 1u;
-        pos[i] = occ ? n + __popc(b & below) : -1;
-        n += __popc(b);
-    }
-    __syncwarp(mask);
-#pragma unroll
-    for (int i = 0; i < 2 * R; ++i)
-        if (pos[i] >= 0 && pos[i] < G * R) {
-            keys[pos[i]] = kk[i];
-            vals[pos[i]] = vv[i];
-        }
-    __syncwarp(mask);
-    int32_t key[R];
-    VT val[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int e = r * G + gl;
-        if (e < n) {
-            key[r] = keys[e];
-            val[r] = vals[e];
-        } else {
-            key[r] = 0x7fffffff;
-            val[r] = VT(0);
-        }
-    }
-    group_bitonic_sort<G, R, VT>(mask, key, val);
     const int64_t c0 = Ccp[j];
-    const int64_t nn = Ccp[j + 1] - c0;
+    bool ovf = false;
+    const bool ok = num_group_column<G, R, VT>(group_mask(G), typed<VT>(o), j, c0, Ccp[j + 1] - c0, keys, vals,
+                                               Hj, Crow, Cval, ovf);
     if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
-    if (nn != n || n > G * R) {
-        set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
-        return;
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int e = r * G + gl;
-        if (e < n) {
-            Crow[c0 + e] = key[r];
-            Cval[c0 + e] = val[r];
-        }
-    }
+    if (!ok) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
 }
 
 // ------------------------------------------------------- CTA hash bins
-__host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
-
 // Placement of the table (TSM) and of the row bitmap (BSM) is a template
 // parameter: pointers derived straight from the shared-memory array let the
 // compiler use shared-space loads and atomics instead of generic ones.
@@ -137,7 +69,7 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
     const int64_t W1 = (t.W + 31) / 32;
     const WalkSmem<VT> w = carve_walk<VT>(smem);
     const size_t o_walk = walk_smem_bytes<VT>(blockDim.x);
-    const size_t tab = al16((size_t)cap * 4) + al16((size_t)cap * sizeof(VT)) + al16((size_t)cap * 4);
+    const size_t tab = cta_table_bytes<VT>(cap);
     unsigned char *gp = t.scratch + (size_t)blockIdx.x * t.scratch_stride;
     // the table and the word list scale with the table size: both live in
     // shared memory, or both in the CTA's global scratch
@@ -150,13 +82,9 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
     uint32_t *L1 = reinterpret_cast<uint32_t *>(smem + o_l0 + (BSM ? al16((size_t)t.W * 4) : 0));
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) L0[i] = 0u;
     for (int64_t i = threadIdx.x; i < W1; i += blockDim.x) L1[i] = 0u;
-    const VT *Aval = static_cast<const VT *>(o.Aval);
-    const VT *Bval = static_cast<const VT *>(o.Bval);
+    const TOps<VT> ops = typed<VT>(o);
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
-            s_occ = 0;
-        }
+        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
         __syncthreads();
         const int64_t ci = s_col;
         if (ci >= t.count) break;
@@ -167,42 +95,11 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
         if (want > cap) want = cap;
         uint32_t H = (uint32_t)(want >> t.shrink);
         if (H < 1) H = 1;
-        for (uint32_t s = threadIdx.x; s < H; s += blockDim.x) {
-            keys[s] = kEmptyKey;
-            vals[s] = VT(0);
-        }
-        __syncthreads();
         bool ovf = false;
-        cta_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                            [&](int32_t row, VT prod) {
-                                bool fresh;
-                                const int32_t slot = hash_insert(keys, H, row, fresh);
-                                if (slot < 0) ovf = true;
-                                else atomicAdd(&vals[slot], prod);
-                            });
+        const bool ok = num_cta_column<VT>(ops, j, c0, nn, keys, vals, wlist, H, L0, L1, t.W, w, &s_occ, s_warp,
+                                           Crow, Cval, ovf);
         if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
-        unsigned occ = 0;
-        for (uint32_t s = threadIdx.x; s < H; s += blockDim.x) {
-            const int32_t key = keys[s];
-            if (key != kEmptyKey) {
-                mark_row(L0, L1, key);
-                ++occ;
-            }
-        }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) occ += __shfl_xor_sync(0xffffffffu, occ, d);
-        if ((threadIdx.x & 31) == 0 && occ) atomicAdd(&s_occ, occ);
-        __syncthreads();
-        const bool ok = (int64_t)s_occ == nn;
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
-        const int64_t K = cta_list_words(L1, W1, wlist, s_warp);
-        cta_expand_words(L0, wlist, K, s_warp, [&](int32_t row, int64_t rank) {
-            const int32_t slot = hash_find(keys, H, row);
-            if (ok && slot >= 0) {
-                Crow[c0 + rank] = row;
-                Cval[c0 + rank] = vals[slot];
-            }
-        });
     }
 }
 
@@ -219,8 +116,7 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
                     : reinterpret_cast<uint2 *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
     VT *s_acc = reinterpret_cast<VT *>(smem + o_walk + (BSM ? (size_t)t.W * 8 : 0));
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
-    const VT *Aval = static_cast<const VT *>(o.Aval);
-    const VT *Bval = static_cast<const VT *>(o.Bval);
+    const TOps<VT> ops = typed<VT>(o);
     for (;;) {
         if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
         __syncthreads();
@@ -229,49 +125,9 @@ __global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const
         const int32_t j = t.cols[ci];
         const int64_t c0 = Ccp[j];
         const int64_t nn = Ccp[j + 1] - c0;
-        if (ci < t.cache_cols) {
-            // SPA flags kept by the symbolic phase
-            const uint32_t *keep = t.flag_cache + (size_t)ci * t.W;
-            for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i].x = keep[i];
-            __syncthreads();
-        } else {
-            // walk 1: SPA flags
-            cta_walk<false, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                                [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
-        }
-        const int64_t total = cta_bitmap_prefix(bm, t.W, s_warp);
-        const bool ok = total == nn;
+        const uint32_t *keep = ci < t.cache_cols ? t.flag_cache + (size_t)ci * t.W : nullptr;
+        const bool ok = num_dense_column<VT>(ops, j, c0, nn, bm, t.W, keep, s_acc, cap, w, s_warp, Crow, Cval);
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
-        const bool in_smem = nn <= cap;
-        // walk 2: accumulate every product at its row's sorted position, in
-        // shared memory when the column fits, else in place in C
-        if (in_smem) {
-            if (ok)
-                for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) s_acc[i] = VT(0);
-            __syncthreads();
-            cta_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                                [&](int32_t row, VT prod) {
-                                    const int32_t r = bitmap_rank(bm, row);
-                                    if (ok) atomicAdd(&s_acc[r], prod);
-                                });
-        } else {
-            VT *gacc = Cval + c0;
-            if (ok)
-                for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) gacc[i] = VT(0);
-            __syncthreads();
-            cta_walk<true, VT>(o.Acp, o.Arow, Aval, o.Brow, Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                                [&](int32_t row, VT prod) {
-                                    const int32_t r = bitmap_rank(bm, row);
-                                    if (ok) atomicAdd(&gacc[r], prod);
-                                });
-        }
-        cta_bitmap_expand(bm, t.W, true, [&](int32_t row, int64_t rank) {
-            if (ok) {
-                Crow[c0 + rank] = row;
-                if (in_smem) Cval[c0 + rank] = s_acc[rank];
-            }
-        });
-        __syncthreads();
     }
 }
 

@@ -5,7 +5,7 @@
 // larger than the column's product count); the dense bin (Op_j >= t,
 // Section 3.3) sets one bit per touched row, the SPA flags of Algorithm 1,
 // and counts the bits (Algorithm 1's counter).
-#include "kernels.cuh"
+#include "columns.cuh"
 
 namespace spg {
 
@@ -29,18 +29,8 @@ __global__ void __launch_bounds__(kGroupThreads) k_sym_group(BinTask t, Operands
     if (Hj < 1) Hj = 1;
     if (gidx < t.count) {
         const int32_t j = t.cols[gidx];
-        for (int s = gl; s < H; s += G) keys[s] = kEmptyKey;
-        __syncwarp(mask);
-        int cnt = 0;
         bool ovf = false;
-        group_products<G, false, float>(mask, o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j],
-                                        o.Bcp[j + 1], [&](int32_t row, float) {
-                                            bool fresh;
-                                            if (hash_insert(keys, Hj, row, fresh) < 0) ovf = true;
-                                            cnt += fresh;
-                                        });
-#pragma unroll
-        for (int d = G / 2; d > 0; d >>= 1) cnt += __shfl_xor_sync(mask, cnt, d, G);
+        const int cnt = sym_group_column<G, R>(mask, typed<float>(o), j, keys, Hj, ovf);
         if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
         if (gl == 0) {
             Ccp[j + 1] = cnt;
@@ -57,7 +47,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_sym_group(BinTask t, Operands
 
 // ------------------------------------------------------- CTA hash bins
 // One CTA per column (dynamic work counter); table of pow2 >= 2 Op_j keys in
-// shared memory, or in the CTA's global scratch for the global bin.
+// shared memory (KSM), or in the CTA's global scratch for the global bin.
 template <bool KSM>
 __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t *Ccp, int64_t cap_slots) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -66,12 +56,10 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
     const WalkSmem<float> w = carve_walk<float>(smem);
     int32_t *keys = KSM ? reinterpret_cast<int32_t *>(smem + walk_smem_bytes<float>(blockDim.x))
                         : reinterpret_cast<int32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
+    const TOps<float> ops = typed<float>(o);
     if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
-            s_cnt = 0;
-        }
+        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
         __syncthreads();
         const int64_t ci = s_col;
         if (ci >= t.count) break;
@@ -80,27 +68,14 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
         if (want > cap_slots) want = cap_slots;
         uint32_t H = (uint32_t)(want >> t.shrink);
         if (H < 1) H = 1;
-        for (uint32_t s = threadIdx.x; s < H; s += blockDim.x) keys[s] = kEmptyKey;
-        __syncthreads();
-        unsigned cnt = 0;
         bool ovf = false;
-        cta_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
-                                [&](int32_t row, float) {
-                                    bool fresh;
-                                    if (hash_insert(keys, H, row, fresh) < 0) ovf = true;
-                                    cnt += fresh;
-                                });
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
-        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, (unsigned long long)cnt);
+        const int64_t cnt = sym_cta_column(ops, j, keys, H, w, &s_cnt, ovf);
         if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
-        __syncthreads();
         if (threadIdx.x == 0) {
-            Ccp[j + 1] = (int64_t)s_cnt;
-            if (s_cnt > s_max) s_max = s_cnt;
-            s_sum += s_cnt;
+            Ccp[j + 1] = cnt;
+            if ((unsigned long long)cnt > s_max) s_max = cnt;
+            s_sum += cnt;
         }
-        __syncthreads();
     }
     if (threadIdx.x == 0 && s_max) {
         atomicMax(&t.ctrl->maxnnz[t.bin], s_max);
@@ -109,8 +84,9 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
 }
 
 // ------------------------------------------------------------ dense bin
-// SPA flags as a bitmap of m bits (shared memory, or global scratch when m
-// is large); nnz(C_j) is the number of set bits.
+// SPA flags as a bitmap of m bits (shared memory when BSM, else global
+// scratch); nnz(C_j) is the number of set bits.  Columns with a cache slot
+// keep their flags for the numeric phase.
 template <bool BSM>
 __global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64_t *Ccp) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -119,40 +95,22 @@ __global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64
     const WalkSmem<float> w = carve_walk<float>(smem);
     uint32_t *bm = BSM ? reinterpret_cast<uint32_t *>(smem + walk_smem_bytes<float>(blockDim.x))
                        : reinterpret_cast<uint32_t *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
+    const TOps<float> ops = typed<float>(o);
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = 0u;
     if (threadIdx.x == 0) s_max = s_sum = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
-            s_cnt = 0;
-        }
+        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
         __syncthreads();
         const int64_t ci = s_col;
         if (ci >= t.count) break;
         const int32_t j = t.cols[ci];
-        // a row is new when its flag bit was still clear (Algorithm 1's counter)
-        unsigned long long cnt = 0;
-        cta_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
-                                [&](int32_t row, float) {
-                                    const uint32_t bit = 1u << (row & 31);
-                                    cnt += (atomicOr(&bm[row >> 5], bit) & bit) ? 0 : 1;
-                                });
-        // keep the flags for the numeric phase when the column has a cache slot
         uint32_t *keep = ci < t.cache_cols ? t.flag_cache + (size_t)ci * t.W : nullptr;
-        for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) {
-            if (keep) keep[i] = bm[i];
-            bm[i] = 0u;
-        }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
-        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
-        __syncthreads();
+        const int64_t cnt = sym_dense_column(ops, j, bm, t.W, keep, w, &s_cnt);
         if (threadIdx.x == 0) {
-            Ccp[j + 1] = (int64_t)s_cnt;
-            if (s_cnt > s_max) s_max = s_cnt;
-            s_sum += s_cnt;
+            Ccp[j + 1] = cnt;
+            if ((unsigned long long)cnt > s_max) s_max = cnt;
+            s_sum += cnt;
         }
-        __syncthreads();
     }
     if (threadIdx.x == 0 && s_max) {
         atomicMax(&t.ctrl->maxnnz[t.bin], s_max);

@@ -264,3 +264,116 @@ def csc_transpose(M: CscMatrix, with_perm: bool = True):
     N.check(N.lib().spg_csc_transpose(ctypes.byref(cM), _ptr(cp), _ptr(row), _ptr(vals), _ptr(perm),
                                       _ptr(ws), ws.numel(), _stream()), "spg_csc_transpose")
     return CscMatrix(M.ncols, M.nrows, cp, row, vals), perm
+
+
+# ------------------------------------------------------------------ batched
+class BatchedPlan:
+    """Host plan of a batch plus the device workspace and concatenated colptr."""
+
+    def __init__(self, handle, workspace, colptr, nnz, segs, shapes, config):
+        self._h = handle
+        self.workspace = workspace
+        self.colptr = colptr        # concatenated int64 column pointers
+        self.nnz = nnz              # list of nnz(C_i)
+        self.segs = segs            # start of product i's column pointers in colptr
+        self.shapes = shapes        # (m_i, n_i)
+        self.config = config
+        self.outputs = None
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan destroyed")
+        return self._h
+
+    def colptr_of(self, i: int) -> torch.Tensor:
+        return self.colptr[self.segs[i]:self.segs[i] + self.shapes[i][1] + 1]
+
+    def info(self):
+        counts = (ctypes.c_int64 * 64)()
+        prod = ctypes.c_int64()
+        launches = (ctypes.c_int64 * 3)()
+        N.check(N.lib().spg_bplan_info(self.handle, counts, ctypes.byref(prod), launches), "spg_bplan_info")
+        return {"bins": list(counts[:14]), "products": prod.value, "launches": list(launches)}
+
+    def check(self) -> None:
+        N.check(N.lib().spg_bplan_check(self.handle, _stream()), "spg_bplan_check")
+
+    def destroy(self) -> None:
+        if self._h is not None:
+            N.lib().spg_bplan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _csc_array(Ms):
+    arr = (N.SpgCsc * max(1, len(Ms)))()
+    for i, M in enumerate(Ms):
+        arr[i] = _csc(M)
+    return arr
+
+
+def spgemm_batched_symbolic(As, Bs, config: Optional[Config] = None) -> BatchedPlan:
+    """Column pointers and nnz of every C_i = A_i B_i (synchronises)."""
+    if len(As) != len(Bs):
+        raise ValueError("A and B lists differ in length")
+    config = config or Config()
+    cfg = config.native()
+    nb = len(As)
+    cA, cB = _csc_array(As), _csc_array(Bs)
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().spgemm_batched_workspace_size(nb, cA, cB, ctypes.byref(cfg), ctypes.byref(nbytes)),
+            "spgemm_batched_workspace_size")
+    dev = As[0].device if nb else torch.device("cuda")
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    segs, off = [], 0
+    for B in Bs:
+        segs.append(off)
+        off += B.ncols + 1
+    colptr = torch.empty(max(off, 1), dtype=torch.int64, device=dev)
+    nnz = (ctypes.c_int64 * max(1, nb))()
+    h = ctypes.c_void_p()
+    N.check(N.lib().spgemm_batched_symbolic(nb, cA, cB, ctypes.byref(cfg), _ptr(ws), ws.numel(), _ptr(colptr),
+                                            nnz, ctypes.byref(h), _stream()), "spgemm_batched_symbolic")
+    shapes = [(A.nrows, B.ncols) for A, B in zip(As, Bs)]
+    return BatchedPlan(h, ws, colptr, list(nnz[:nb]), segs, shapes, config)
+
+
+def spgemm_batched_numeric(plan: BatchedPlan, As, Bs, use_graph: bool = False):
+    """All C_i in one persistent launch (optionally a replayed CUDA graph).
+    Output buffers are allocated on the first call and reused, so a captured
+    graph stays valid across calls."""
+    nb = len(As)
+    if plan.outputs is None:
+        plan.outputs = [(torch.empty(n, dtype=torch.int32, device=A.device),
+                         torch.empty(n, dtype=A.dtype, device=A.device)) for n, A in zip(plan.nnz, As)]
+    rows = (ctypes.c_void_p * max(1, nb))(*[r.data_ptr() if r.numel() else None for r, _ in plan.outputs])
+    vals = (ctypes.c_void_p * max(1, nb))(*[v.data_ptr() if v.numel() else None for _, v in plan.outputs])
+    N.check(N.lib().spgemm_batched_numeric(plan.handle, _csc_array(As), _csc_array(Bs), _ptr(plan.colptr), rows,
+                                           vals, int(bool(use_graph)), _stream()), "spgemm_batched_numeric")
+    return [CscMatrix(A.nrows, B.ncols, plan.colptr_of(i), r, v)
+            for i, (A, B, (r, v)) in enumerate(zip(As, Bs, plan.outputs))]
+
+
+def spgemm_batched(As, Bs, config: Optional[Config] = None, use_graph: bool = False):
+    plan = spgemm_batched_symbolic(As, Bs, config)
+    return spgemm_batched_numeric(plan, As, Bs, use_graph), plan
+
+
+def spgemm_batched_backward(plan: BatchedPlan, As, Bs, Cs, dCs, need_dA: bool = True, need_dB: bool = True):
+    nb = len(As)
+    dA = [torch.empty(A.nnz, dtype=A.dtype, device=A.device) for A in As] if need_dA else None
+    dB = [torch.empty(B.nnz, dtype=B.dtype, device=B.device) for B in Bs] if need_dB else None
+    rows = (ctypes.c_void_p * max(1, nb))(*[C.rowidx.data_ptr() if C.nnz else None for C in Cs])
+    dcs = [d.contiguous() for d in dCs]
+    dcp = (ctypes.c_void_p * max(1, nb))(*[d.data_ptr() if d.numel() else None for d in dcs])
+    dap = (ctypes.c_void_p * max(1, nb))(*[d.data_ptr() if d.numel() else None for d in dA]) if need_dA else None
+    dbp = (ctypes.c_void_p * max(1, nb))(*[d.data_ptr() if d.numel() else None for d in dB]) if need_dB else None
+    N.check(N.lib().spgemm_batched_backward(plan.handle, _csc_array(As), _csc_array(Bs), _ptr(plan.colptr), rows,
+                                            dcp, dap, dbp, _stream()), "spgemm_batched_backward")
+    return dA, dB

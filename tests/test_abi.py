@@ -1,0 +1,72 @@
+"""The C ABI without a GPU: the library builds and loads, exports every
+function include/spgemm.h declares, and the ctypes layouts match."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spgemm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:spg_status|const char \*)\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2303_02471_gb300 import _native, build
+    if not os.path.exists(_native.LIB_PATH):
+        build.build()
+    return _native.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("spgemm_symbolic", "spgemm_numeric", "spgemm_backward", "spgemm_batched_symbolic",
+                     "spgemm_batched_numeric", "spgemm_batched_backward", "spgemm_workspace_size"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2303_02471_gb300 import _native
+    names = declared_functions()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_native.SIGNATURES), set(names) ^ set(_native.SIGNATURES)
+
+
+def test_struct_layouts():
+    from paper_2303_02471_gb300 import _native as N
+    assert ctypes.sizeof(N.SpgCsc) == 56
+    assert N.SpgCsc.values.offset == 40 and N.SpgCsc.dtype.offset == 48
+    assert ctypes.sizeof(N.SpgConfig) == 40
+    assert N.SpgConfig.dense_cache_bytes.offset == 32
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2303_02471_gb300 import _native as N
+    for code, name in N.STATUS.items():
+        assert lib.spg_status_string(code).decode().startswith(name)
+    c = N.SpgConfig()
+    assert lib.spg_config_default(ctypes.byref(c)) == 0
+    assert c.t == -1 and c.validate == 1 and c.hash_cta_max == 8192
+    assert lib.spg_config_default(None) == 1
+
+
+def test_host_only_calls(lib):
+    from paper_2303_02471_gb300 import _native as N
+    M = N.SpgCsc(10, 7, 30, None, None, None, 0)
+    nbytes = ctypes.c_size_t()
+    assert lib.spg_transpose_workspace_size(ctypes.byref(M), ctypes.byref(nbytes)) == 0
+    assert nbytes.value >= 30 * 8
+    bad = N.SpgCsc(-1, 7, 30, None, None, None, 0)
+    assert lib.spg_transpose_workspace_size(ctypes.byref(bad), ctypes.byref(nbytes)) == 1
+    assert lib.spg_plan_destroy(None) == 0
+    assert lib.spg_bplan_destroy(None) == 0
+    assert lib.spg_plan_check(None, None) == 1
+    assert lib.spg_permute_values(None, None, None, 0, 0, 0, None) == 0
+    assert lib.spg_permute_values(None, None, None, 5, 0, 0, None) == 1

@@ -1,0 +1,138 @@
+"""Batched products (one persistent launch, CUDA-graph replay, autotuner)
+against the per-matrix calls and the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_02471_gb300 import synth
+
+from gpu_helpers import TAU, assert_matches_oracle, upload
+
+pytestmark = pytest.mark.gpu
+
+INF = (1 << 63) - 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _upload_pairs(pairs):
+    return [upload(A) for A, _ in pairs], [upload(B) for _, B in pairs]
+
+
+@pytest.mark.parametrize("t", [None, 0, 257, INF])
+def test_batched_matches_oracle_and_plain(t):
+    from paper_2303_02471_gb300 import ops
+    pairs = synth.batch_pairs(24, seed=3, n_scale=0.05)
+    As, Bs = _upload_pairs(pairs)
+    cfg = ops.Config(t=t)
+    Cs, plan = ops.spgemm_batched(As, Bs, cfg)
+    plan.check()
+    info = plan.info()
+    assert info["launches"][1] == 1
+    for (A, B), C, dA, dB in zip(pairs, Cs, As, Bs):
+        assert_matches_oracle(C, A, B)
+        P, pp = ops.spgemm(dA, dB, cfg)
+        assert (P.colptr == C.colptr).all() and (P.rowidx == C.rowidx).all()
+
+
+def test_batched_mixed_shapes_and_empty_products():
+    from paper_2303_02471_gb300 import ops
+    rng = np.random.default_rng(5)
+    pairs = [synth.fuzz_pair(s) for s in range(12)]
+    pairs += [(synth.random_pattern(rng, 300, 200, 0.05), synth.random_pattern(rng, 200, 150, 0.05))]
+    As, Bs = _upload_pairs(pairs)
+    Cs, plan = ops.spgemm_batched(As, Bs)
+    plan.check()
+    for (A, B), C in zip(pairs, Cs):
+        assert_matches_oracle(C, A, B)
+
+
+def test_batched_graph_replay():
+    import torch
+    from paper_2303_02471_gb300 import ops
+    pairs = synth.batch_pairs(32, seed=4, n_scale=0.05)
+    As, Bs = _upload_pairs(pairs)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan = ops.spgemm_batched_symbolic(As, Bs)
+        first = [(C.rowidx.clone(), C.values.clone()) for C in ops.spgemm_batched_numeric(plan, As, Bs, True)]
+        for C in plan.outputs:
+            C[0].zero_()
+            C[1].zero_()
+        Cs = ops.spgemm_batched_numeric(plan, As, Bs, True)  # replay
+        plan.check()
+    s.synchronize()
+    refs = [oracle.spgemm(A, B) for A, B in pairs]
+    for (A, B), C, (r0, v0), ref in zip(pairs, Cs, first, refs):
+        assert (C.rowidx == r0).all()
+        assert_matches_oracle(C, A, B, ref=ref)
+
+
+def test_batched_backward_matches_plain():
+    import torch
+    from paper_2303_02471_gb300 import ops
+    pairs = synth.batch_pairs(16, seed=6, n_scale=0.04)
+    As, Bs = _upload_pairs(pairs)
+    Cs, plan = ops.spgemm_batched(As, Bs)
+    rng = np.random.default_rng(1)
+    dCs = [torch.as_tensor(rng.standard_normal(C.nnz), device="cuda").to(C.values.dtype) for C in Cs]
+    gA, gB = ops.spgemm_batched_backward(plan, As, Bs, Cs, dCs)
+    plan.check()
+    for (A, B), C, dc, ga, gb in zip(pairs, Cs, dCs, gA, gB):
+        Ch = C.to_host()
+        d = dc.cpu().numpy()
+        rA, rB = oracle.backward(A, B, Ch, d)
+        sA, sB = oracle.backward(A.with_values(np.abs(A.values)), B.with_values(np.abs(B.values)), Ch, np.abs(d))
+        tau = TAU[np.dtype(A.values.dtype)]
+        assert np.all(np.abs(ga.cpu().numpy().astype(np.float64) - rA) <= tau * sA)
+        assert np.all(np.abs(gb.cpu().numpy().astype(np.float64) - rB) <= tau * sB)
+
+
+def test_batched_rejects_bad_input():
+    from paper_2303_02471_gb300 import ops
+    from paper_2303_02471_gb300._native import SpgError
+    pairs = synth.batch_pairs(4, seed=7, n_scale=0.03)
+    As, Bs = _upload_pairs(pairs)
+    bad = Bs[2].rowidx.clone()
+    bad[3] = Bs[2].nrows  # out of range
+    Bs[2] = ops.CscMatrix(Bs[2].nrows, Bs[2].ncols, Bs[2].colptr, bad, Bs[2].values)
+    with pytest.raises(SpgError) as e:
+        ops.spgemm_batched_symbolic(As, Bs)
+    assert e.value.name == "SPG_ERR_INVALID"
+
+
+def test_workload4_full_batch_sampled():
+    """The 512-product batch (n_i log-uniform 500..20000, Z_i ~ U{2..40}, half
+    float64 and half float32): sampled products against the oracle, all
+    against the closed form of their product count (Op_j = Z_i^2)."""
+    from paper_2303_02471_gb300 import ops
+    pairs = synth.batch_pairs(512, seed=0)
+    As, Bs = _upload_pairs(pairs)
+    Cs, plan = ops.spgemm_batched(As, Bs)
+    plan.check()
+    want = sum(A.ncols * (A.colptr[1] - A.colptr[0]) ** 2 for A, _ in pairs)
+    assert plan.info()["products"] == want
+    for i in list(range(0, 512, 43)) + [255, 256, 511]:
+        A, B = pairs[i]
+        assert_matches_oracle(Cs[i], A, B, nthreads=8)
+
+
+def test_autotune_chooses_and_caches(tmp_path):
+    from paper_2303_02471_gb300 import autotune
+    pairs = synth.batch_pairs(16, seed=8, n_scale=0.05)
+    As, Bs = _upload_pairs(pairs)
+    path = str(tmp_path / "tune.json")
+    grid = {"t": [257, None], "hash_cta_max": [2048], "cta_threads": [256, 512]}
+    cfg, rep = autotune.tune(As, Bs, grid=grid, repeats=1, cache=path)
+    assert len(rep["candidates"]) == 4
+    cfg2, rep2 = autotune.tune(As, Bs, grid=grid, repeats=1, cache=path)
+    assert rep2["config"] == rep["config"]
+    from paper_2303_02471_gb300 import ops
+    Cs, plan = ops.spgemm_batched(As, Bs, cfg)
+    for (A, B), C in zip(pairs, Cs):
+        assert_matches_oracle(C, A, B)
