@@ -221,7 +221,9 @@ __device__ __forceinline__ void bnum_group(const BTask &b, const BProb &P, int64
     const int NG = blockDim.x / G;
     const int grp = threadIdx.x / G;
     int32_t *keys = reinterpret_cast<int32_t *>(smem) + grp * H;
-    VT *vals = reinterpret_cast<VT *>(smem + al16((size_t)NG * H * 4)) + grp * H;
+    // value slots of a group are strided by 8 bytes whatever the dtype: groups
+    // of one tile may belong to products of different dtypes
+    VT *vals = reinterpret_cast<VT *>(smem + al16((size_t)NG * H * 4) + (size_t)grp * H * 8);
     uint32_t Hj = (uint32_t)H >> b.shrink;
     if (Hj < 1) Hj = 1;
     const int64_t c0 = P.Ccp[j];
@@ -307,12 +309,12 @@ __device__ __forceinline__ void bgroup_item(const BTask &b, int bin, int64_t idx
         if (P.dtype == SPG_F64)
             ok = bwd_group_column<G, double>(group_mask(G), prob_ops<double>(P), (int32_t)j, P.Ccp[j], P.Ccp[j + 1],
                                              P.Crow, static_cast<const double *>(P.dC), keys,
-                                             reinterpret_cast<double *>(vb) + grp * H, (uint32_t)H,
+                                             reinterpret_cast<double *>(vb + (size_t)grp * H * 8), (uint32_t)H,
                                              static_cast<double *>(P.dA), static_cast<double *>(P.dB));
         else
             ok = bwd_group_column<G, float>(group_mask(G), prob_ops<float>(P), (int32_t)j, P.Ccp[j], P.Ccp[j + 1],
                                             P.Crow, static_cast<const float *>(P.dC), keys,
-                                            reinterpret_cast<float *>(vb) + grp * H, (uint32_t)H,
+                                            reinterpret_cast<float *>(vb + (size_t)grp * H * 8), (uint32_t)H,
                                             static_cast<float *>(P.dA), static_cast<float *>(P.dB));
         if (!ok) set_error(b.ctrl, SPG_ERR_TABLE_OVERFLOW, bin, g);
     }
@@ -536,7 +538,7 @@ size_t phase_smem(const spg_bplan &P, int phase, int threads, int64_t &cap_cta, 
     for (int b = 0; b < kNumWarpBins; ++b)
         if (P.host.hist[BIN_WARP0 + b])
             need = std::max(need, al16((size_t)threads * 2 * warp_bin_R(b) * 4) +
-                                      (size_t)threads * 2 * warp_bin_R(b) * w);
+                                      (size_t)threads * 2 * warp_bin_R(b) * 8);
     bool cta = false;
     int64_t maxop = 0, maxnnz = 0;
     for (int c = 0; c < kNumCtaBins; ++c)
