@@ -335,6 +335,35 @@ spg_status spg_permute_values(const void *src, const int64_t *idx, void *dst,
                               int64_t n, int32_t dtype, int32_t scatter,
                               spg_stream stream);
 
+/*
+ * spg_csc_transpose for callers that cannot allocate device memory and
+ * cannot pass a workspace: code that runs where cudaMalloc is unavailable or
+ * forbidden (a plug-in whose host owns every allocation, a fixed device
+ * memory budget, a pool that hands out only the inputs and outputs).  The
+ * paper has no counterpart; it is a service of this library.
+ *
+ * Same arguments and results as spg_csc_transpose minus the workspace: the
+ * scratch is a file-scope device array of SPG_NOALLOC_SCRATCH_BYTES inside
+ * this library, which every GPU that loads the library holds until the
+ * process exits.  Nothing is allocated by the call.
+ *   - The matrix must satisfy spg_transpose_workspace_size(M) <=
+ *     SPG_NOALLOC_SCRATCH_BYTES (32 MiB, about 1.3 million entries);
+ *     larger ones are rejected with SPG_ERR_WORKSPACE before any device work.
+ *   - The first call on a device looks up the array's device address on the
+ *     current device (cudaGetSymbolAddress); make that first call before any
+ *     stream capture on that device.
+ *   - All calls on a device share the array, which keeps the last call's
+ *     contents (the parts that must start at zero are cleared by every
+ *     call); calls whose work overlaps on the GPU race on it, so order them,
+ *     e.g. on one stream.
+ * Errors: as spg_csc_transpose, plus SPG_ERR_WORKSPACE for a matrix beyond
+ * the limit and SPG_ERR_CUDA if the address lookup fails.
+ */
+#define SPG_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+spg_status spg_csc_transpose_noalloc(const spg_csc *M, int64_t *T_colptr,
+                                     int32_t *T_rowidx, void *T_values,
+                                     int64_t *perm, spg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

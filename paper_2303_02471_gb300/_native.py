@@ -59,6 +59,7 @@ SIGNATURES = {
     "spg_transpose_workspace_size": (i32, [vp, ctypes.POINTER(ctypes.c_size_t)]),
     "spg_csc_transpose": (i32, [vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     "spg_permute_values": (i32, [vp, vp, vp, i64, i32, i32, vp]),
+    "spg_csc_transpose_noalloc": (i32, [vp, vp, vp, vp, vp, vp]),
     "spgemm_batched_workspace_size": (i32, [i32, vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
     "spgemm_batched_symbolic": (i32, [i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(vp), vp]),
     "spgemm_batched_numeric": (i32, [vp, vp, vp, vp, vp, vp, i32, vp]),
