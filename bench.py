@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--workload", type=int, default=3, choices=[1, 2, 3])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-aux", action="store_true",
+                   help="skip the batched (512 products) and backward (Galerkin 40^3) measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU seconds of the oracle sample")
     p.add_argument("--t", type=int, default=None,
@@ -329,6 +331,9 @@ def run_ours(args, rank, world):
         base = None
         if not args.no_cpu_baseline and world == 1:
             base = cpu_baseline(A_h, B_h, args.cpu_seconds, "GFLOP/s")
+        aux = {}
+        if not args.no_aux:
+            aux = {"batched": run_batched(args, dev), "backward": run_backward(args, dev)}
         line = {"metric": "SpGEMM GFLOP/s (2 x intermediate products / s)", "value": round(value, 3),
                 "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
@@ -338,10 +343,118 @@ def run_ours(args, rank, world):
                            "parallelism": f"replicas x{world}"},
                 "phases_ms": {"symbolic": round(float(np.mean([a.elapsed_time(b) for a, b, c in ev])), 4),
                               "numeric": round(num_avg, 4)},
-                "roofline": roof, "numeric_bins": per_bin, "cpu_baseline": base, "e2e": e2e,
+                "roofline": roof, "numeric_bins": per_bin, "cpu_baseline": base, "e2e": e2e, **aux,
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clk}
     return line
+
+
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def run_batched(args, dev):
+    """The 512-product batch: autotuned persistent launches (symbolic + numeric,
+    numeric replayed from a CUDA graph) against the plain per-matrix calls."""
+    import torch
+    from paper_2303_02471_gb300 import autotune, ops, synth
+    pairs = synth.batch_pairs(512, seed=0)
+    As = [ops.CscMatrix.from_host(A, device=dev) for A, _ in pairs]
+    Bs = [ops.CscMatrix.from_host(B, device=dev) for _, B in pairs]
+    products = int(sum(A.ncols * (A.colptr[1] - A.colptr[0]) ** 2 for A, _ in pairs))
+    cfg, rep = autotune.tune(As, Bs, repeats=1)
+    side = torch.cuda.Stream(device=dev)
+    steps = max(3, min(args.steps, 10))
+    with torch.cuda.stream(side):
+        plan = ops.spgemm_batched_symbolic(As, Bs, cfg)
+        ops.spgemm_batched_numeric(plan, As, Bs, use_graph=True)
+        ops.spgemm_batched_numeric(plan, As, Bs, use_graph=True)
+        plan.check()
+        ev = _events(2)
+        ev[0].record(side)
+        for _ in range(steps):
+            ops.spgemm_batched_numeric(plan, As, Bs, use_graph=True)
+        ev[1].record(side)
+        side.synchronize()
+        num_ms = ev[0].elapsed_time(ev[1]) / steps
+        ev = _events(2)
+        ev[0].record(side)
+        for _ in range(steps):
+            p2 = ops.spgemm_batched_symbolic(As, Bs, cfg)
+            ops.spgemm_batched_numeric(p2, As, Bs)
+            p2.destroy()
+        ev[1].record(side)
+        side.synchronize()
+        step_ms = ev[0].elapsed_time(ev[1]) / steps
+        plan.check()
+        # plain per-matrix calls, same products
+        for A, B in zip(As[:8], Bs[:8]):
+            ops.spgemm(A, B, cfg)
+        ev = _events(2)
+        ev[0].record(side)
+        for A, B in zip(As, Bs):
+            C, pl = ops.spgemm(A, B, cfg)
+            pl.destroy()
+        ev[1].record(side)
+        side.synchronize()
+        plain_ms = ev[0].elapsed_time(ev[1])
+    launches = plan.info()["launches"]
+    gf = lambda ms: round(2.0 * products / (ms * 1e-3) / 1e9, 3)
+    return {"workload": "512 products C_i = A_i x B_i, n_i log-uniform 500..20000, Z_i ~ U{2..40}, "
+                        "half f64 half f32", "products": products,
+            "config": rep["config"], "GFLOPs_batched_step": gf(step_ms), "ms_batched_step": round(step_ms, 3),
+            "GFLOPs_batched_numeric_graph": gf(num_ms), "ms_batched_numeric_graph": round(num_ms, 3),
+            "GFLOPs_plain_per_matrix": gf(plain_ms), "ms_plain_per_matrix": round(plain_ms, 3),
+            "launches_symbolic_numeric": launches[:2]}
+
+
+def run_backward(args, dev):
+    """Galerkin product P^T (A P) on the 40^3 Laplacian: forward (two products
+    and the transpose) against the backward (two masked-product passes)."""
+    import torch
+    from paper_2303_02471_gb300 import ops, synth
+    A_h, P_h = synth.workload(5)
+    A = ops.CscMatrix.from_host(A_h, device=dev)
+    P = ops.CscMatrix.from_host(P_h, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def forward():
+        M, pm = ops.spgemm(A, P)
+        Pt, perm = ops.csc_transpose(P)
+        C, pc = ops.spgemm(Pt, M)
+        return M, pm, Pt, C, pc
+
+    M, pm, Pt, C, pc = forward()
+    G = torch.ones_like(C.values)
+    products = pm.info()["products"] + pc.info()["products"]
+
+    def backward():
+        dPt, dM = ops.spgemm_backward(pc, Pt, M, C, G)
+        _, dP = ops.spgemm_backward(pm, A, P, M, dM, need_dA=False)
+        return dP
+
+    for _ in range(3):
+        forward()
+        backward()
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 20))
+    ev = _events(4)
+    ev[0].record(stream)
+    for _ in range(steps):
+        forward()
+    ev[1].record(stream)
+    ev[2].record(stream)
+    for _ in range(steps):
+        backward()
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    f_ms = ev[0].elapsed_time(ev[1]) / steps
+    b_ms = ev[2].elapsed_time(ev[3]) / steps
+    gf = lambda ms: round(2.0 * products / (ms * 1e-3) / 1e9, 3)
+    return {"workload": "Galerkin P^T (A P), A 40^3 7-point Laplacian, P 64000 x 8000 aggregation",
+            "products": int(products), "ms_forward": round(f_ms, 4), "ms_backward": round(b_ms, 4),
+            "GFLOPs_forward": gf(f_ms), "GFLOPs_backward": gf(b_ms)}
 
 
 def run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world):
