@@ -52,6 +52,8 @@ def parse():
                    help="target CPU seconds of the oracle sample")
     p.add_argument("--t", type=int, default=None,
                    help="H-HASH(t) threshold (default: the library's)")
+    p.add_argument("--cta-threads", type=int, default=None,
+                   help="threads per CTA of the CTA-level kernels (default: the library's)")
     p.add_argument("--dense-cache", type=int, default=None,
                    help="bytes of workspace for dense-column SPA flags kept between phases")
     p.add_argument("--rmat-scale", type=int, default=18,
@@ -220,7 +222,7 @@ def run_ours(args, rank, world):
     w = 8
     A = ops.CscMatrix.from_host(A_h, device=dev)
     B = A if B_h is A_h else ops.CscMatrix.from_host(B_h, device=dev)
-    cfg = ops.Config(t=args.t, dense_cache_bytes=args.dense_cache)
+    cfg = ops.Config(t=args.t, dense_cache_bytes=args.dense_cache, cta_threads=args.cta_threads)
     ncfg = cfg.native()
     lib = N.lib()
     stream = torch.cuda.current_stream()

@@ -31,7 +31,7 @@ static int occupancy(K kernel, int threads, size_t smem) {
 }
 
 template <int G, int R, typename VT>
-__global__ void __launch_bounds__(kGroupThreads) k_bwd_group(BinTask t, Operands o, const int64_t *Ccp,
+__global__ void __launch_bounds__(kGroupThreads, 1) k_bwd_group(BinTask t, Operands o, const int64_t *Ccp,
                                                              const int32_t *Crow, const VT *dC, VT *dA, VT *dB) {
     constexpr int H = 2 * G * R;
     constexpr int NG = kGroupThreads / G;
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_bwd_group(BinTask t, Operands
 }
 
 template <typename VT, bool TSM>
-__global__ void __launch_bounds__(1024) k_bwd_cta(BinTask t, Operands o, const int64_t *Ccp, const int32_t *Crow,
+__global__ void __launch_bounds__(1024, 1) k_bwd_cta(BinTask t, Operands o, const int64_t *Ccp, const int32_t *Crow,
                                                   const VT *dC, VT *dA, VT *dB, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(1024) k_bwd_cta(BinTask t, Operands o, const i
 }
 
 template <typename VT, bool BSM>
-__global__ void __launch_bounds__(1024) k_bwd_dense(BinTask t, Operands o, const int64_t *Ccp, const int32_t *Crow,
+__global__ void __launch_bounds__(1024, 1) k_bwd_dense(BinTask t, Operands o, const int64_t *Ccp, const int32_t *Crow,
                                                     const VT *dC, VT *dA, VT *dB, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;

@@ -332,7 +332,7 @@ __device__ __forceinline__ void bgroup_dispatch(const BTask &b, int bin, int64_t
 }
 
 // phase 0: symbolic, 1: numeric, 2: backward.  One launch per phase.
-__global__ void __launch_bounds__(1024) k_batched(BTask b, BItems it, int phase) {
+__global__ void __launch_bounds__(512, 1) k_batched(BTask b, BItems it, int phase) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_item;
     __shared__ int64_t s_warp[32];
@@ -671,7 +671,8 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
     if (!P) return SPG_ERR_INVALID;
     P->nb = nb;
     P->cfg = c;
-    P->threads = c.cta_threads;
+    // the persistent kernel is built for at most 512 threads (register budget)
+    P->threads = c.cta_threads > 512 ? 512 : c.cta_threads;
     cudaGetDevice(&P->device);
     int sms = 1, optin = 48 * 1024;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);

@@ -189,6 +189,8 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                                          const VT *__restrict__ Aval, const int32_t *__restrict__ Brow,
                                          const VT *__restrict__ Bval, int64_t p0, int64_t p1,
                                          const WalkSmem<VT> &w, F &&f) {
+    // gathers in flight per lane; fewer for double values to stay in registers
+    constexpr int UB = (VALS && sizeof(VT) == 8) ? 2 : kWalkBatch;
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
     const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
@@ -239,11 +241,11 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                     if (w.key[mid] <= win0) li = mid; else hi = mid - 1;
                 }
             }
-            for (int win = win0; win < e1; win += kWalkBatch) {
-                int32_t rows[kWalkBatch];
-                VT av[kWalkBatch], bvs[kWalkBatch];
+            for (int win = win0; win < e1; win += UB) {
+                int32_t rows[UB];
+                VT av[UB], bvs[UB];
 #pragma unroll
-                for (int u = 0; u < kWalkBatch; ++u) {
+                for (int u = 0; u < UB; ++u) {
                     rows[u] = -1;
                     if (win + u < e1) {
                         while (li + 1 < nl && w.key[li + 1] <= win + u) ++li;
@@ -259,7 +261,7 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < kWalkBatch; ++u) {
+                for (int u = 0; u < UB; ++u) {
                     if (rows[u] >= 0) {
                         VT prod = VT(0);
                         if (VALS) prod = av[u] * bvs[u];
@@ -281,11 +283,11 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                     const int mid = (s + hi + 1) >> 1;
                     if (sk[mid] <= qs) s = mid; else hi = mid - 1;
                 }
-                for (int win = s0w; win < s1w; win += kWalkBatch) {
-                    int32_t rows[kWalkBatch];
-                    VT av[kWalkBatch], bvs[kWalkBatch];
+                for (int win = s0w; win < s1w; win += UB) {
+                    int32_t rows[UB];
+                    VT av[UB], bvs[UB];
 #pragma unroll
-                    for (int u = 0; u < kWalkBatch; ++u) {
+                    for (int u = 0; u < UB; ++u) {
                         rows[u] = -1;
                         if (win + u < s1w) {  // uniform over the warp
                             const int qf = (win + u) << 5;
@@ -306,7 +308,7 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < kWalkBatch; ++u) {
+                    for (int u = 0; u < UB; ++u) {
                         if (rows[u] >= 0) {
                             VT prod = VT(0);
                             if (VALS) prod = av[u] * bvs[u];

@@ -34,7 +34,7 @@ static int occupancy(K kernel, int threads, size_t smem) {
 
 // ------------------------------------------------- warp-group hash bins
 template <int G, int R, typename VT>
-__global__ void __launch_bounds__(kGroupThreads) k_num_group(BinTask t, Operands o, const int64_t *Ccp,
+__global__ void __launch_bounds__(kGroupThreads, 1) k_num_group(BinTask t, Operands o, const int64_t *Ccp,
                                                              int32_t *Crow, VT *Cval) {
     constexpr int H = 2 * G * R;
     constexpr int NG = kGroupThreads / G;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_num_group(BinTask t, Operands
 // parameter: pointers derived straight from the shared-memory array let the
 // compiler use shared-space loads and atomics instead of generic ones.
 template <typename VT, bool TSM, bool BSM>
-__global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
+__global__ void __launch_bounds__(1024, 1) k_num_cta(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
                                                   VT *Cval, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(1024) k_num_cta(BinTask t, Operands o, const i
 
 // ------------------------------------------------------------ dense bin
 template <typename VT, bool BSM>
-__global__ void __launch_bounds__(1024) k_num_dense(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
+__global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
                                                     VT *Cval, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;

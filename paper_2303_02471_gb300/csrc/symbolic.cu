@@ -15,7 +15,7 @@ constexpr int kGroupThreads = 256;
 // One group of G lanes per column; the group's table has 2 G R slots for
 // Op_j <= G R, so it is at most half full.
 template <int G, int R>
-__global__ void __launch_bounds__(kGroupThreads) k_sym_group(BinTask t, Operands o, int64_t *Ccp) {
+__global__ void __launch_bounds__(kGroupThreads, 1) k_sym_group(BinTask t, Operands o, int64_t *Ccp) {
     constexpr int H = 2 * G * R;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_max, s_sum;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_sym_group(BinTask t, Operands
 // One CTA per column (dynamic work counter); table of pow2 >= 2 Op_j keys in
 // shared memory (KSM), or in the CTA's global scratch for the global bin.
 template <bool KSM>
-__global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t *Ccp, int64_t cap_slots) {
+__global__ void __launch_bounds__(1024, 1) k_sym_cta(BinTask t, Operands o, int64_t *Ccp, int64_t cap_slots) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(1024) k_sym_cta(BinTask t, Operands o, int64_t
 // scratch); nnz(C_j) is the number of set bits.  Columns with a cache slot
 // keep their flags for the numeric phase.
 template <bool BSM>
-__global__ void __launch_bounds__(1024) k_sym_dense(BinTask t, Operands o, int64_t *Ccp) {
+__global__ void __launch_bounds__(1024, 1) k_sym_dense(BinTask t, Operands o, int64_t *Ccp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
