@@ -311,7 +311,9 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     Operands o{A->colptr, A->rowidx, nullptr, B->colptr, B->rowidx, nullptr};
     for (int b = 1; b < NBINS; ++b) {
         if (!P->host.hist[b]) continue;
-        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mA, c.cta_threads, P->dev.sms, P->dev.smem_optin,
+        // the symbolic CTA kernels run best at up to 512 threads (measured)
+        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mA, std::min(c.cta_threads, 512), P->dev.sms,
+                                  P->dev.smem_optin,
                                   (int64_t)P->host.maxop[b], c.table_shrink, P->L.scratch_ctas);
         CK(launch_symbolic_bin(P->task(b), o, C_colptr, g, s));
     }

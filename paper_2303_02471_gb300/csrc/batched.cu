@@ -332,7 +332,7 @@ __device__ __forceinline__ void bgroup_dispatch(const BTask &b, int bin, int64_t
 }
 
 // phase 0: symbolic, 1: numeric, 2: backward.  One launch per phase.
-__global__ void __launch_bounds__(512, 1) k_batched(BTask b, BItems it, int phase) {
+__global__ void __launch_bounds__(512, 2) k_batched(BTask b, BItems it, int phase) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_item;
     __shared__ int64_t s_warp[32];
