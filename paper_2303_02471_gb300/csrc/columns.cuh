@@ -272,7 +272,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                if (ok) atomicAdd(&gacc[r], prod);
                            });
     }
-    cta_bitmap_expand(bm, W, true, [&](int32_t row, int64_t rank) {
+    cta_bitmap_visit(bm, W, true, [&](int32_t row, int64_t rank) {
         if (ok) {
             Crow[c0 + rank] = row;
             if (in_smem) Cval[c0 + rank] = s_acc[rank];

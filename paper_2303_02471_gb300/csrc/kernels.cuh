@@ -536,6 +536,28 @@ __device__ __forceinline__ void cta_bitmap_expand(uint2 *bm, int64_t W, bool cle
     }
 }
 
+// Thread-per-word variant of cta_bitmap_expand: thread t takes words t,
+// t + blockDim, ... and visits the set bits of each in ascending order with
+// rank = .y + (index of the bit among the word's set bits).  Consecutive
+// threads hold consecutive words, so a warp's stores fall in a few lines.
+// Clears the bits when `clear`.  No barrier inside.
+template <typename F>
+__device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W, bool clear, F &&f) {
+    for (int64_t w = threadIdx.x; w < W; w += blockDim.x) {
+        const uint2 v = bm[w];
+        if (!v.x) continue;
+        if (clear) bm[w].x = 0u;
+        uint32_t bits = v.x;
+        int64_t rank = v.y;
+        const int32_t row0 = (int32_t)(w * 32);
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            f(row0 + b, rank++);
+        }
+    }
+}
+
 // ------------------------------------------------------------ launchers
 cudaError_t launch_inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t s);
 int64_t scan_tile_count(int64_t n);
