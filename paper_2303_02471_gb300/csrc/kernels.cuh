@@ -233,39 +233,51 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
         // ---- long entries: windows [win0, min(win1, WL))
         {
             const int e1 = win1 < WL ? win1 : WL;
-            int li = 0;
             if (win0 < e1) {
-                int hi = nl - 1;
+                int li = 0, hi = nl - 1;
                 while (li < hi) {
                     const int mid = (li + hi + 1) >> 1;
                     if (w.key[mid] <= win0) li = mid; else hi = mid - 1;
                 }
-            }
-            for (int win = win0; win < e1; win += UB) {
-                int32_t rows[UB];
-                VT av[UB], bvs[UB];
+                // the owner is the same for every lane of a window: keep its
+                // entry in registers and reload only when it advances
+                int e_key = w.key[li], e_z = w.z[li];
+                int64_t e_a0 = w.a0[li];
+                VT e_b = VALS ? w.bv[li] : VT(0);
+                int next_key = li + 1 < nl ? w.key[li + 1] : 0x7fffffff;
+                for (int win = win0; win < e1; win += UB) {
+                    int32_t rows[UB];
+                    VT av[UB], bvs[UB];
 #pragma unroll
-                for (int u = 0; u < UB; ++u) {
-                    rows[u] = -1;
-                    if (win + u < e1) {
-                        while (li + 1 < nl && w.key[li + 1] <= win + u) ++li;
-                        const int idx = ((win + u - w.key[li]) << 5) + lane;
-                        if (idx < w.z[li]) {
-                            const int64_t qa = w.a0[li] + idx;
-                            rows[u] = Arow[qa];
-                            if (VALS) {
-                                av[u] = Aval[qa];
-                                bvs[u] = w.bv[li];
+                    for (int u = 0; u < UB; ++u) {
+                        rows[u] = -1;
+                        if (win + u < e1) {
+                            while (next_key <= win + u) {
+                                ++li;
+                                e_key = next_key;
+                                e_z = w.z[li];
+                                e_a0 = w.a0[li];
+                                if (VALS) e_b = w.bv[li];
+                                next_key = li + 1 < nl ? w.key[li + 1] : 0x7fffffff;
+                            }
+                            const int idx = ((win + u - e_key) << 5) + lane;
+                            if (idx < e_z) {
+                                const int64_t qa = e_a0 + idx;
+                                rows[u] = Arow[qa];
+                                if (VALS) {
+                                    av[u] = Aval[qa];
+                                    bvs[u] = e_b;
+                                }
                             }
                         }
                     }
-                }
 #pragma unroll
-                for (int u = 0; u < UB; ++u) {
-                    if (rows[u] >= 0) {
-                        VT prod = VT(0);
-                        if (VALS) prod = av[u] * bvs[u];
-                        f(rows[u], prod);
+                    for (int u = 0; u < UB; ++u) {
+                        if (rows[u] >= 0) {
+                            VT prod = VT(0);
+                            if (VALS) prod = av[u] * bvs[u];
+                            f(rows[u], prod);
+                        }
                     }
                 }
             }
