@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, co
 
 // ------------------------------------------------------------- launches
 constexpr size_t kBitmapSmemMax = 96 * 1024;
-constexpr int64_t kDenseStage = 2048;
+constexpr int64_t kDenseStage = 8192;
 
 // Threads per CTA of the CTA-level bins: small columns share an SM among
 // several CTAs, the largest get a whole SM.
