@@ -241,8 +241,7 @@ __device__ __forceinline__ bool num_cta_column(const TOps<VT> &o, int32_t j, int
 template <typename VT>
 __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, int64_t c0, int64_t nn, uint2 *bm,
                                                  int64_t W, const uint32_t *keep, VT *s_acc, int64_t cap,
-                                                 int32_t *s_rows, int64_t stage, const WalkSmem<VT> &w,
-                                                 int64_t *s_warp, int32_t *Crow, VT *Cval) {
+                                                 const WalkSmem<VT> &w, int64_t *s_warp, int32_t *Crow, VT *Cval) {
     if (keep) {
         for (int64_t i = threadIdx.x; i < W; i += blockDim.x) bm[i].x = keep[i];
         __syncthreads();
@@ -273,39 +272,12 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                if (ok) atomicAdd(&gacc[r], prod);
                            });
     }
-    if (in_smem && ok && stage > 0) {
-        // rows through a shared staging buffer, `stage` ranks at a time, so
-        // rows and values both leave in coalesced copies
-        for (int64_t r0 = 0; r0 < nn; r0 += stage) {
-            const int64_t r1 = r0 + stage < nn ? r0 + stage : nn;
-            for (int64_t wd = threadIdx.x; wd < W; wd += blockDim.x) {
-                const uint2 v = bm[wd];
-                if (!v.x || (int64_t)v.y >= r1 || (int64_t)v.y + __popc(v.x) <= r0) continue;
-                uint32_t bits = v.x;
-                int64_t rank = v.y;
-                while (bits) {
-                    const int b = __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    if (rank >= r0 && rank < r1) s_rows[rank - r0] = (int32_t)(wd * 32 + b);
-                    ++rank;
-                }
-            }
-            __syncthreads();
-            for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-                Crow[c0 + r] = s_rows[r - r0];
-                Cval[c0 + r] = s_acc[r];
-            }
-            __syncthreads();
+    cta_bitmap_visit(bm, W, true, [&](int32_t row, int64_t rank) {
+        if (ok) {
+            Crow[c0 + rank] = row;
+            if (in_smem) Cval[c0 + rank] = s_acc[rank];
         }
-        for (int64_t i = threadIdx.x; i < W; i += blockDim.x) bm[i].x = 0u;
-    } else {
-        cta_bitmap_visit(bm, W, true, [&](int32_t row, int64_t rank) {
-            if (ok) {
-                Crow[c0 + rank] = row;
-                if (in_smem) Cval[c0 + rank] = s_acc[rank];
-            }
-        });
-    }
+    });
     __syncthreads();
     return ok;
 }

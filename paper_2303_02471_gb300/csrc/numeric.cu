@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_cta(BinTask t, Operands o, cons
 // ------------------------------------------------------------ dense bin
 template <typename VT, bool BSM>
 __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
-                                                    VT *Cval, int64_t cap, int64_t stage) {
+                                                    VT *Cval, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ int64_t s_warp[32];
@@ -114,9 +114,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, co
     const size_t o_walk = walk_smem_bytes<VT>(blockDim.x);
     uint2 *bm = BSM ? reinterpret_cast<uint2 *>(smem + o_walk)
                     : reinterpret_cast<uint2 *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
-    const size_t o_rows = o_walk + (BSM ? (size_t)t.W * 8 : 0);
-    int32_t *s_rows = reinterpret_cast<int32_t *>(smem + o_rows);
-    VT *s_acc = reinterpret_cast<VT *>(smem + o_rows + al16((size_t)stage * 4));
+    VT *s_acc = reinterpret_cast<VT *>(smem + o_walk + (BSM ? (size_t)t.W * 8 : 0));
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
     const TOps<VT> ops = typed<VT>(o);
     for (;;) {
@@ -128,15 +126,13 @@ __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, co
         const int64_t c0 = Ccp[j];
         const int64_t nn = Ccp[j + 1] - c0;
         const uint32_t *keep = ci < t.cache_cols ? t.flag_cache + (size_t)ci * t.W : nullptr;
-        const bool ok = num_dense_column<VT>(ops, j, c0, nn, bm, t.W, keep, s_acc, cap, s_rows, stage, w, s_warp,
-                                             Crow, Cval);
+        const bool ok = num_dense_column<VT>(ops, j, c0, nn, bm, t.W, keep, s_acc, cap, w, s_warp, Crow, Cval);
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
     }
 }
 
 // ------------------------------------------------------------- launches
 constexpr size_t kBitmapSmemMax = 96 * 1024;
-constexpr int64_t kDenseStage = 8192;
 
 // Threads per CTA of the CTA-level bins: small columns share an SM among
 // several CTAs, the largest get a whole SM.
@@ -183,9 +179,7 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
     const size_t bmb = (size_t)W * 8;
     const size_t walk = walk_smem_bytes<VT>(g.threads);
     g.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
-    // staging buffer of the sorted row extraction (ranks per pass)
-    g.slots = std::min<int64_t>(kDenseStage, std::max<int64_t>(maxnnz, 1));
-    size_t base = walk + (g.bm_global ? 0 : bmb) + al16((size_t)g.slots * 4);
+    size_t base = walk + (g.bm_global ? 0 : bmb);
     size_t room = smem_optin > base ? smem_optin - base : 0;
     int64_t cap = (int64_t)(room / sizeof(VT));
     if (cap > maxnnz) cap = maxnnz;
@@ -230,7 +224,7 @@ static cudaError_t launch_numeric_t(const BinTask &t, const Operands &o, const i
     } else {
         auto k = g.bm_global ? k_num_dense<VT, false> : k_num_dense<VT, true>;
         allow_smem(k, g.smem);
-        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.cap, g.slots);
+        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.cap);
     }
     return cudaGetLastError();
 }
