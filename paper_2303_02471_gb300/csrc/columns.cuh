@@ -100,7 +100,7 @@ __device__ __forceinline__ int64_t sym_dense_column(const TOps<float> &o, int32_
                                cnt += (atomicOr(&bm[row >> 5], bit) & bit) ? 0 : 1;
                            });
     for (int64_t i = threadIdx.x; i < W; i += blockDim.x) {
-        if (keep) __stcs(&keep[i], bm[i]);
+        if (keep) keep[i] = bm[i];
         bm[i] = 0u;
     }
 #pragma unroll
@@ -179,8 +179,8 @@ __device__ __forceinline__ bool num_group_column(unsigned mask, const TOps<VT> &
     for (int r = 0; r < R; ++r) {
         const int e = r * G + gl;
         if (e < n) {
-            __stcs(&Crow[c0 + e], key[r]);
-            __stcs(&Cval[c0 + e], val[r]);
+            Crow[c0 + e] = key[r];
+            Cval[c0 + e] = val[r];
         }
     }
     return true;
@@ -225,8 +225,8 @@ __device__ __forceinline__ bool num_cta_column(const TOps<VT> &o, int32_t j, int
     cta_expand_words(L0, wlist, K, s_warp, [&](int32_t row, int64_t rank) {
         const int32_t slot = hash_find(keys, H, row);
         if (ok && slot >= 0) {
-            __stcs(&Crow[c0 + rank], row);
-            __stcs(&Cval[c0 + rank], vals[slot]);
+            Crow[c0 + rank] = row;
+            Cval[c0 + rank] = vals[slot];
         }
     });
     return ok;
@@ -250,7 +250,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
 #pragma unroll
             for (int u = 0; u < KB; ++u) {
                 const int64_t i = base + (int64_t)u * blockDim.x;
-                v[u] = i < W ? __ldcs(&keep[i]) : 0u;
+                v[u] = i < W ? keep[i] : 0u;
             }
 #pragma unroll
             for (int u = 0; u < KB; ++u) {
@@ -286,12 +286,10 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                if (ok) atomicAdd(&gacc[r], prod);
                            });
     }
-    // C is written once and not read again here: streaming stores keep the
-    // gathered A columns in L2
     cta_bitmap_visit(bm, W, true, [&](int32_t row, int64_t rank) {
         if (ok) {
-            __stcs(&Crow[c0 + rank], row);
-            if (in_smem) __stcs(&Cval[c0 + rank], s_acc[rank]);
+            Crow[c0 + rank] = row;
+            if (in_smem) Cval[c0 + rank] = s_acc[rank];
         }
     });
     __syncthreads();
