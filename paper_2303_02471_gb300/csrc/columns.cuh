@@ -243,21 +243,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                                  int64_t W, const uint32_t *keep, VT *s_acc, int64_t cap,
                                                  const WalkSmem<VT> &w, int64_t *s_warp, int32_t *Crow, VT *Cval) {
     if (keep) {
-        // every load of a batch is issued before its stores: one round trip
-        constexpr int KB = 8;
-        for (int64_t base = threadIdx.x; base < W; base += (int64_t)KB * blockDim.x) {
-            uint32_t v[KB];
-#pragma unroll
-            for (int u = 0; u < KB; ++u) {
-                const int64_t i = base + (int64_t)u * blockDim.x;
-                v[u] = i < W ? keep[i] : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < KB; ++u) {
-                const int64_t i = base + (int64_t)u * blockDim.x;
-                if (i < W) bm[i].x = v[u];
-            }
-        }
+        for (int64_t i = threadIdx.x; i < W; i += blockDim.x) bm[i].x = keep[i];
         __syncthreads();
     } else {
         cta_walk<false, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
