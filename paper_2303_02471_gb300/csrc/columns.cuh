@@ -241,7 +241,10 @@ __device__ __forceinline__ bool num_cta_column(const TOps<VT> &o, int32_t j, int
 template <typename VT>
 __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, int64_t c0, int64_t nn, uint2 *bm,
                                                  int64_t W, const uint32_t *keep, VT *s_acc, int64_t cap,
-                                                 const WalkSmem<VT> &w, int64_t *s_warp, int32_t *Crow, VT *Cval) {
+                                                 const WalkSmem<VT> &w, int64_t *s_warp, unsigned *s_next,
+                                                 int32_t *Crow, VT *Cval) {
+    // the previous user of *s_next finished before the caller's last barrier
+    if (threadIdx.x == 0) *s_next = blockDim.x >> 5;
     if (keep) {
         for (int64_t i = threadIdx.x; i < W; i += blockDim.x) bm[i].x = keep[i];
         __syncthreads();
@@ -272,7 +275,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                if (ok) atomicAdd(&gacc[r], prod);
                            });
     }
-    cta_bitmap_visit(bm, W, true, [&](int32_t row, int64_t rank) {
+    cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int64_t rank) {
         if (ok) {
             Crow[c0 + rank] = row;
             if (in_smem) Cval[c0 + rank] = s_acc[rank];

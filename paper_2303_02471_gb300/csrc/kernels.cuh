@@ -509,64 +509,48 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, int64
     return total;
 }
 
-// Visits the set bits of bm[0..W) in ascending row order, calling
-// f(row, rank) with rank = position of the row in the sorted column;
-// consecutive lanes get consecutive ranks, so writes at C[c0 + rank] are
-// coalesced.  With `clear`, the bits are reset on the way (.y is left stale).
-// Every thread must call it; bm[..].y must hold the prefix counts.
-template <typename F>
-__device__ __forceinline__ void cta_bitmap_expand(uint2 *bm, int64_t W, bool clear, F &&f) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t nchunks = (W + 31) / 32;
-    for (int64_t c = warp; c < nchunks; c += nw) {
-        const int64_t w = c * 32 + lane;
-        const uint2 v = w < W ? bm[w] : make_uint2(0u, 0u);
-        if (clear && v.x) bm[w].x = 0u;
-        if (__ballot_sync(0xffffffffu, v.x != 0u) == 0u) continue;
-        const int cnt = __popc(v.x);
-        int incl = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int o = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += o;
-        }
-        const int S = __shfl_sync(0xffffffffu, incl, 31);
-        const int excl = incl - cnt;
-        for (int o0 = 0; o0 < S; o0 += 32) {
-            const int o = o0 + lane;
-            int s = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int ex = __shfl_sync(0xffffffffu, excl, s + step);
-                if (ex <= o) s += step;
-            }
-            unsigned b = __shfl_sync(0xffffffffu, v.x, s);
-            const int k = o - __shfl_sync(0xffffffffu, excl, s);
-            const unsigned ys = __shfl_sync(0xffffffffu, v.y, s);
-            if (o < S) f((int32_t)((c * 32 + s) * 32 + select_bit(b, k)), (int64_t)ys + k);
-        }
-    }
-}
+// Visits the set bits of bm[0..W) with f(row, rank), rank = position of the
+// row in the sorted column (bm[..].y must hold the prefix counts).  Warps
+// take chunks of 32 words, the first one by warp index and the next ones
+// from the shared counter *s_next, which must hold the number of warps
+// before a barrier that precedes the call.  Each lane visits up to
+// kVisitLight bits of its own word; the rest of a fuller word is visited by
+// the whole warp, one lane per bit, so a dense stretch of rows (the hub rows
+// of a power-law matrix) costs no single lane many serial steps, and its
+// stores are coalesced.  Clears the bits when `clear`.  No barrier inside.
+constexpr int kVisitLight = 4;
 
-// Thread-per-word variant of cta_bitmap_expand: thread t takes words t,
-// t + blockDim, ... and visits the set bits of each in ascending order with
-// rank = .y + (index of the bit among the word's set bits).  Consecutive
-// threads hold consecutive words, so a warp's stores fall in a few lines.
-// Clears the bits when `clear`.  No barrier inside.
 template <typename F>
-__device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W, bool clear, F &&f) {
-    for (int64_t w = threadIdx.x; w < W; w += blockDim.x) {
-        const uint2 v = bm[w];
-        if (!v.x) continue;
-        if (clear) bm[w].x = 0u;
+__device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W, bool clear, unsigned *s_next, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t nchunks = (W + 31) >> 5;
+    int64_t c = threadIdx.x >> 5;
+    while (c < nchunks) {
+        const int64_t wd = (c << 5) + lane;
+        const uint2 v = wd < W ? bm[wd] : make_uint2(0u, 0u);
+        if (clear && v.x) bm[wd].x = 0u;
+        const int32_t row0 = (int32_t)(wd << 5);
         uint32_t bits = v.x;
         int64_t rank = v.y;
-        const int32_t row0 = (int32_t)(w * 32);
-        while (bits) {
+        for (int i = 0; i < kVisitLight && bits; ++i) {
             const int b = __ffs(bits) - 1;
             bits &= bits - 1u;
             f(row0 + b, rank++);
         }
+        unsigned heavy = __ballot_sync(0xffffffffu, bits != 0u);
+        while (heavy) {
+            const int s = __ffs(heavy) - 1;
+            heavy &= heavy - 1u;
+            const uint32_t hb = __shfl_sync(0xffffffffu, v.x, s);
+            const uint32_t hy = __shfl_sync(0xffffffffu, v.y, s);
+            const int k = __popc(hb & below);
+            if (((hb >> lane) & 1u) && k >= kVisitLight)
+                f((int32_t)((((c << 5) + s) << 5) + lane), (int64_t)hy + k);
+        }
+        unsigned nc = 0;
+        if (lane == 0) nc = atomicAdd(s_next, 1u);
+        c = (int64_t)__shfl_sync(0xffffffffu, nc, 0);
     }
 }
 

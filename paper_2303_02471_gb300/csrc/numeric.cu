@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, co
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ int64_t s_warp[32];
+    __shared__ unsigned s_chunk;
     const WalkSmem<VT> w = carve_walk<VT>(smem);
     const size_t o_walk = walk_smem_bytes<VT>(blockDim.x);
     uint2 *bm = BSM ? reinterpret_cast<uint2 *>(smem + o_walk)
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, co
         const int64_t c0 = Ccp[j];
         const int64_t nn = Ccp[j + 1] - c0;
         const uint32_t *keep = ci < t.cache_cols ? t.flag_cache + (size_t)ci * t.W : nullptr;
-        const bool ok = num_dense_column<VT>(ops, j, c0, nn, bm, t.W, keep, s_acc, cap, w, s_warp, Crow, Cval);
+        const bool ok = num_dense_column<VT>(ops, j, c0, nn, bm, t.W, keep, s_acc, cap, w, s_warp, &s_chunk, Crow, Cval);
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
     }
 }
