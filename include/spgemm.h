@@ -97,7 +97,8 @@ typedef struct {
     /* Bytes of workspace that keep the SPA flag bitmaps (m bits per column)
      * the symbolic phase builds for dense-SPA columns, so that the numeric
      * phase reuses them instead of walking the column's products twice.
-     * Columns beyond the budget rebuild their flags.  0 disables. */
+     * Columns beyond the budget rebuild their flags.  0 disables;
+     * default 2 GiB. */
     int64_t dense_cache_bytes;
 } spg_config;
 

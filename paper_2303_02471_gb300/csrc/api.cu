@@ -187,7 +187,7 @@ spg_status spg_config_default(spg_config *cfg) {
     cfg->validate = 1;
     cfg->table_shrink = 0;
     cfg->scratch_cap_bytes = (int64_t)1 << 30;
-    cfg->dense_cache_bytes = (int64_t)1 << 30;
+    cfg->dense_cache_bytes = (int64_t)2 << 30;
     return SPG_OK;
 }
 

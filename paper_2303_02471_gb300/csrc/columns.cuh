@@ -245,14 +245,12 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                                  int32_t *Crow, VT *Cval) {
     // the previous user of *s_next finished before the caller's last barrier
     if (threadIdx.x == 0) *s_next = blockDim.x >> 5;
-    if (keep) {
-        for (int64_t i = threadIdx.x; i < W; i += blockDim.x) bm[i].x = keep[i];
-        __syncthreads();
-    } else {
+    // flags kept from the symbolic phase are read straight into the prefix
+    // pass; otherwise the walk sets them again
+    if (!keep)
         cta_walk<false, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                             [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
-    }
-    const int64_t total = cta_bitmap_prefix(bm, W, s_warp);
+    const int64_t total = cta_bitmap_prefix(bm, W, keep, s_warp);
     const bool ok = total == nn;
     const bool in_smem = nn <= cap;
     if (in_smem) {
@@ -477,7 +475,7 @@ __device__ __forceinline__ void bwd_dense_column(const TOps<VT> &o, int32_t j, i
         atomicOr(&bm[r >> 5].x, 1u << (r & 31));
     }
     __syncthreads();
-    cta_bitmap_prefix(bm, W, s_warp);
+    cta_bitmap_prefix(bm, W, nullptr, s_warp);
     const bool in_smem = nn <= cap;
     if (in_smem)
         for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) s_dc[e] = dC[c0 + e];

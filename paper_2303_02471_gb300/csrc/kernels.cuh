@@ -472,41 +472,79 @@ __device__ __forceinline__ int32_t bitmap_rank(const uint2 *bm, int32_t row) {
 }
 
 // Exclusive prefix of popcounts over W words into .y; returns the total.
-// Each warp owns a contiguous range of words.  Every thread must call it.
-__device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, int64_t *s_warp) {
+// The bits come from src[0..W) when src is given (a copy kept in global
+// memory, written to .x on the way), else from .x.  A warp takes 256
+// consecutive words as four rounds of 64, lane l holding words 2l and 2l+1
+// of each round: loads and 16-byte stores are contiguous across the warp,
+// and the four rounds' counts share one packed 64-bit warp scan (16 bits per
+// round; a round counts at most 2048 bits).  Warps cover consecutive runs;
+// one block-wide offset per pass.  Every thread must call it.
+__device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, const uint32_t *src, int64_t *s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t per = ((W + nw - 1) / nw + 31) & ~int64_t(31);
-    const int64_t w0 = ((int64_t)warp * per < W) ? (int64_t)warp * per : W;
-    const int64_t w1 = (w0 + per < W) ? w0 + per : W;
-    // pass 1: words of this warp
-    int64_t cnt = 0;
-    for (int64_t w = w0 + lane; w < w1; w += 32) cnt += __popc(bm[w].x);
+    // pair loads and 16-byte stores need aligned starts (uniform over the CTA)
+    const bool vec = (reinterpret_cast<uintptr_t>(bm) & 15) == 0 &&
+                     (src == nullptr || (reinterpret_cast<uintptr_t>(src) & 7) == 0);
+    int64_t carry = 0;
+    for (int64_t r0 = 0; r0 < W; r0 += (int64_t)256 * nw) {
+        const int64_t wb = r0 + (int64_t)warp * 256 + 2 * lane;
+        uint32_t b[8];
+        uint64_t packed = 0;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
-    if (lane == 0) s_warp[warp] = cnt;
-    __syncthreads();
-    int64_t off = 0, total = 0;
-    for (int i = 0; i < nw; ++i) {
-        const int64_t c = s_warp[i];
-        if (i < warp) off += c;
-        total += c;
-    }
-    // pass 2: running prefix inside the warp's range
-    for (int64_t base = w0; base < w1; base += 32) {
-        const int64_t w = base + lane;
-        const unsigned bits = w < w1 ? bm[w].x : 0u;
-        int c = __popc(bits);
-        int incl = c;
+        for (int k = 0; k < 4; ++k) {
+            const int64_t w = wb + 64 * k;
+            if (vec && w + 1 < W) {
+                if (src) {
+                    const uint2 u = *reinterpret_cast<const uint2 *>(src + w);
+                    b[2 * k] = u.x;
+                    b[2 * k + 1] = u.y;
+                } else {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(bm + w);
+                    b[2 * k] = u.x;
+                    b[2 * k + 1] = u.z;
+                }
+            } else {
+                b[2 * k] = w < W ? (src ? src[w] : bm[w].x) : 0u;
+                b[2 * k + 1] = w + 1 < W ? (src ? src[w + 1] : bm[w + 1].x) : 0u;
+            }
+            packed |= (uint64_t)(__popc(b[2 * k]) + __popc(b[2 * k + 1])) << (16 * k);
+        }
+        const uint64_t mine = packed;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            int o = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += o;
+            const uint64_t o = __shfl_up_sync(0xffffffffu, packed, d);
+            if (lane >= d) packed += o;
         }
-        if (w < w1) bm[w].y = (unsigned)(off + incl - c);
-        off += __shfl_sync(0xffffffffu, incl, 31);
+        const uint64_t tot = __shfl_sync(0xffffffffu, packed, 31);
+        const int64_t wsum = (int64_t)((tot & 0xffff) + ((tot >> 16) & 0xffff) + ((tot >> 32) & 0xffff) + (tot >> 48));
+        if (lane == 31) s_warp[warp] = wsum;
+        __syncthreads();
+        int64_t tw = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xffffffffu, tw, d);
+            if (lane >= d) tw += o;
+        }
+        const int64_t before = __shfl_sync(0xffffffffu, tw, warp > 0 ? warp - 1 : 0);
+        const int64_t pass = __shfl_sync(0xffffffffu, tw, nw - 1);
+        int64_t base = carry + (warp > 0 ? before : 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t w = wb + 64 * k;
+            const uint32_t y0 = (uint32_t)(base + (int64_t)((packed >> (16 * k)) & 0xffff) -
+                                           (int64_t)((mine >> (16 * k)) & 0xffff));
+            const uint32_t y1 = y0 + (uint32_t)__popc(b[2 * k]);
+            if (vec && w + 1 < W) {
+                *reinterpret_cast<uint4 *>(bm + w) = make_uint4(b[2 * k], y0, b[2 * k + 1], y1);
+            } else {
+                if (w < W) bm[w] = make_uint2(b[2 * k], y0);
+                if (w + 1 < W) bm[w + 1] = make_uint2(b[2 * k + 1], y1);
+            }
+            base += (int64_t)((tot >> (16 * k)) & 0xffff);
+        }
+        carry += pass;
+        __syncthreads();
     }
-    __syncthreads();
-    return total;
+    return carry;
 }
 
 // Visits the set bits of bm[0..W) with f(row, rank), rank = position of the

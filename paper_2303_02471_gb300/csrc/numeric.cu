@@ -176,7 +176,10 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
         g.grid = (int)std::max<int64_t>(1, grid);
         return g;
     }
-    // dense
+    // dense; with the double sums in C, a CTA holds only the walk scratch and
+    // the flags, so two CTAs of 512 threads share an SM and one's barriers
+    // overlap the other's work
+    if (sizeof(VT) == 8 && g.threads > 512) g.threads = 512;
     const size_t bmb = (size_t)W * 8;
     const size_t walk = walk_smem_bytes<VT>(g.threads);
     g.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
@@ -184,6 +187,11 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
     size_t room = smem_optin > base ? smem_optin - base : 0;
     int64_t cap = (int64_t)(room / sizeof(VT));
     if (cap > maxnnz) cap = maxnnz;
+    // Double sums go to C in place: on GB300 a walk that adds with RED.F64
+    // into L2-resident C runs about 1.3x the products per SM-second of one
+    // that adds with shared-memory f64 atomics, and the extraction then copies
+    // no values.  Float sums stay in shared memory (native f32 atomics).
+    if (sizeof(VT) == 8) cap = 0;
     g.cap = cap;
     g.smem = base + (size_t)cap * sizeof(VT);
     int occ = occupancy(k_num_dense<VT, true>, g.threads, g.smem);
