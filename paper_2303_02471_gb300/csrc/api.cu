@@ -55,7 +55,9 @@ spg_config normalized(const spg_config *cfg) {
 // product count reaches m / 128, within [257, hash_cta_max + 1].
 int64_t effective_t(const spg_config &c, int64_t m) {
     if (c.t >= 0) return c.t;
-    int64_t t = (m + 127) / 128;
+    // measured crossover on GB300: the dense SPA is the faster one from
+    // Op_j of about m / 256 up (the flags cost O(m / 32) words per column)
+    int64_t t = (m + 255) / 256;
     if (t > (int64_t)c.hash_cta_max + 1) t = (int64_t)c.hash_cta_max + 1;
     if (t < 257) t = 257;
     return t;

@@ -235,9 +235,11 @@ __device__ __forceinline__ bool num_cta_column(const TOps<VT> &o, int32_t j, int
 // Column j by the dense SPA (Algorithm 1): flags as a bitmap (from `keep`
 // when the symbolic phase kept them, else a first product walk), prefix
 // counts, then every product is added at its row's position in the sorted
-// column -- in shared memory (s_acc, up to cap entries) or in place in C --
-// and the rows are written in ascending order.  bm (W uint2) is zero on entry
-// and on return.  Returns false on a count mismatch.
+// column, and the rows are written in ascending order.  The sums of the
+// first `cap` positions live in shared memory (s_acc), the others in place
+// in C, so the shared-memory and the L2 atomic units both take products.
+// bm (W uint2) is zero on entry and on return.  Returns false on a count
+// mismatch.
 template <typename VT>
 __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, int64_t c0, int64_t nn, uint2 *bm,
                                                  int64_t W, const uint32_t *keep, VT *s_acc, int64_t cap,
@@ -252,31 +254,25 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                             [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
     const int64_t total = cta_bitmap_prefix(bm, W, keep, s_warp);
     const bool ok = total == nn;
-    const bool in_smem = nn <= cap;
-    if (in_smem) {
-        if (ok)
-            for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) s_acc[i] = VT(0);
-        __syncthreads();
-        cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                           [&](int32_t row, VT prod) {
-                               const int32_t r = bitmap_rank(bm, row);
-                               if (ok) atomicAdd(&s_acc[r], prod);
-                           });
-    } else {
-        VT *gacc = Cval + c0;
-        if (ok)
-            for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) gacc[i] = VT(0);
-        __syncthreads();
-        cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                           [&](int32_t row, VT prod) {
-                               const int32_t r = bitmap_rank(bm, row);
-                               if (ok) atomicAdd(&gacc[r], prod);
-                           });
+    const int32_t ns = (int32_t)(nn < cap ? nn : cap);
+    VT *gacc = Cval + c0;
+    if (ok) {
+        for (int32_t i = threadIdx.x; i < ns; i += blockDim.x) s_acc[i] = VT(0);
+        for (int64_t i = ns + threadIdx.x; i < nn; i += blockDim.x) gacc[i] = VT(0);
     }
+    __syncthreads();
+    cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                       [&](int32_t row, VT prod) {
+                           const int32_t r = bitmap_rank(bm, row);
+                           if (ok) {
+                               if (r < ns) atomicAdd(&s_acc[r], prod);
+                               else atomicAdd(&gacc[r], prod);
+                           }
+                       });
     cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int64_t rank) {
         if (ok) {
             Crow[c0 + rank] = row;
-            if (in_smem) Cval[c0 + rank] = s_acc[rank];
+            if (rank < ns) Cval[c0 + rank] = s_acc[rank];
         }
     });
     __syncthreads();

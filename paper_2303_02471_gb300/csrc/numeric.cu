@@ -188,9 +188,10 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
     int64_t cap = (int64_t)(room / sizeof(VT));
     if (cap > maxnnz) cap = maxnnz;
     // Double sums go to C in place: on GB300 a walk that adds with RED.F64
-    // into L2-resident C runs about 1.3x the products per SM-second of one
-    // that adds with shared-memory f64 atomics, and the extraction then copies
-    // no values.  Float sums stay in shared memory (native f32 atomics).
+    // into L2-resident C takes about 1.3x the products per SM-second of one
+    // that adds with shared-memory f64 atomics (also when the first positions
+    // of a column stay in shared memory), and the extraction then copies no
+    // values.  Float sums stay in shared memory (native f32 atomics).
     if (sizeof(VT) == 8) cap = 0;
     g.cap = cap;
     g.smem = base + (size_t)cap * sizeof(VT);
