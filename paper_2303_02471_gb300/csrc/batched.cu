@@ -247,7 +247,8 @@ __device__ __forceinline__ void bnum_cta(const BTask &b, const BProb &P, int64_t
         for (int64_t i = threadIdx.x; i < W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
         __syncthreads();
         const bool ok = num_dense_column<VT>(prob_ops<VT>(P), (int32_t)j, c0, nn, bm, W, nullptr, acc,
-                                             b.cap_dense, w, s_warp, s_occ, P.Crow, static_cast<VT *>(P.Cval));
+                                             b.cap_dense, w, s_warp, s_occ, P.Crow, static_cast<VT *>(P.Cval),
+                                             []() {});
         if (!ok && threadIdx.x == 0) set_error(b.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + bin, j);
         return;
     }

@@ -238,13 +238,14 @@ __device__ __forceinline__ bool num_cta_column(const TOps<VT> &o, int32_t j, int
 // column, and the rows are written in ascending order.  The sums of the
 // first `cap` positions live in shared memory (s_acc), the others in place
 // in C, so the shared-memory and the L2 atomic units both take products.
-// bm (W uint2) is zero on entry and on return.  Returns false on a count
-// mismatch.
-template <typename VT>
+// bm (W uint2) is zero on entry and on return.  after_prefix() runs on
+// every thread once the flags (and `keep`) have been read.  Returns false on
+// a count mismatch.
+template <typename VT, typename AP>
 __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, int64_t c0, int64_t nn, uint2 *bm,
                                                  int64_t W, const uint32_t *keep, VT *s_acc, int64_t cap,
                                                  const WalkSmem<VT> &w, int64_t *s_warp, unsigned *s_next,
-                                                 int32_t *Crow, VT *Cval) {
+                                                 int32_t *Crow, VT *Cval, AP &&after_prefix) {
     // the previous user of *s_next finished before the caller's last barrier
     if (threadIdx.x == 0) *s_next = blockDim.x >> 5;
     // flags kept from the symbolic phase are read straight into the prefix
@@ -253,6 +254,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
         cta_walk<false, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                             [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
     const int64_t total = cta_bitmap_prefix(bm, W, keep, s_warp);
+    after_prefix();
     const bool ok = total == nn;
     const int32_t ns = (int32_t)(nn < cap ? nn : cap);
     VT *gacc = Cval + c0;

@@ -592,6 +592,49 @@ __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W, bool clea
     }
 }
 
+// ------------------------------------------------------- bulk copies
+// One-shot global -> shared bulk copies (TMA, cp.async.bulk) completing on
+// an mbarrier in shared memory.  Addresses and sizes are multiples of 16
+// bytes; the caller checks.  The wait gives up after kBulkWaitCycles.
+constexpr long long kBulkWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Thread of the caller's choice: orders earlier generic accesses of the CTA
+// (made visible by a barrier) before the copy, arms the barrier with the
+// byte count and starts the copy.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(d), "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+// Waits for the phase of the given parity to complete; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kBulkWaitCycles) return false;
+    }
+}
+
 // ------------------------------------------------------------ launchers
 cudaError_t launch_inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t s);
 int64_t scan_tile_count(int64_t n);
@@ -611,6 +654,7 @@ struct Geo {
     int64_t slots = 0;     // table slots per CTA (CTA hash bins, global bin)
     bool bm_global = false;  // dense flags bitmap in global scratch
     int64_t cap = 0;       // dense bin: values kept in shared memory up to this nnz
+    bool prefetch = false;   // dense bin: next column's kept flags staged by a bulk copy
 };
 
 // Everything a bin kernel needs, passed by value.

@@ -104,32 +104,70 @@ __global__ void __launch_bounds__(1024, 1) k_num_cta(BinTask t, Operands o, cons
 }
 
 // ------------------------------------------------------------ dense bin
+// With `prefetch`, the flags the symbolic phase kept for the next column are
+// brought into shared memory by a bulk copy issued as soon as the current
+// column's prefix pass has consumed the staging buffer, so the copy overlaps
+// the current column's walk and extraction.
 template <typename VT, bool BSM>
 __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, const int64_t *Ccp, int32_t *Crow,
-                                                    VT *Cval, int64_t cap) {
+                                                    VT *Cval, int64_t cap, int prefetch) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ int64_t s_warp[32];
     __shared__ unsigned s_chunk;
+    __shared__ __align__(8) uint64_t s_bar;
     const WalkSmem<VT> w = carve_walk<VT>(smem);
     const size_t o_walk = walk_smem_bytes<VT>(blockDim.x);
     uint2 *bm = BSM ? reinterpret_cast<uint2 *>(smem + o_walk)
                     : reinterpret_cast<uint2 *>(t.scratch + (size_t)blockIdx.x * t.scratch_stride);
     VT *s_acc = reinterpret_cast<VT *>(smem + o_walk + (BSM ? (size_t)t.W * 8 : 0));
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem + o_walk + (BSM ? (size_t)t.W * 8 : 0) +
+                                                   al16((size_t)cap * sizeof(VT)));
+    const int64_t n_cached = t.cache_cols < t.count ? t.cache_cols : t.count;
+    const unsigned stage_bytes = (unsigned)(t.W * 4);
     for (int64_t i = threadIdx.x; i < t.W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
+    if (threadIdx.x == 0) {
+        if (prefetch) mbar_init(&s_bar, 1);
+        s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
+        if (prefetch && s_col < n_cached) bulk_load(stage, t.flag_cache + (size_t)s_col * t.W, stage_bytes, &s_bar);
+    }
+    __syncthreads();
     const TOps<VT> ops = typed<VT>(o);
+    unsigned phase = 0;
+    bool timed_out = false;
     for (;;) {
-        if (threadIdx.x == 0) s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
-        __syncthreads();
         const int64_t ci = s_col;
         if (ci >= t.count) break;
         const int32_t j = t.cols[ci];
         const int64_t c0 = Ccp[j];
         const int64_t nn = Ccp[j + 1] - c0;
         const uint32_t *keep = ci < t.cache_cols ? t.flag_cache + (size_t)ci * t.W : nullptr;
-        const bool ok = num_dense_column<VT>(ops, j, c0, nn, bm, t.W, keep, s_acc, cap, w, s_warp, &s_chunk, Crow, Cval);
+        if (prefetch && keep) {
+            const bool arrived = mbar_wait(&s_bar, phase);
+            if (__syncthreads_or(!arrived)) {
+                if (threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_TIMEOUT, t.bin, j);
+                timed_out = true;
+                break;
+            }
+            phase ^= 1u;
+            keep = stage;
+        }
+        // after the prefix pass: take the next column and start its copy
+        // (no thread reads s_col again before the column's last barrier)
+        auto next = [&]() {
+            if (threadIdx.x == 0) {
+                s_col = (int64_t)atomicAdd(&t.ctrl->work[t.bin], 1ULL);
+                if (prefetch && s_col < n_cached)
+                    bulk_load(stage, t.flag_cache + (size_t)s_col * t.W, stage_bytes, &s_bar);
+            }
+        };
+        const bool ok = num_dense_column<VT>(ops, j, c0, nn, bm, t.W, keep, s_acc, cap, w, s_warp, &s_chunk, Crow,
+                                             Cval, next);
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
     }
+    // a copy is in flight only after a time-out: wait for it (bounded)
+    // before the CTA's shared memory goes away
+    if (timed_out) mbar_wait(&s_bar, phase);
 }
 
 // ------------------------------------------------------------- launches
@@ -184,7 +222,7 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
     const size_t walk = walk_smem_bytes<VT>(g.threads);
     g.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
     size_t base = walk + (g.bm_global ? 0 : bmb);
-    size_t room = smem_optin > base ? smem_optin - base : 0;
+    const size_t room = smem_optin > base ? (smem_optin - base) & ~size_t(15) : 0;
     int64_t cap = (int64_t)(room / sizeof(VT));
     if (cap > maxnnz) cap = maxnnz;
     // Double sums go to C in place: on GB300 a walk that adds with RED.F64
@@ -194,8 +232,17 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
     // values.  Float sums stay in shared memory (native f32 atomics).
     if (sizeof(VT) == 8) cap = 0;
     g.cap = cap;
-    g.smem = base + (size_t)cap * sizeof(VT);
+    g.smem = base + al16((size_t)cap * sizeof(VT));
     int occ = occupancy(k_num_dense<VT, true>, g.threads, g.smem);
+    // staging buffer for the next column's kept flags: bulk copies need
+    // 16-byte aligned columns (W a multiple of 4); only if it costs no CTA
+    if (!g.bm_global && W % 4 == 0) {
+        const size_t with = g.smem + (size_t)W * 4;
+        if (with <= smem_optin && occupancy(k_num_dense<VT, true>, g.threads, with) >= occ) {
+            g.smem = with;
+            g.prefetch = true;
+        }
+    }
     int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
     if (g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);
     g.grid = (int)std::max<int64_t>(1, grid);
@@ -234,7 +281,7 @@ static cudaError_t launch_numeric_t(const BinTask &t, const Operands &o, const i
     } else {
         auto k = g.bm_global ? k_num_dense<VT, false> : k_num_dense<VT, true>;
         allow_smem(k, g.smem);
-        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.cap);
+        k<<<g.grid, g.threads, g.smem, s>>>(t, o, Ccp, Crow, Cval, g.cap, g.prefetch ? 1 : 0);
     }
     return cudaGetLastError();
 }
