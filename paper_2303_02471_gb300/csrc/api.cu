@@ -286,7 +286,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
         if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     }
     if (P->nB > 0) {
-        const int g = (int)std::min<int64_t>(ceil_div(P->nB, 256), 16 * (int64_t)P->dev.sms);
+        const int g = (int)std::min<int64_t>(ceil_div(P->nB, 8), 16 * (int64_t)P->dev.sms);
         k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->op(), C_colptr, ctrl);
         CK(cudaGetLastError());
     } else {
@@ -313,8 +313,9 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     Operands o{A->colptr, A->rowidx, nullptr, B->colptr, B->rowidx, nullptr};
     for (int b = 1; b < NBINS; ++b) {
         if (!P->host.hist[b]) continue;
-        // the symbolic CTA kernels run best at up to 512 threads (measured)
-        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mA, std::min(c.cta_threads, 512), P->dev.sms,
+        // the symbolic CTA kernels carry no values: CTAs of up to 256 threads,
+        // several per SM, overlap one another's barriers (measured faster)
+        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mA, std::min(c.cta_threads, 256), P->dev.sms,
                                   P->dev.smem_optin,
                                   (int64_t)P->host.maxop[b], c.table_shrink, P->L.scratch_ctas);
         CK(launch_symbolic_bin(P->task(b), o, C_colptr, g, s));

@@ -41,23 +41,30 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
     }
     if (threadIdx.x == 0) s_prod = 0;
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // one warp per column: its B entries are read coalesced and the Z^A_k
+    // loads are independent, so long columns take no serial chain
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long mine = 0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nB; j += stride) {
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nB; j += nwarps) {
         const int64_t p0 = Bcp[j], p1 = Bcp[j + 1];
         int64_t s = 0;
-        for (int64_t p = p0; p < p1; ++p) {
+        for (int64_t p = p0 + lane; p < p1; p += 32) {
             const int32_t k = Brow[p];
             s += Acp[k + 1] - Acp[k];
         }
-        op[j] = s;
-        mine += (unsigned long long)s;
-        const int b = bin_of(s, t, hmax);
-        atomicAdd(&s_hist[b], 1ULL);
-        atomicMax(&s_max[b], (unsigned long long)s);
-        if (s) atomicAdd(&s_binprod[b], (unsigned long long)s);
-        if (p1 > p0) atomicAdd(&s_binb[b], (unsigned long long)(p1 - p0));
-        if (b == BIN_EMPTY) Ccp[j + 1] = 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) {
+            op[j] = s;
+            mine += (unsigned long long)s;
+            const int b = bin_of(s, t, hmax);
+            atomicAdd(&s_hist[b], 1ULL);
+            atomicMax(&s_max[b], (unsigned long long)s);
+            if (s) atomicAdd(&s_binprod[b], (unsigned long long)s);
+            if (p1 > p0) atomicAdd(&s_binb[b], (unsigned long long)(p1 - p0));
+            if (b == BIN_EMPTY) Ccp[j + 1] = 0;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) Ccp[0] = 0;
     for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, d);
