@@ -19,6 +19,31 @@ struct BinOffsets { int64_t v[NBINS + 1]; };
 // Products a lane of a group walk gathers before it consumes them.
 constexpr int kGroupBatch = 2;
 
+// ------------------------------------------------------ L2 residency
+// Gathers of A's rows and values carry an L2 evict-last policy: every column
+// of B reads A's columns again, while C (and the kept flags) stream through
+// L2 once and would otherwise push A out.
+__device__ __forceinline__ uint64_t keep_policy() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int32_t ld_keep(const int32_t *a, uint64_t p) {
+    int32_t v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_keep(const float *a, uint64_t p) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_keep(const double *a, uint64_t p) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(p));
+    return v;
+}
+
 // ------------------------------------------------------------ group walk
 // A group of G lanes (G divides 32) walks the products of B entries
 // [p0, p1) in chunks of G entries.  f(row, product) runs once per product
@@ -32,6 +57,7 @@ __device__ __forceinline__ void group_products(unsigned mask, const int64_t *__r
                                                const VT *__restrict__ Bval, int64_t p0, int64_t p1,
                                                F &&f) {
     const int gl = threadIdx.x & (G - 1);
+    const uint64_t pol = keep_policy();
     for (int64_t base = p0; base < p1; base += G) {
         const int64_t p = base + gl;
         int z = 0;
@@ -65,8 +91,8 @@ __device__ __forceinline__ void group_products(unsigned mask, const int64_t *__r
                     if (VALS) bvs[u] = __shfl_sync(mask, bv, s, G);
                     if (q < total) {
                         const int64_t qa = a0s + (q - exs);
-                        rows[u] = Arow[qa];
-                        if (VALS) av[u] = Aval[qa];
+                        rows[u] = ld_keep(Arow + qa, pol);
+                        if (VALS) av[u] = ld_keep(Aval + qa, pol);
                     }
                 }
             }
@@ -194,6 +220,7 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
     const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const uint64_t pol = keep_policy();
     for (int64_t base = p0; base < p1; base += T) {
         const int64_t p = base + threadIdx.x;
         int z = 0;
@@ -263,9 +290,9 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                             const int idx = ((win + u - e_key) << 5) + lane;
                             if (idx < e_z) {
                                 const int64_t qa = e_a0 + idx;
-                                rows[u] = Arow[qa];
+                                rows[u] = ld_keep(Arow + qa, pol);
                                 if (VALS) {
-                                    av[u] = Aval[qa];
+                                    av[u] = ld_keep(Aval + qa, pol);
                                     bvs[u] = e_b;
                                 }
                             }
@@ -310,9 +337,9 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                             const int q = qf + lane;
                             if (q < ZS) {
                                 const int64_t qa = sa[own] + (q - sk[own]);
-                                rows[u] = Arow[qa];
+                                rows[u] = ld_keep(Arow + qa, pol);
                                 if (VALS) {
-                                    av[u] = Aval[qa];
+                                    av[u] = ld_keep(Aval + qa, pol);
                                     bvs[u] = sb[own];
                                 }
                             }
