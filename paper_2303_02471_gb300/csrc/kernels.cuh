@@ -580,40 +580,54 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, const
 // row in the sorted column (bm[..].y must hold the prefix counts).  Warps
 // take chunks of 32 words, the first one by warp index and the next ones
 // from the shared counter *s_next, which must hold the number of warps
-// before a barrier that precedes the call.  Each lane visits up to
-// kVisitLight bits of its own word; the rest of a fuller word is visited by
-// the whole warp, one lane per bit, so a dense stretch of rows (the hub rows
-// of a power-law matrix) costs no single lane many serial steps, and its
-// stores are coalesced.  Clears the bits when `clear`.  No barrier inside.
-constexpr int kVisitLight = 4;
+// before a barrier that precedes the call.  In a chunk whose words hold at
+// most kVisitLight bits each, every lane visits its own word; otherwise the
+// warp expands the chunk's S bits 32 ranks at a time: lane l takes rank
+// y0 + o (o = round * 32 + l), finds the word holding it by a search over
+// the words' prefix counts and the bit by select_bit.  So a dense stretch of
+// rows (the hub rows of a power-law matrix) costs no lane serial steps and
+// its stores are coalesced.  Clears the bits when `clear`.  No barrier
+// inside.
+constexpr int kVisitLight = 2;
 
 template <typename F>
 __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W, bool clear, unsigned *s_next, F &&f) {
     const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
     const int64_t nchunks = (W + 31) >> 5;
     int64_t c = threadIdx.x >> 5;
     while (c < nchunks) {
         const int64_t wd = (c << 5) + lane;
         const uint2 v = wd < W ? bm[wd] : make_uint2(0u, 0u);
         if (clear && v.x) bm[wd].x = 0u;
-        const int32_t row0 = (int32_t)(wd << 5);
-        uint32_t bits = v.x;
-        int64_t rank = v.y;
-        for (int i = 0; i < kVisitLight && bits; ++i) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1u;
-            f(row0 + b, rank++);
-        }
-        unsigned heavy = __ballot_sync(0xffffffffu, bits != 0u);
-        while (heavy) {
-            const int s = __ffs(heavy) - 1;
-            heavy &= heavy - 1u;
-            const uint32_t hb = __shfl_sync(0xffffffffu, v.x, s);
-            const uint32_t hy = __shfl_sync(0xffffffffu, v.y, s);
-            const int k = __popc(hb & below);
-            if (((hb >> lane) & 1u) && k >= kVisitLight)
-                f((int32_t)((((c << 5) + s) << 5) + lane), (int64_t)hy + k);
+        const int cnt = __popc(v.x);
+        const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+        if (maxc <= kVisitLight) {
+            const int32_t row0 = (int32_t)(wd << 5);
+            uint32_t bits = v.x;
+            int64_t rank = v.y;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                f(row0 + b, rank++);
+            }
+        } else {
+            // lane 0's word always exists; words past W never hold rank o < S
+            const uint32_t y0 = __shfl_sync(0xffffffffu, v.y, 0);
+            const int excl = wd < W ? (int)(v.y - y0) : 0x3fffffff;
+            const int S = (int)__reduce_max_sync(0xffffffffu, wd < W ? (unsigned)(excl + cnt) : 0u);
+            const int32_t crow = (int32_t)(c << 10);
+            for (int o0 = 0; o0 < S; o0 += 32) {
+                const int o = o0 + lane;
+                int sl = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int ex = __shfl_sync(0xffffffffu, excl, sl + step);
+                    if (ex <= o) sl += step;
+                }
+                const uint32_t bw = __shfl_sync(0xffffffffu, v.x, sl);
+                const int k = o - __shfl_sync(0xffffffffu, excl, sl);
+                if (o < S) f(crow + (sl << 5) + select_bit(bw, k), (int64_t)y0 + o);
+            }
         }
         unsigned nc = 0;
         if (lane == 0) nc = atomicAdd(s_next, 1u);
