@@ -271,10 +271,11 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                else atomicAdd(&gacc[r], prod);
                            }
                        });
-    cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int64_t rank) {
+    int32_t *crow = Crow + c0;
+    cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) {
         if (ok) {
-            Crow[c0 + rank] = row;
-            if (rank < ns) Cval[c0 + rank] = s_acc[rank];
+            crow[rank] = row;
+            if (rank < ns) gacc[rank] = s_acc[rank];
         }
     });
     __syncthreads();

@@ -268,44 +268,69 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                     const int mid = (li + hi + 1) >> 1;
                     if (w.key[mid] <= win0) li = mid; else hi = mid - 1;
                 }
-                // the owner is the same for every lane of a window: keep its
-                // entry in registers and reload only when it advances
-                int e_key = w.key[li], e_z = w.z[li];
-                int64_t e_a0 = w.a0[li];
-                VT e_b = VALS ? w.bv[li] : VT(0);
-                int next_key = li + 1 < nl ? w.key[li + 1] : 0x7fffffff;
-                for (int win = win0; win < e1; win += UB) {
-                    int32_t rows[UB];
-                    VT av[UB], bvs[UB];
-#pragma unroll
-                    for (int u = 0; u < UB; ++u) {
-                        rows[u] = -1;
-                        if (win + u < e1) {
-                            while (next_key <= win + u) {
-                                ++li;
-                                e_key = next_key;
-                                e_z = w.z[li];
-                                e_a0 = w.a0[li];
-                                if (VALS) e_b = w.bv[li];
-                                next_key = li + 1 < nl ? w.key[li + 1] : 0x7fffffff;
-                            }
-                            const int idx = ((win + u - e_key) << 5) + lane;
+                if constexpr (UB == 1) {
+                    // entry by entry: the entry's windows in [win, e_end)
+                    // are one warp-uniform loop over idx = window * 32 + lane
+                    // of its A column
+                    for (int win = win0; win < e1; ++li) {
+                        const int e_key = w.key[li], e_z = w.z[li];
+                        const int nk = li + 1 < nl ? w.key[li + 1] : 0x7fffffff;
+                        const int e_end = nk < e1 ? nk : e1;
+                        const int64_t a0 = w.a0[li];
+                        const int32_t *rp = Arow + a0;
+                        const VT *vp = VALS ? Aval + a0 : nullptr;
+                        const VT b = VALS ? w.bv[li] : VT(0);
+                        const int i1 = (e_end - e_key) << 5;
+                        for (int idx = ((win - e_key) << 5) + lane; idx < i1; idx += 32) {
                             if (idx < e_z) {
-                                const int64_t qa = e_a0 + idx;
-                                rows[u] = ld_keep(Arow + qa, pol);
-                                if (VALS) {
-                                    av[u] = ld_keep(Aval + qa, pol);
-                                    bvs[u] = e_b;
+                                const int32_t row = ld_keep(rp + idx, pol);
+                                VT prod = VT(0);
+                                if (VALS) prod = ld_keep(vp + idx, pol) * b;
+                                f(row, prod);
+                            }
+                        }
+                        win = e_end;
+                    }
+                } else {
+                    // the owner is the same for every lane of a window: keep its
+                    // entry in registers and reload only when it advances
+                    int e_key = w.key[li], e_z = w.z[li];
+                    int64_t e_a0 = w.a0[li];
+                    VT e_b = VALS ? w.bv[li] : VT(0);
+                    int next_key = li + 1 < nl ? w.key[li + 1] : 0x7fffffff;
+                    for (int win = win0; win < e1; win += UB) {
+                        int32_t rows[UB];
+                        VT av[UB], bvs[UB];
+    #pragma unroll
+                        for (int u = 0; u < UB; ++u) {
+                            rows[u] = -1;
+                            if (win + u < e1) {
+                                while (next_key <= win + u) {
+                                    ++li;
+                                    e_key = next_key;
+                                    e_z = w.z[li];
+                                    e_a0 = w.a0[li];
+                                    if (VALS) e_b = w.bv[li];
+                                    next_key = li + 1 < nl ? w.key[li + 1] : 0x7fffffff;
+                                }
+                                const int idx = ((win + u - e_key) << 5) + lane;
+                                if (idx < e_z) {
+                                    const int64_t qa = e_a0 + idx;
+                                    rows[u] = ld_keep(Arow + qa, pol);
+                                    if (VALS) {
+                                        av[u] = ld_keep(Aval + qa, pol);
+                                        bvs[u] = e_b;
+                                    }
                                 }
                             }
                         }
-                    }
-#pragma unroll
-                    for (int u = 0; u < UB; ++u) {
-                        if (rows[u] >= 0) {
-                            VT prod = VT(0);
-                            if (VALS) prod = av[u] * bvs[u];
-                            f(rows[u], prod);
+    #pragma unroll
+                        for (int u = 0; u < UB; ++u) {
+                            if (rows[u] >= 0) {
+                                VT prod = VT(0);
+                                if (VALS) prod = av[u] * bvs[u];
+                                f(rows[u], prod);
+                            }
                         }
                     }
                 }
@@ -591,20 +616,22 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, const
 constexpr int kVisitLight = 2;
 
 template <typename F>
-__device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W, bool clear, unsigned *s_next, F &&f) {
+__device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W64, bool clear, unsigned *s_next, F &&f) {
+    // m < 2^31, so words, chunks and ranks all fit 32-bit indices
+    const int W = (int)W64;
     const int lane = threadIdx.x & 31;
-    const int64_t nchunks = (W + 31) >> 5;
-    int64_t c = threadIdx.x >> 5;
+    const int nchunks = (W + 31) >> 5;
+    int c = threadIdx.x >> 5;
     while (c < nchunks) {
-        const int64_t wd = (c << 5) + lane;
+        const int wd = (c << 5) + lane;
         const uint2 v = wd < W ? bm[wd] : make_uint2(0u, 0u);
         if (clear && v.x) bm[wd].x = 0u;
         const int cnt = __popc(v.x);
         const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
         if (maxc <= kVisitLight) {
-            const int32_t row0 = (int32_t)(wd << 5);
+            const int32_t row0 = wd << 5;
             uint32_t bits = v.x;
-            int64_t rank = v.y;
+            int32_t rank = (int32_t)v.y;
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1u;
@@ -615,7 +642,7 @@ __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W, bool clea
             const uint32_t y0 = __shfl_sync(0xffffffffu, v.y, 0);
             const int excl = wd < W ? (int)(v.y - y0) : 0x3fffffff;
             const int S = (int)__reduce_max_sync(0xffffffffu, wd < W ? (unsigned)(excl + cnt) : 0u);
-            const int32_t crow = (int32_t)(c << 10);
+            const int32_t crow = c << 10;
             for (int o0 = 0; o0 < S; o0 += 32) {
                 const int o = o0 + lane;
                 int sl = 0;
@@ -626,12 +653,12 @@ __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W, bool clea
                 }
                 const uint32_t bw = __shfl_sync(0xffffffffu, v.x, sl);
                 const int k = o - __shfl_sync(0xffffffffu, excl, sl);
-                if (o < S) f(crow + (sl << 5) + select_bit(bw, k), (int64_t)y0 + o);
+                if (o < S) f(crow + (sl << 5) + select_bit(bw, k), (int32_t)y0 + o);
             }
         }
         unsigned nc = 0;
         if (lane == 0) nc = atomicAdd(s_next, 1u);
-        c = (int64_t)__shfl_sync(0xffffffffu, nc, 0);
+        c = (int)__shfl_sync(0xffffffffu, nc, 0);
     }
 }
 
