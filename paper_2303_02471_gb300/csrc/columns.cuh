@@ -255,31 +255,39 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                             [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
     const int64_t total = cta_bitmap_prefix(bm, W, keep, s_warp);
     after_prefix();
-    const bool ok = total == nn;
+    if (total != nn) {
+        // the pattern changed since the symbolic phase: the caller reports
+        // it and the column is left unwritten
+        for (int i = threadIdx.x; i < (int)W; i += blockDim.x) bm[i].x = 0u;
+        __syncthreads();
+        return false;
+    }
+    // nn <= m < 2^31: positions are 32-bit
+    const int32_t n32 = (int32_t)nn;
     const int32_t ns = (int32_t)(nn < cap ? nn : cap);
     VT *gacc = Cval + c0;
-    if (ok) {
-        for (int32_t i = threadIdx.x; i < ns; i += blockDim.x) s_acc[i] = VT(0);
-        for (int64_t i = ns + threadIdx.x; i < nn; i += blockDim.x) gacc[i] = VT(0);
-    }
+    int32_t *crow = Crow + c0;
+    for (int32_t i = threadIdx.x; i < ns; i += blockDim.x) s_acc[i] = VT(0);
+    for (int32_t i = ns + threadIdx.x; i < n32; i += blockDim.x) gacc[i] = VT(0);
     __syncthreads();
-    cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
-                       [&](int32_t row, VT prod) {
-                           const int32_t r = bitmap_rank(bm, row);
-                           if (ok) {
+    if (ns == 0) {  // every sum in C (uniform over the CTA)
+        cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                           [&](int32_t row, VT prod) { atomicAdd(&gacc[bitmap_rank(bm, row)], prod); });
+        cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) { crow[rank] = row; });
+    } else {
+        cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
+                           [&](int32_t row, VT prod) {
+                               const int32_t r = bitmap_rank(bm, row);
                                if (r < ns) atomicAdd(&s_acc[r], prod);
                                else atomicAdd(&gacc[r], prod);
-                           }
-                       });
-    int32_t *crow = Crow + c0;
-    cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) {
-        if (ok) {
+                           });
+        cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) {
             crow[rank] = row;
             if (rank < ns) gacc[rank] = s_acc[rank];
-        }
-    });
+        });
+    }
     __syncthreads();
-    return ok;
+    return true;
 }
 
 // ================================================================ backward

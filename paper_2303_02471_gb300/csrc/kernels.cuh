@@ -533,19 +533,20 @@ __device__ __forceinline__ int32_t bitmap_rank(const uint2 *bm, int32_t row) {
 // and the four rounds' counts share one packed 64-bit warp scan (16 bits per
 // round; a round counts at most 2048 bits).  Warps cover consecutive runs;
 // one block-wide offset per pass.  Every thread must call it.
-__device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, const uint32_t *src, int64_t *s_warp) {
+__device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W64, const uint32_t *src, int64_t *s_warp) {
+    const int W = (int)W64;  // m < 2^31: words and counts are 32-bit
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // pair loads and 16-byte stores need aligned starts (uniform over the CTA)
     const bool vec = (reinterpret_cast<uintptr_t>(bm) & 15) == 0 &&
                      (src == nullptr || (reinterpret_cast<uintptr_t>(src) & 7) == 0);
-    int64_t carry = 0;
-    for (int64_t r0 = 0; r0 < W; r0 += (int64_t)256 * nw) {
-        const int64_t wb = r0 + (int64_t)warp * 256 + 2 * lane;
+    int carry = 0;
+    for (int r0 = 0; r0 < W; r0 += 256 * nw) {
+        const int wb = r0 + warp * 256 + 2 * lane;
         uint32_t b[8];
         uint64_t packed = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int64_t w = wb + 64 * k;
+            const int w = wb + 64 * k;
             if (vec && w + 1 < W) {
                 if (src) {
                     const uint2 u = *reinterpret_cast<const uint2 *>(src + w);
@@ -569,23 +570,22 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, const
             if (lane >= d) packed += o;
         }
         const uint64_t tot = __shfl_sync(0xffffffffu, packed, 31);
-        const int64_t wsum = (int64_t)((tot & 0xffff) + ((tot >> 16) & 0xffff) + ((tot >> 32) & 0xffff) + (tot >> 48));
+        const int wsum = (int)((tot & 0xffff) + ((tot >> 16) & 0xffff) + ((tot >> 32) & 0xffff) + (tot >> 48));
         if (lane == 31) s_warp[warp] = wsum;
         __syncthreads();
-        int64_t tw = lane < nw ? s_warp[lane] : 0;
+        int tw = lane < nw ? (int)s_warp[lane] : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int64_t o = __shfl_up_sync(0xffffffffu, tw, d);
+            const int o = __shfl_up_sync(0xffffffffu, tw, d);
             if (lane >= d) tw += o;
         }
-        const int64_t before = __shfl_sync(0xffffffffu, tw, warp > 0 ? warp - 1 : 0);
-        const int64_t pass = __shfl_sync(0xffffffffu, tw, nw - 1);
-        int64_t base = carry + (warp > 0 ? before : 0);
+        const int before = __shfl_sync(0xffffffffu, tw, warp > 0 ? warp - 1 : 0);
+        const int pass = __shfl_sync(0xffffffffu, tw, nw - 1);
+        int base = carry + (warp > 0 ? before : 0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int64_t w = wb + 64 * k;
-            const uint32_t y0 = (uint32_t)(base + (int64_t)((packed >> (16 * k)) & 0xffff) -
-                                           (int64_t)((mine >> (16 * k)) & 0xffff));
+            const int w = wb + 64 * k;
+            const uint32_t y0 = (uint32_t)(base + (int)((packed >> (16 * k)) & 0xffff) - (int)((mine >> (16 * k)) & 0xffff));
             const uint32_t y1 = y0 + (uint32_t)__popc(b[2 * k]);
             if (vec && w + 1 < W) {
                 *reinterpret_cast<uint4 *>(bm + w) = make_uint4(b[2 * k], y0, b[2 * k + 1], y1);
@@ -593,7 +593,7 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W, const
                 if (w < W) bm[w] = make_uint2(b[2 * k], y0);
                 if (w + 1 < W) bm[w + 1] = make_uint2(b[2 * k + 1], y1);
             }
-            base += (int64_t)((tot >> (16 * k)) & 0xffff);
+            base += (int)((tot >> (16 * k)) & 0xffff);
         }
         carry += pass;
         __syncthreads();
