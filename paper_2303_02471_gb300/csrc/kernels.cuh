@@ -215,10 +215,10 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                                          const VT *__restrict__ Aval, const int32_t *__restrict__ Brow,
                                          const VT *__restrict__ Bval, int64_t p0, int64_t p1,
                                          const WalkSmem<VT> &w, F &&f) {
-    // windows gathered per lane before any is consumed; with double values
-    // one at a time measured fastest (the warps of two CTAs per SM give the
-    // memory parallelism, and the loop stays small)
-    constexpr int UB = (VALS && sizeof(VT) == 8) ? 1 : kWalkBatch;
+    // windows gathered per lane before any is consumed: with values, one at
+    // a time measured fastest (the warps of two CTAs per SM give the memory
+    // parallelism, and the loop stays small enough not to spill)
+    constexpr int UB = VALS ? 1 : kWalkBatch;
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
     const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
