@@ -92,16 +92,33 @@ __device__ __forceinline__ int64_t sym_cta_column(const TOps<float> &o, int32_t 
 __device__ __forceinline__ int64_t sym_dense_column(const TOps<float> &o, int32_t j, uint32_t *bm, int64_t W,
                                                     uint32_t *keep, const WalkSmem<float> &w,
                                                     unsigned long long *s_cnt) {
+    // (a dense column has B entries, so the walk's barriers order this reset
+    // before every add below)
     if (threadIdx.x == 0) *s_cnt = 0;
-    unsigned long long cnt = 0;
+    // the OR's old value is not needed: the rows are counted afterwards with
+    // popcounts while the words are copied out and cleared
     cta_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
-                           [&](int32_t row, float) {
-                               const uint32_t bit = 1u << (row & 31);
-                               cnt += (atomicOr(&bm[row >> 5], bit) & bit) ? 0 : 1;
-                           });
-    for (int64_t i = threadIdx.x; i < W; i += blockDim.x) {
-        if (keep) keep[i] = bm[i];
-        bm[i] = 0u;
+                           [&](int32_t row, float) { atomicOr(&bm[row >> 5], 1u << (row & 31)); });
+    unsigned long long cnt = 0;
+    const bool vec = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(bm) & 15) == 0 &&
+                     (!keep || (reinterpret_cast<uintptr_t>(keep) & 15) == 0);
+    if (vec) {
+        uint4 *b4 = reinterpret_cast<uint4 *>(bm);
+        uint4 *k4 = reinterpret_cast<uint4 *>(keep);
+        const int W4 = (int)(W >> 2);
+        for (int i = threadIdx.x; i < W4; i += blockDim.x) {
+            const uint4 v = b4[i];
+            cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            if (keep) k4[i] = v;
+            b4[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    } else {
+        for (int i = threadIdx.x; i < (int)W; i += blockDim.x) {
+            const uint32_t v = bm[i];
+            cnt += __popc(v);
+            if (keep) keep[i] = v;
+            bm[i] = 0u;
+        }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
