@@ -315,7 +315,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
         if (!P->host.hist[b]) continue;
         // the symbolic CTA kernels carry no values: CTAs of up to 256 threads,
         // several per SM, overlap one another's barriers (measured faster)
-        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mA, std::min(c.cta_threads, 256), P->dev.sms,
+        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mA, std::min(c.cta_threads, kSymCtaThreads), P->dev.sms,
                                   P->dev.smem_optin,
                                   (int64_t)P->host.maxop[b], c.table_shrink, P->L.scratch_ctas);
         CK(launch_symbolic_bin(P->task(b), o, C_colptr, g, s));

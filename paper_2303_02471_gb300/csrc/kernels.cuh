@@ -19,6 +19,9 @@ struct BinOffsets { int64_t v[NBINS + 1]; };
 // Products a lane of a group walk gathers before it consumes them.
 constexpr int kGroupBatch = 2;
 
+// Threads per CTA of the symbolic CTA-level kernels (several CTAs per SM).
+constexpr int kSymCtaThreads = 256;
+
 // ------------------------------------------------------ L2 residency
 // Gathers of A's rows and values carry an L2 evict-last policy: every column
 // of B reads A's columns again, while C (and the kept flags) stream through
