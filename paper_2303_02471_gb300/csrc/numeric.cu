@@ -34,7 +34,7 @@ static int occupancy(K kernel, int threads, size_t smem) {
 
 // ------------------------------------------------- warp-group hash bins
 template <int G, int R, typename VT>
-__global__ void __launch_bounds__(kGroupThreads, 1) k_num_group(BinTask t, Operands o, const int64_t *Ccp,
+__global__ void __launch_bounds__(kGroupThreads, 4) k_num_group(BinTask t, Operands o, const int64_t *Ccp,
                                                              int32_t *Crow, VT *Cval) {
     constexpr int H = 2 * G * R;
     constexpr int NG = kGroupThreads / G;
