@@ -297,8 +297,9 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A,
  * C_rowidx, C_values: host arrays of nb device pointers (nnzC[i] entries).
  * use_graph: nonzero captures the launch (with its counter reset) into a CUDA
  * graph on the first call and replays it while the pointers stay the same
- * (re-captured when they change); the stream must then not be the legacy
- * default stream.  Asynchronous. */
+ * (re-captured when they change).  The legacy default stream (0) cannot be
+ * captured: there the launch runs directly, as with use_graph = 0.
+ * Asynchronous. */
 spg_status spgemm_batched_numeric(spg_bplan *plan, const spg_csc *A,
                                   const spg_csc *B, const int64_t *C_colptr,
                                   int32_t *const *C_rowidx,

@@ -25,7 +25,7 @@ INF = (1 << 63) - 1
 DEFAULT_GRID = {
     "t": [257, 513, 1025, 2049, None],
     "hash_cta_max": [2048, 8192],
-    "cta_threads": [256, 512],
+    "cta_threads": [128, 256, 512],
 }
 
 

@@ -235,7 +235,7 @@ __device__ __forceinline__ void bnum_group(const BTask &b, const BProb &P, int64
 }
 
 template <typename VT>
-__device__ __forceinline__ void bnum_cta(const BTask &b, const BProb &P, int64_t j, unsigned char *smem,
+__device__ __noinline__ void bnum_cta(const BTask &b, const BProb &P, int64_t j, unsigned char *smem,
                                          int64_t *s_warp, unsigned *s_occ, int bin) {
     const WalkSmem<VT> w = carve_walk<VT>(smem);
     unsigned char *p = smem + walk_smem_bytes<VT>(blockDim.x);
@@ -246,9 +246,11 @@ __device__ __forceinline__ void bnum_cta(const BTask &b, const BProb &P, int64_t
         VT *acc = reinterpret_cast<VT *>(p + al16((size_t)b.Wmax * 8));
         for (int64_t i = threadIdx.x; i < W; i += blockDim.x) bm[i] = make_uint2(0u, 0u);
         __syncthreads();
-        const bool ok = num_dense_column<VT>(prob_ops<VT>(P), (int32_t)j, c0, nn, bm, W, nullptr, acc,
-                                             b.cap_dense, w, s_warp, s_occ, P.Crow, static_cast<VT *>(P.Cval),
-                                             []() {});
+        // double sums go to C in place (RED.F64 beats shared-memory f64
+        // atomics on GB300); float sums stay in shared memory
+        const int64_t cap = sizeof(VT) == 8 ? 0 : b.cap_dense;
+        const bool ok = num_dense_column<VT>(prob_ops<VT>(P), (int32_t)j, c0, nn, bm, W, nullptr, acc, cap, w,
+                                             s_warp, s_occ, P.Crow, static_cast<VT *>(P.Cval), []() {});
         if (!ok && threadIdx.x == 0) set_error(b.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + bin, j);
         return;
     }
@@ -321,7 +323,7 @@ __device__ __forceinline__ void bgroup_item(const BTask &b, int bin, int64_t idx
     }
 }
 
-__device__ __forceinline__ void bgroup_dispatch(const BTask &b, int bin, int64_t idx, unsigned char *smem, int phase) {
+__device__ __noinline__ void bgroup_dispatch(const BTask &b, int bin, int64_t idx, unsigned char *smem, int phase) {
     switch (bin - BIN_WARP0) {
         case 0: bgroup_item<warp_bin_G(0), warp_bin_R(0)>(b, bin, idx, smem, phase); break;
         case 1: bgroup_item<warp_bin_G(1), warp_bin_R(1)>(b, bin, idx, smem, phase); break;
@@ -333,7 +335,10 @@ __device__ __forceinline__ void bgroup_dispatch(const BTask &b, int bin, int64_t
 }
 
 // phase 0: symbolic, 1: numeric, 2: backward.  One launch per phase.
-__global__ void __launch_bounds__(512, 2) k_batched(BTask b, BItems it, int phase) {
+// One instantiation per phase, so each carries only its own code paths
+// (and registers).
+template <int phase>
+__global__ void __launch_bounds__(512, 2) k_batched(BTask b, BItems it) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_item;
     __shared__ int64_t s_warp[32];
@@ -575,6 +580,12 @@ size_t phase_smem(const spg_bplan &P, int phase, int threads, int64_t &cap_cta, 
     return need;
 }
 
+const void *batched_kernel(int phase) {
+    return phase == 0 ? reinterpret_cast<const void *>(k_batched<0>)
+                      : phase == 1 ? reinterpret_cast<const void *>(k_batched<1>)
+                                   : reinterpret_cast<const void *>(k_batched<2>);
+}
+
 // Launch shape of a phase; the function attribute is set here, outside any
 // stream capture.
 struct PhaseLaunch {
@@ -594,11 +605,12 @@ spg_status prepare_phase(spg_bplan &P, int phase, PhaseLaunch &L) {
     L.b.cap_dense = cap_dense;
     L.b.cap_sym = cap_sym;
     L.it = make_items(P, threads);
-    if (cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const void *kfn = batched_kernel(phase);
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)std::max<size_t>(L.smem, 1)) != cudaSuccess)
         return SPG_ERR_CUDA;
     int occ = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, threads, L.smem) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, L.smem) != cudaSuccess || occ < 1)
         occ = 1;
     L.grid = (int)std::min<int64_t>(std::max<int64_t>(L.it.nitems, 1), (int64_t)occ * P.sms);
     return SPG_OK;
@@ -608,7 +620,9 @@ spg_status prepare_phase(spg_bplan &P, int phase, PhaseLaunch &L) {
 spg_status enqueue_phase(const spg_bplan &P, int phase, const PhaseLaunch &L, cudaStream_t s) {
     if (cudaMemsetAsync(L.b.counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return SPG_ERR_CUDA;
     if (L.it.nitems == 0) return SPG_OK;
-    k_batched<<<L.grid, P.threads, L.smem, s>>>(L.b, L.it, phase);
+    if (phase == 0) k_batched<0><<<L.grid, P.threads, L.smem, s>>>(L.b, L.it);
+    else if (phase == 1) k_batched<1><<<L.grid, P.threads, L.smem, s>>>(L.b, L.it);
+    else k_batched<2><<<L.grid, P.threads, L.smem, s>>>(L.b, L.it);
     return cudaGetLastError() == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }
 
@@ -810,7 +824,8 @@ spg_status spgemm_batched_numeric(spg_bplan *P, const spg_csc *A, const spg_csc 
                             cudaMemcpyHostToDevice, s) != cudaSuccess)
             return SPG_ERR_CUDA;
     }
-    if (!use_graph) return launch_phase(*P, 1, s);
+    // the legacy default stream cannot be captured: launch directly there
+    if (!use_graph || s == nullptr || s == cudaStreamLegacy) return launch_phase(*P, 1, s);
     if (!same) {
         // (re)capture: counter reset + the persistent launch
         if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }

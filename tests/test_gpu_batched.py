@@ -73,6 +73,32 @@ def test_batched_graph_replay():
         assert_matches_oracle(C, A, B, ref=ref)
 
 
+def test_batched_graph_request_on_default_stream_launches_directly():
+    # the legacy default stream cannot be captured; the launch still runs
+    import torch
+    from paper_2303_02471_gb300 import ops
+    pairs = synth.batch_pairs(12, seed=8, n_scale=0.05)
+    As, Bs = _upload_pairs(pairs)
+    assert torch.cuda.current_stream().cuda_stream == 0
+    plan = ops.spgemm_batched_symbolic(As, Bs)
+    Cs = ops.spgemm_batched_numeric(plan, As, Bs, True)
+    Cs = ops.spgemm_batched_numeric(plan, As, Bs, True)
+    plan.check()
+    for (A, B), C in zip(pairs, Cs):
+        assert_matches_oracle(C, A, B)
+
+
+@pytest.mark.parametrize("threads", [128, 256])
+def test_batched_small_ctas_match_oracle(threads):
+    from paper_2303_02471_gb300 import ops
+    pairs = synth.batch_pairs(16, seed=9, n_scale=0.05)
+    As, Bs = _upload_pairs(pairs)
+    Cs, plan = ops.spgemm_batched(As, Bs, ops.Config(cta_threads=threads))
+    plan.check()
+    for (A, B), C in zip(pairs, Cs):
+        assert_matches_oracle(C, A, B)
+
+
 def test_batched_backward_matches_plain():
     import torch
     from paper_2303_02471_gb300 import ops
