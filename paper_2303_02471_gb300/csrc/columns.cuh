@@ -264,7 +264,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                                  const WalkSmem<VT> &w, int64_t *s_warp, unsigned *s_next,
                                                  int32_t *Crow, VT *Cval, AP &&after_prefix) {
     // the previous user of *s_next finished before the caller's last barrier
-    if (threadIdx.x == 0) *s_next = blockDim.x >> 5;
+    if (threadIdx.x == 0) *s_next = (blockDim.x >> 5) * kVisitGroup;
     // flags kept from the symbolic phase are read straight into the prefix
     // pass; otherwise the walk sets them again
     if (!keep)

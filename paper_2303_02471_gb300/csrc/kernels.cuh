@@ -606,17 +606,20 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W64, con
 
 // Visits the set bits of bm[0..W) with f(row, rank), rank = position of the
 // row in the sorted column (bm[..].y must hold the prefix counts).  Warps
-// take chunks of 32 words, the first one by warp index and the next ones
-// from the shared counter *s_next, which must hold the number of warps
-// before a barrier that precedes the call.  In a chunk whose words hold at
-// most kVisitLight bits each, every lane visits its own word; otherwise the
-// warp expands the chunk's S bits 32 ranks at a time: lane l takes rank
+// take groups of kVisitGroup chunks of 32 words, the first group by warp
+// index and the next ones from the shared counter *s_next, which must hold
+// kVisitGroup * (number of warps) before a barrier that precedes the call
+// (one shared atomic per 4096 rows).  In a chunk whose words hold at most
+// kVisitLight bits each, every lane visits its own word; otherwise the warp
+// expands the chunk's S bits 32 ranks at a time: lane l takes rank
 // y0 + o (o = round * 32 + l), finds the word holding it by a search over
 // the words' prefix counts and the bit by select_bit.  So a dense stretch of
 // rows (the hub rows of a power-law matrix) costs no lane serial steps and
 // its stores are coalesced.  Clears the bits when `clear`.  No barrier
 // inside.
 constexpr int kVisitLight = 2;
+// Chunks of 32 words a warp takes per grab in cta_bitmap_visit.
+constexpr int kVisitGroup = 4;
 
 template <typename F>
 __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W64, bool clear, unsigned *s_next, F &&f) {
@@ -624,8 +627,9 @@ __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W64, bool cl
     const int W = (int)W64;
     const int lane = threadIdx.x & 31;
     const int nchunks = (W + 31) >> 5;
-    int c = threadIdx.x >> 5;
-    while (c < nchunks) {
+    for (int g = (threadIdx.x >> 5) * kVisitGroup; g < nchunks;) {
+        const int gend = g + kVisitGroup < nchunks ? g + kVisitGroup : nchunks;
+        for (int c = g; c < gend; ++c) {
         const int wd = (c << 5) + lane;
         const uint2 v = wd < W ? bm[wd] : make_uint2(0u, 0u);
         if (clear && v.x) bm[wd].x = 0u;
@@ -659,9 +663,10 @@ __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W64, bool cl
                 if (o < S) f(crow + (sl << 5) + select_bit(bw, k), (int32_t)y0 + o);
             }
         }
+        }
         unsigned nc = 0;
-        if (lane == 0) nc = atomicAdd(s_next, 1u);
-        c = (int)__shfl_sync(0xffffffffu, nc, 0);
+        if (lane == 0) nc = atomicAdd(s_next, (unsigned)kVisitGroup);
+        g = (int)__shfl_sync(0xffffffffu, nc, 0);
     }
 }
 
