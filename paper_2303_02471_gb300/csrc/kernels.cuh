@@ -617,7 +617,7 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W64, con
 // rows (the hub rows of a power-law matrix) costs no lane serial steps and
 // its stores are coalesced.  Clears the bits when `clear`.  No barrier
 // inside.
-constexpr int kVisitLight = 2;
+constexpr int kVisitLight = 3;
 // Chunks of 32 words a warp takes per grab in cta_bitmap_visit.
 constexpr int kVisitGroup = 4;
 
