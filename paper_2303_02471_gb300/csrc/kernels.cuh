@@ -284,13 +284,18 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                         const VT *vp = VALS ? Aval + a0 : nullptr;
                         const VT b = VALS ? w.bv[li] : VT(0);
                         const int i1 = (e_end - e_key) << 5;
-                        for (int idx = ((win - e_key) << 5) + lane; idx < i1; idx += 32) {
-                            if (idx < e_z) {
-                                const int32_t row = ld_keep(rp + idx, pol);
-                                VT prod = VT(0);
-                                if (VALS) prod = ld_keep(vp + idx, pol) * b;
-                                f(row, prod);
-                            }
+                        // one window ahead: the next window's gathers are in
+                        // flight while this one is consumed
+                        int idx = ((win - e_key) << 5) + lane;
+                        int32_t row = idx < e_z ? ld_keep(rp + idx, pol) : -1;
+                        VT av = VALS && idx < e_z ? ld_keep(vp + idx, pol) : VT(0);
+                        for (; idx < i1; idx += 32) {
+                            const int nx = idx + 32;
+                            const int32_t row_n = nx < i1 && nx < e_z ? ld_keep(rp + nx, pol) : -1;
+                            const VT av_n = VALS && nx < i1 && nx < e_z ? ld_keep(vp + nx, pol) : VT(0);
+                            if (row >= 0) f(row, VALS ? av * b : VT(0));
+                            row = row_n;
+                            av = av_n;
                         }
                         win = e_end;
                     }
