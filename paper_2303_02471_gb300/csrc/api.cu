@@ -281,8 +281,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
         k_validate<<<vb, 256, 0, s>>>(B->colptr, B->rowidx, B->nrows, B->ncols, B->nnz, 1, ctrl);
         CK(cudaGetLastError());
         // a malformed colptr would make the walks read out of bounds: stop here
-        CK(cudaMemcpyAsync(&P->host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        CK(readback(&P->host, ctrl, sizeof(Ctrl), nullptr, nullptr, 0, s));
         if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     }
     if (P->nB > 0) {
@@ -292,8 +291,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     } else {
         CK(cudaMemsetAsync(C_colptr, 0, sizeof(int64_t), s));
     }
-    CK(cudaMemcpyAsync(&P->host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(readback(&P->host, ctrl, sizeof(Ctrl), nullptr, nullptr, 0, s));
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     // the walks index a column's products with 32-bit offsets
     for (int b = 0; b < NBINS; ++b)
@@ -321,9 +319,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
         CK(launch_symbolic_bin(P->task(b), o, C_colptr, g, s));
     }
     CK(launch_inclusive_scan(C_colptr + 1, P->nB, P->tiles(), s));
-    CK(cudaMemcpyAsync(&P->nnzC, C_colptr + P->nB, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&P->host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(readback(&P->nnzC, C_colptr + P->nB, sizeof(int64_t), &P->host, ctrl, sizeof(Ctrl), s));
 #undef CK
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     for (int b = 1; b < NBINS; ++b) {
@@ -407,9 +403,7 @@ spg_status spg_plan_check(spg_plan *P, spg_stream stream) {
     if (!P) return SPG_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int32_t err = 0;
-    if (cudaMemcpyAsync(&err, &P->ctrl()->err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return SPG_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return SPG_ERR_CUDA;
+    if (readback(&err, &P->ctrl()->err, sizeof(err), nullptr, nullptr, 0, s) != cudaSuccess) return SPG_ERR_CUDA;
     return (spg_status)err;
 }
 

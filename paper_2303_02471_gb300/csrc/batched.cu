@@ -753,16 +753,14 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
         if (ntot > 0)
             k_bvalidate<<<vg, 256, 0, s>>>(reinterpret_cast<const VMat *>(ws + P->L.vB), nb,
                                            reinterpret_cast<const int64_t *>(ws + P->L.col0s), ntot, 1, P->ctrl());
-        CK(cudaMemcpyAsync(&P->host, P->ctrl(), sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        CK(readback(&P->host, P->ctrl(), sizeof(Ctrl), nullptr, nullptr, 0, s));
         if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     }
     BTask b = P->task();
     int64_t *op = reinterpret_cast<int64_t *>(ws + P->L.op);
     if (ntot > 0) k_bcount<<<vg, 256, 0, s>>>(b, ntot, op);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(&P->host, P->ctrl(), sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(readback(&P->host, P->ctrl(), sizeof(Ctrl), nullptr, nullptr, 0, s));
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     for (int k = 0; k < NBINS; ++k)
         if (P->host.maxop[k] >= (1ULL << 31)) { delete P; return SPG_ERR_UNSUPPORTED; }
@@ -780,9 +778,7 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
         b, ccp, ncp, reinterpret_cast<const int64_t *>(ws + P->L.base), reinterpret_cast<const int64_t *>(ws + P->L.segs),
         reinterpret_cast<int64_t *>(ws + P->L.nnz));
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(P->nnz.data(), ws + P->L.nnz, (size_t)nb * 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&P->host, P->ctrl(), sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(readback(P->nnz.data(), ws + P->L.nnz, (size_t)nb * 8, &P->host, P->ctrl(), sizeof(Ctrl), s));
 #undef CK
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     for (int i = 0; i < nb; ++i) nnzC[i] = P->nnz[i];
@@ -887,9 +883,7 @@ spg_status spg_bplan_check(spg_bplan *P, spg_stream stream) {
     if (P->nb == 0) return SPG_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int32_t err = 0;
-    if (cudaMemcpyAsync(&err, &P->ctrl()->err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return SPG_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return SPG_ERR_CUDA;
+    if (readback(&err, &P->ctrl()->err, sizeof(err), nullptr, nullptr, 0, s) != cudaSuccess) return SPG_ERR_CUDA;
     return (spg_status)err;
 }
 

@@ -719,6 +719,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
 }
 
 // ------------------------------------------------------------ launchers
+// Small device -> host reads (control blocks, counts): a one-CTA kernel
+// copies src0[0..n0) and src1[0..n1) into a mapped pinned mirror of the
+// calling host thread, the stream is synchronised and the bytes are copied to
+// dst0 / dst1.  No copy engine is used, so these reads are not queued behind
+// large copies that the caller has in flight on other streams.
+cudaError_t readback(void *dst0, const void *src0, size_t n0, void *dst1, const void *src1, size_t n1,
+                     cudaStream_t s);
 cudaError_t launch_inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t s);
 int64_t scan_tile_count(int64_t n);
 

@@ -2,6 +2,8 @@
 // input validation, the operation count Op_j with binning (Section 3.1's
 // "Sorting" pre-pass, done as a bucket pass), per-bin column lists, and the
 // int64 scan that turns per-column counts into C's column pointers.
+#include <cstring>
+
 #include "kernels.cuh"
 
 namespace spg {
@@ -193,5 +195,60 @@ cudaError_t launch_inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cud
 }
 
 int64_t scan_tile_count(int64_t n) { return n <= 0 ? 1 : ceil_div(n, kScanTile); }
+
+
+// ------------------------------------------------------------ readback
+namespace {
+
+__global__ void k_readback(const unsigned char *s0, size_t n0, const unsigned char *s1, size_t n1,
+                           unsigned char *dst, size_t off1) {
+    for (size_t i = threadIdx.x; i < n0; i += blockDim.x) dst[i] = s0[i];
+    for (size_t i = threadIdx.x; i < n1; i += blockDim.x) dst[off1 + i] = s1[i];
+}
+
+// Mapped pinned staging of one host thread on one device.
+struct Mirror {
+    void *host = nullptr;
+    void *dev = nullptr;
+    size_t cap = 0;
+    ~Mirror() {
+        if (host) cudaFreeHost(host);
+    }
+};
+constexpr int kMaxDevices = 64;
+thread_local Mirror t_mirror[kMaxDevices];
+
+}  // namespace
+
+cudaError_t readback(void *dst0, const void *src0, size_t n0, void *dst1, const void *src1, size_t n1,
+                     cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    Mirror &m = t_mirror[dev];
+    const size_t off1 = (n0 + 15) & ~size_t(15);
+    const size_t need = off1 + n1;
+    if (m.cap < need) {
+        if (m.host) cudaFreeHost(m.host);
+        m.host = m.dev = nullptr;
+        m.cap = 0;
+        const size_t cap = need > (size_t(64) << 10) ? need : (size_t(64) << 10);
+        if ((e = cudaHostAlloc(&m.host, cap, cudaHostAllocMapped)) != cudaSuccess) {
+            m.host = nullptr;
+            return e;
+        }
+        if ((e = cudaHostGetDevicePointer(&m.dev, m.host, 0)) != cudaSuccess) return e;
+        m.cap = cap;
+    }
+    k_readback<<<1, 256, 0, s>>>(static_cast<const unsigned char *>(src0), n0,
+                                 static_cast<const unsigned char *>(src1), n1,
+                                 static_cast<unsigned char *>(m.dev), off1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (n0) std::memcpy(dst0, m.host, n0);
+    if (n1) std::memcpy(dst1, static_cast<unsigned char *>(m.host) + off1, n1);
+    return cudaSuccess;
+}
 
 }  // namespace spg
