@@ -75,7 +75,8 @@ typedef struct {
      * the dense SPA, a column with 0 < Op_j < t a hash table.  t = 0 sends
      * every non-empty column to the dense SPA; INT64_MAX ("infinity") sends
      * all to hash tables; a negative value picks the library default
-     * ceil(m / 256) clamped to [257, hash_cta_max + 1], m = rows of A. */
+     * ceil(m / 512) clamped to [257, hash_cta_max + 1], m = rows of A that
+     * hold entries. */
     int64_t t;
     /* Largest Op_j served by shared-memory hash tables; must be one of
      * 256, 512, 1024, 2048, 4096 or 8192.  Hash columns above it use a

@@ -38,9 +38,11 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
     size_t ctrl = 0, op = 0, cols = 0, tiles = 0, scratch = 0, cache = 0, total = 0;
+    size_t rmark = 0, rtiles = 0, rmap = 0, rinv = 0, arow = 0;
     size_t scratch_stride = 0;
     int64_t scratch_ctas = 0;
     int64_t cache_cols = 0;
+    size_t cache_bytes = 0;
 };
 
 spg_config normalized(const spg_config *cfg) {
@@ -56,8 +58,9 @@ spg_config normalized(const spg_config *cfg) {
 int64_t effective_t(const spg_config &c, int64_t m) {
     if (c.t >= 0) return c.t;
     // measured crossover on GB300: the dense SPA is the faster one from
-    // Op_j of about m / 256 up (the flags cost O(m / 32) words per column)
-    int64_t t = (m + 255) / 256;
+    // Op_j of about m / 512 up (the flags cost O(m / 32) words per column;
+    // m counts the rows the forward passes number)
+    int64_t t = (m + 511) / 512;
     if (t > (int64_t)c.hash_cta_max + 1) t = (int64_t)c.hash_cta_max + 1;
     if (t < 257) t = 257;
     return t;
@@ -77,6 +80,13 @@ Layout make_layout(int64_t m, int64_t nB, int64_t nnzA, int dtype, const spg_con
     L.op = off; off = align256(off + (size_t)nB * 8);
     L.cols = off; off = align256(off + (size_t)nB * 4);
     L.tiles = off; off = align256(off + (size_t)scan_tile_count(nB) * 8);
+    // row compaction: marks (scanned in place), the map to compact rows and
+    // back, and A's rows renumbered
+    L.rmark = off; off = align256(off + (size_t)m * 8);
+    L.rtiles = off; off = align256(off + (size_t)scan_tile_count(m) * 8);
+    L.rmap = off; off = align256(off + (size_t)m * 4);
+    L.rinv = off; off = align256(off + (size_t)m * 4);
+    L.arow = off; off = align256(off + (size_t)nnzA * 4);
     // per-CTA global scratch: a bitmap (uint2 per 32 rows) plus, for hash
     // tables that do not fit shared memory, keys and values
     const int64_t reach = std::min<int64_t>(std::max<int64_t>(nnzA, 1), std::max<int64_t>(m, 1));
@@ -101,7 +111,8 @@ Layout make_layout(int64_t m, int64_t nB, int64_t nnzA, int dtype, const spg_con
     L.cache = off;
     if (c.dense_cache_bytes > 0 && W > 0) {
         L.cache_cols = std::min<int64_t>(nB, c.dense_cache_bytes / (W * 4));
-        off = align256(off + (size_t)L.cache_cols * (size_t)W * 4);
+        L.cache_bytes = (size_t)L.cache_cols * (size_t)W * 4;
+        off = align256(off + L.cache_bytes);
     }
     L.total = off;
     return L;
@@ -125,6 +136,10 @@ struct spg_plan {
     int device = 0;
     DeviceInfo dev;
     int64_t mA = 0, nA = 0, nB = 0, nnzA = 0, nnzB = 0;
+    // rows of the forward pass: A's rows renumbered over the rows that hold
+    // entries (mC of them) when that saves at least a tenth of the rows
+    bool compact = false;
+    int64_t mC = 0;
     int dtype = 0;
     spg_config cfg{};
     int64_t t_eff = 0;
@@ -160,21 +175,30 @@ struct spg_plan {
     int32_t *cols() const { return reinterpret_cast<int32_t *>(ws + L.cols); }
     int64_t *tiles() const { return reinterpret_cast<int64_t *>(ws + L.tiles); }
     unsigned char *scratch() const { return ws + L.scratch; }
+    int64_t *rmark() const { return reinterpret_cast<int64_t *>(ws + L.rmark); }
+    int32_t *rmap() const { return reinterpret_cast<int32_t *>(ws + L.rmap); }
+    int32_t *rinv() const { return reinterpret_cast<int32_t *>(ws + L.rinv); }
+    int32_t *arow() const { return reinterpret_cast<int32_t *>(ws + L.arow); }
 
-    BinTask task(int b) const {
+    // fwd: the symbolic and numeric passes (compact rows when `compact`);
+    // otherwise the backward, which works on C's own rows
+    BinTask task(int b, bool fwd = true) const {
         BinTask t;
         t.cols = cols() + off.v[b];
         t.count = (int64_t)host.hist[b];
         t.bin = b;
         t.shrink = cfg.table_shrink;
-        t.m = mA;
-        t.W = ceil_div(mA, 32);
+        t.m = fwd ? mC : mA;
+        t.W = ceil_div(t.m, 32);
         t.op = op();
         t.scratch = scratch();
         t.scratch_stride = L.scratch_stride;
         t.ctrl = ctrl();
         t.flag_cache = b == BIN_DENSE ? reinterpret_cast<uint32_t *>(ws + L.cache) : nullptr;
-        t.cache_cols = b == BIN_DENSE ? L.cache_cols : 0;
+        // the cache region holds more columns of the shorter compact flags
+        t.cache_cols = b == BIN_DENSE && fwd && t.W > 0
+                           ? std::min<int64_t>(nB, (int64_t)(L.cache_bytes / ((size_t)t.W * 4)))
+                           : 0;
         return t;
     }
 };
@@ -259,7 +283,6 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     P->nnzA = A->nnz; P->nnzB = B->nnz;
     P->dtype = A->dtype;
     P->cfg = c;
-    P->t_eff = effective_t(c, A->nrows);
     P->L = make_layout(P->mA, P->nB, P->nnzA, P->dtype, c, P->dev.sms);
     if (ws_bytes < P->L.total) { delete P; return SPG_ERR_WORKSPACE; }
     P->ws = static_cast<unsigned char *>(workspace);
@@ -280,10 +303,32 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
         const int vb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max(B->nnz, B->ncols + 1), 256), 8 * P->dev.sms));
         k_validate<<<vb, 256, 0, s>>>(B->colptr, B->rowidx, B->nrows, B->ncols, B->nnz, 1, ctrl);
         CK(cudaGetLastError());
-        // a malformed colptr would make the walks read out of bounds: stop here
-        CK(readback(&P->host, ctrl, sizeof(Ctrl), nullptr, nullptr, 0, s));
-        if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     }
+    // Row compaction of the forward passes (bounds-checked, so it may run
+    // before the validation verdict): a row of A without entries has none in
+    // C, and the dense flags, their cache and the CTA bitmaps then span only
+    // the rows that hold entries.
+    int64_t mC = P->mA;
+    const bool try_compact = P->mA > 0 && P->nnzA > 0;
+    if (try_compact) {
+        CK(cudaMemsetAsync(P->rmark(), 0, (size_t)P->mA * 8, s));
+        const int ga = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A->nnz, 256), 8 * P->dev.sms));
+        const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(P->mA, 256), 8 * P->dev.sms));
+        k_row_mark<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->mA, P->rmark());
+        CK(cudaGetLastError());
+        CK(launch_inclusive_scan(P->rmark(), P->mA, reinterpret_cast<int64_t *>(P->ws + P->L.rtiles), s));
+        k_row_map<<<gm, 256, 0, s>>>(P->rmark(), P->mA, P->rmap(), P->rinv());
+        k_row_remap<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->rmap(), P->mA, P->arow(), ctrl);
+        CK(cudaGetLastError());
+    }
+    // one read: the validation verdict (a malformed colptr would make the
+    // walks read out of bounds: stop here) and the count of rows with entries
+    CK(readback(&P->host, ctrl, sizeof(Ctrl), try_compact ? &mC : nullptr,
+                try_compact ? P->rmark() + (P->mA - 1) : nullptr, try_compact ? sizeof(int64_t) : 0, s));
+    if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
+    P->compact = try_compact && mC > 0 && mC * 10 <= P->mA * 9;
+    P->mC = P->compact ? mC : P->mA;
+    P->t_eff = effective_t(c, P->mC);
     if (P->nB > 0) {
         const int g = (int)std::min<int64_t>(ceil_div(P->nB, 8), 16 * (int64_t)P->dev.sms);
         k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->op(), C_colptr, ctrl);
@@ -308,12 +353,12 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
         CK(cudaGetLastError());
     }
     CK(cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s));
-    Operands o{A->colptr, A->rowidx, nullptr, B->colptr, B->rowidx, nullptr};
+    Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, nullptr, B->colptr, B->rowidx, nullptr};
     for (int b = 1; b < NBINS; ++b) {
         if (!P->host.hist[b]) continue;
         // the symbolic CTA kernels carry no values: CTAs of up to 256 threads,
         // several per SM, overlap one another's barriers (measured faster)
-        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mA, std::min(c.cta_threads, kSymCtaThreads), P->dev.sms,
+        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mC, std::min(c.cta_threads, kSymCtaThreads), P->dev.sms,
                                   P->dev.smem_optin,
                                   (int64_t)P->host.maxop[b], c.table_shrink, P->L.scratch_ctas);
         CK(launch_symbolic_bin(P->task(b), o, C_colptr, g, s));
@@ -324,12 +369,14 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     for (int b = 1; b < NBINS; ++b) {
         if (!P->host.hist[b]) continue;
-        P->num_geo[b] = numeric_geometry(b, (int64_t)P->host.hist[b], P->mA, c.cta_threads, P->dev.sms,
+        P->num_geo[b] = numeric_geometry(b, (int64_t)P->host.hist[b], P->mC, c.cta_threads, P->dev.sms,
                                          P->dev.smem_optin, (int64_t)P->host.maxnnz[b], P->dtype, c.table_shrink,
                                          P->L.scratch_ctas);
     }
     P->num_geo_ready = true;
-    P->sym_launches = (c.validate ? 2 : 0) + (P->nB > 0 ? 5 : 0) + P->nonempty_bins();
+    // validation, row compaction (mark, 3 scan kernels, map, remap), the
+    // three control reads, Op counting + scatter + 3 scan kernels, the bins
+    P->sym_launches = (c.validate ? 2 : 0) + (try_compact ? 6 : 0) + 3 + (P->nB > 0 ? 5 : 0) + P->nonempty_bins();
     *nnzC = P->nnzC;
     *plan_out = P;
     return SPG_OK;
@@ -353,7 +400,15 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Ctrl *ctrl = P->ctrl();
     if (cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s) != cudaSuccess) return SPG_ERR_CUDA;
-    Operands o{A->colptr, A->rowidx, A->values, B->colptr, B->rowidx, B->values};
+    if (P->compact && P->nnzA > 0) {
+        // A's rows renumbered again from the A given here: an entry in a row
+        // that held none at planning time is reported, not walked
+        const int ga = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A->nnz, 256), 8 * P->dev.sms));
+        k_row_remap<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->rmap(), P->mA, P->arow(), ctrl);
+        if (cudaGetLastError() != cudaSuccess) return SPG_ERR_CUDA;
+    }
+    Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, A->values, B->colptr, B->rowidx, B->values,
+               P->compact ? P->rinv() : nullptr};
     for (int b = 1; b < NBINS; ++b) {
         if (!P->host.hist[b]) continue;
         if (P->timing && cudaEventRecord(P->ev0[b], s) != cudaSuccess) return SPG_ERR_CUDA;
@@ -392,7 +447,7 @@ spg_status spgemm_backward(spg_plan *P, const spg_csc *A, const spg_csc *B, cons
     Operands o{A->colptr, A->rowidx, A->values, B->colptr, B->rowidx, B->values};
     for (int b = 1; b < NBINS; ++b) {
         if (!P->host.hist[b]) continue;
-        cudaError_t e = launch_backward_bin(P->task(b), o, C_colptr, C_rowidx, dC_values, dA_values, dB_values,
+        cudaError_t e = launch_backward_bin(P->task(b, false), o, C_colptr, C_rowidx, dC_values, dA_values, dB_values,
                                             P->dtype, P->bwd_geo[b], s);
         if (e != cudaSuccess) return SPG_ERR_CUDA;
     }
@@ -439,7 +494,7 @@ spg_status spg_plan_bin_stats(const spg_plan *P, int64_t *bin_products, int64_t 
 spg_status spg_plan_launch_count(const spg_plan *P, int64_t *symbolic, int64_t *numeric, int64_t *backward) {
     if (!P) return SPG_ERR_INVALID;
     if (symbolic) *symbolic = P->sym_launches;
-    if (numeric) *numeric = P->nonempty_bins();
+    if (numeric) *numeric = P->nonempty_bins() + (P->compact ? 1 : 0);
     if (backward) *backward = P->nonempty_bins();
     return SPG_OK;
 }

@@ -25,11 +25,16 @@ struct TOps {
     const int64_t *Bcp;
     const int32_t *Brow;
     const VT *Bval;
+    // C's row of a (compact) row of the walk; nullptr: the same row
+    const int32_t *Rmap = nullptr;
+
+    __device__ __forceinline__ int32_t crow(int32_t r) const { return Rmap ? __ldg(Rmap + r) : r; }
 };
 
 template <typename VT>
 __device__ __forceinline__ TOps<VT> typed(const Operands &o) {
-    return TOps<VT>{o.Acp, o.Arow, static_cast<const VT *>(o.Aval), o.Bcp, o.Brow, static_cast<const VT *>(o.Bval)};
+    return TOps<VT>{o.Acp, o.Arow, static_cast<const VT *>(o.Aval), o.Bcp, o.Brow, static_cast<const VT *>(o.Bval),
+                    o.Rmap};
 }
 
 __host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
@@ -196,7 +201,7 @@ __device__ __forceinline__ bool num_group_column(unsigned mask, const TOps<VT> &
     for (int r = 0; r < R; ++r) {
         const int e = r * G + gl;
         if (e < n) {
-            Crow[c0 + e] = key[r];
+            Crow[c0 + e] = o.crow(key[r]);
             Cval[c0 + e] = val[r];
         }
     }
@@ -242,7 +247,7 @@ __device__ __forceinline__ bool num_cta_column(const TOps<VT> &o, int32_t j, int
     cta_expand_words(L0, wlist, K, s_warp, [&](int32_t row, int64_t rank) {
         const int32_t slot = hash_find(keys, H, row);
         if (ok && slot >= 0) {
-            Crow[c0 + rank] = row;
+            Crow[c0 + rank] = o.crow(row);
             Cval[c0 + rank] = vals[slot];
         }
     });
@@ -290,7 +295,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
     if (ns == 0) {  // every sum in C (uniform over the CTA)
         cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                            [&](int32_t row, VT prod) { atomicAdd(&gacc[bitmap_rank(bm, row)], prod); });
-        cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) { crow[rank] = row; });
+        cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) { crow[rank] = o.crow(row); });
     } else {
         cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                            [&](int32_t row, VT prod) {
@@ -299,7 +304,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                else atomicAdd(&gacc[r], prod);
                            });
         cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) {
-            crow[rank] = row;
+            crow[rank] = o.crow(row);
             if (rank < ns) gacc[rank] = s_acc[rank];
         });
     }

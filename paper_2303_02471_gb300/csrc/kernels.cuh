@@ -719,6 +719,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
 }
 
 // ------------------------------------------------------------ launchers
+// Row compaction.  Rows of A without entries have none in C = A B, so the
+// forward passes may number only the rows that hold entries: mark[r] = 1 for
+// every row of an entry (in range), an inclusive scan of mark gives the count,
+// k_row_map writes map[r] (compact index or -1) and inv[compact] = r, and
+// k_row_remap rewrites A's rows through map, reporting a row without a
+// compact index (kDetailRowMap).
+__global__ void k_row_mark(const int32_t *Arow, int64_t nnz, int64_t m, int64_t *mark);
+__global__ void k_row_map(const int64_t *incl, int64_t m, int32_t *map, int32_t *inv);
+__global__ void k_row_remap(const int32_t *Arow, int64_t nnz, const int32_t *map, int64_t m, int32_t *out,
+                            Ctrl *ctrl);
+
 // Small device -> host reads (control blocks, counts): a one-CTA kernel
 // copies src0[0..n0) and src1[0..n1) into a mapped pinned mirror of the
 // calling host thread, the stream is synchronised and the bytes are copied to
@@ -766,6 +777,7 @@ struct BinTask {
 struct Operands {
     const int64_t *Acp; const int32_t *Arow; const void *Aval;
     const int64_t *Bcp; const int32_t *Brow; const void *Bval;
+    const int32_t *Rmap = nullptr;  // C's row of a compact row (numeric)
 };
 
 // symbolic.cu

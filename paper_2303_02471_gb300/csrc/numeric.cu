@@ -214,34 +214,57 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
         g.grid = (int)std::max<int64_t>(1, grid);
         return g;
     }
-    // dense; with the double sums in C, a CTA holds only the walk scratch and
-    // the flags, so two CTAs of 512 threads share an SM and one's barriers
-    // overlap the other's work
-    if (sizeof(VT) == 8 && g.threads > 512) g.threads = 512;
+    // dense
     const size_t bmb = (size_t)W * 8;
-    const size_t walk = walk_smem_bytes<VT>(g.threads);
-    g.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
-    size_t base = walk + (g.bm_global ? 0 : bmb);
-    const size_t room = smem_optin > base ? (smem_optin - base) & ~size_t(15) : 0;
-    int64_t cap = (int64_t)(room / sizeof(VT));
-    if (cap > maxnnz) cap = maxnnz;
-    // Double sums go to C in place: on GB300 a walk that adds with RED.F64
-    // into L2-resident C takes about 1.3x the products per SM-second of one
-    // that adds with shared-memory f64 atomics (also when the first positions
-    // of a column stay in shared memory), and the extraction then copies no
-    // values.  Float sums stay in shared memory (native f32 atomics).
-    if (sizeof(VT) == 8) cap = 0;
-    g.cap = cap;
-    g.smem = base + al16((size_t)cap * sizeof(VT));
-    int occ = occupancy(k_num_dense<VT, true>, g.threads, g.smem);
-    // staging buffer for the next column's kept flags: bulk copies need
-    // 16-byte aligned columns (W a multiple of 4); only if it costs no CTA
-    if (!g.bm_global && W % 4 == 0) {
-        const size_t with = g.smem + (size_t)W * 4;
-        if (with <= smem_optin && occupancy(k_num_dense<VT, true>, g.threads, with) >= occ) {
-            g.smem = with;
-            g.prefetch = true;
+    // shape of one CTA with t threads: its cap (values kept in shared
+    // memory), dynamic shared memory, staging of the next column's flags,
+    // and CTAs per SM
+    auto shape = [&](int tt, Geo &o) {
+        o = g;
+        o.threads = tt;
+        const size_t walk = walk_smem_bytes<VT>(tt);
+        o.bm_global = bmb > kBitmapSmemMax || walk + bmb > smem_optin;
+        const size_t base = walk + (o.bm_global ? 0 : bmb);
+        const size_t room = smem_optin > base ? (smem_optin - base) & ~size_t(15) : 0;
+        int64_t cap = (int64_t)(room / sizeof(VT));
+        if (cap > maxnnz) cap = maxnnz;
+        // Double sums go to C in place: on GB300 a walk that adds with
+        // RED.F64 into L2-resident C takes about 1.3x the products per
+        // SM-second of one that adds with shared-memory f64 atomics (also
+        // when the first positions of a column stay in shared memory), and
+        // the extraction then copies no values.  Float sums stay in shared
+        // memory (native f32 atomics).
+        if (sizeof(VT) == 8) cap = 0;
+        o.cap = cap;
+        o.smem = base + al16((size_t)cap * sizeof(VT));
+        int occ = occupancy(k_num_dense<VT, true>, tt, o.smem);
+        // staging buffer for the next column's kept flags: bulk copies need
+        // 16-byte aligned columns (W a multiple of 4); only if it costs no CTA
+        o.prefetch = false;
+        if (!o.bm_global && W % 4 == 0) {
+            const size_t with = o.smem + (size_t)W * 4;
+            if (with <= smem_optin && occupancy(k_num_dense<VT, true>, tt, with) >= occ) {
+                o.smem = with;
+                o.prefetch = true;
+            }
         }
+        return occ;
+    };
+    // With the double sums in C a CTA holds only the walk scratch and the
+    // flags: where four 256-thread CTAs fit an SM they beat two of 512 (more
+    // CTAs overlap one another's per-column barriers; measured), else two of
+    // 512, else the configured size.
+    Geo g256, g512;
+    int occ = 0;
+    if (sizeof(VT) == 8 && threads >= 256) {
+        const int o256 = shape(256, g256);
+        const int o512 = threads >= 512 ? shape(512, g512) : 0;
+        if (o256 * 256 >= o512 * 512) { g = g256; occ = o256; }
+        else { g = g512; occ = o512; }
+    } else {
+        Geo gc;
+        occ = shape(threads, gc);
+        g = gc;
     }
     int64_t grid = std::min<int64_t>(count, (int64_t)occ * sms);
     if (g.bm_global) grid = std::min<int64_t>(grid, scratch_ctas);

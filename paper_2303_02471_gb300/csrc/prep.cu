@@ -197,6 +197,40 @@ cudaError_t launch_inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cud
 int64_t scan_tile_count(int64_t n) { return n <= 0 ? 1 : ceil_div(n, kScanTile); }
 
 
+
+// ------------------------------------------------------- row compaction
+__global__ void k_row_mark(const int32_t *Arow, int64_t nnz, int64_t m, int64_t *mark) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = Arow[i];
+        if (r >= 0 && r < m) mark[r] = 1;
+    }
+}
+
+__global__ void k_row_map(const int64_t *incl, int64_t m, int32_t *map, int32_t *inv) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t before = r > 0 ? incl[r - 1] : 0;
+        if (incl[r] != before) {
+            map[r] = (int32_t)before;
+            inv[before] = (int32_t)r;
+        } else {
+            map[r] = -1;
+        }
+    }
+}
+
+__global__ void k_row_remap(const int32_t *Arow, int64_t nnz, const int32_t *map, int64_t m, int32_t *out,
+                            Ctrl *ctrl) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = Arow[i];
+        int32_t c = r >= 0 && r < m ? map[r] : -1;
+        if (c < 0) {
+            set_error(ctrl, SPG_ERR_INVALID, kDetailRowMap, i);
+            c = 0;
+        }
+        out[i] = c;
+    }
+}
+
 // ------------------------------------------------------------ readback
 namespace {
 

@@ -69,6 +69,8 @@ struct Ctrl {
 // Code for a column whose numeric count disagrees with the symbolic one
 // (the pattern changed between the phases).
 constexpr int kDetailCountMismatch = 100;
+// Code for an entry of A whose row held no entry when the plan was made.
+constexpr int kDetailRowMap = 200;
 
 __device__ inline void set_error(Ctrl *ctrl, int code, int detail, int64_t index) {
     if (atomicCAS(&ctrl->err, 0, code) == 0) {
