@@ -190,6 +190,24 @@ def test_invalid_inputs_are_rejected():
     del bad, torch
 
 
+def test_numeric_reports_rows_outside_the_plan():
+    # the forward passes number only the rows of A that hold entries (R-MAT
+    # leaves many empty); a numeric call whose A has an entry in a row that
+    # was empty when the plan was made is reported, not walked
+    from paper_2303_02471_gb300 import ops
+    A = synth.rmat(12, seed=9, col_cap=400)
+    present = np.unique(A.rowidx)
+    assert present.size < 0.9 * A.nrows
+    empty = int(np.setdiff1d(np.arange(A.nrows), present)[0])
+    dA = upload(A)
+    _, _, plan = ops.spgemm_symbolic(dA, dA)
+    plan.check()
+    moved = dA.rowidx.clone()
+    moved[0] = empty
+    ops.spgemm_numeric(plan, ops.CscMatrix(A.nrows, A.ncols, dA.colptr, moved, dA.values), dA)
+    assert _status(plan.check) == "SPG_ERR_INVALID"
+
+
 def test_workspace_too_small():
     import torch
     from paper_2303_02471_gb300 import _native as N
