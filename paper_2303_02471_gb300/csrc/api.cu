@@ -305,7 +305,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
         CK(cudaGetLastError());
     }
     // Row compaction of the forward passes (bounds-checked, so it may run
-    // before the validation verdict): a row of A without entries has none in
+    // before the validation outcome): a row of A without entries has none in
     // C, and the dense flags, their cache and the CTA bitmaps then span only
     // the rows that hold entries.
     int64_t mC = P->mA;
@@ -321,7 +321,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
         k_row_remap<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->rmap(), P->mA, P->arow(), ctrl);
         CK(cudaGetLastError());
     }
-    // one read: the validation verdict (a malformed colptr would make the
+    // one read: the validation outcome (a malformed colptr would make the
     // walks read out of bounds: stop here) and the count of rows with entries
     CK(readback(&P->host, ctrl, sizeof(Ctrl), try_compact ? &mC : nullptr,
                 try_compact ? P->rmark() + (P->mA - 1) : nullptr, try_compact ? sizeof(int64_t) : 0, s));
