@@ -37,22 +37,26 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _declare(lib):
+    """Argument and result types of the library's entry points."""
+    i64, i32, p = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+    lib.oracle_op_counts.restype = i64
+    lib.oracle_op_counts.argtypes = [i64, p, p, p, p]
+    lib.oracle_spgemm_count.restype = i32
+    lib.oracle_spgemm_count.argtypes = [i64, i64, p, p, p, p, p, i32]
+    lib.oracle_spgemm_fill.restype = i32
+    lib.oracle_spgemm_fill.argtypes = [i64, i64] + [p] * 10 + [i32]
+    lib.oracle_spgemm_backward.restype = i32
+    lib.oracle_spgemm_backward.argtypes = [i64, i64, i64] + [p] * 11
+    lib.oracle_threads.restype = i32
+    lib.oracle_threads.argtypes = [i32]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        i64, i32, p = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
-        lib.oracle_op_counts.restype = i64
-        lib.oracle_op_counts.argtypes = [i64, p, p, p, p]
-        lib.oracle_spgemm_count.restype = i32
-        lib.oracle_spgemm_count.argtypes = [i64, i64, p, p, p, p, p, i32]
-        lib.oracle_spgemm_fill.restype = i32
-        lib.oracle_spgemm_fill.argtypes = [i64, i64] + [p] * 10 + [i32]
-        lib.oracle_spgemm_backward.restype = i32
-        lib.oracle_spgemm_backward.argtypes = [i64, i64, i64] + [p] * 11
-        lib.oracle_threads.restype = i32
-        lib.oracle_threads.argtypes = [i32]
-        _lib = lib
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
 
 

@@ -229,3 +229,24 @@ def test_galerkin_finite_differences():
         Lm = oracle.galerkin(A, P.with_values(vm), T_values=T)[0]
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - dP[idx]) <= 1e-6 * max(1.0, abs(dP[idx])), (idx, fd, dP[idx])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_transpose_matches_dense(seed):
+    # transpose against the dense transpose; values follow their entries (perm)
+    rng = np.random.default_rng(100 + seed)
+    m, n = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+    M = synth.random_pattern(rng, m, n, float(rng.uniform(0.0, 0.5)))
+    T, perm = oracle.transpose(M)
+    assert (T.nrows, T.ncols) == (n, m)
+    D = np.zeros((m, n))
+    for j in range(n):
+        for q in range(M.colptr[j], M.colptr[j + 1]):
+            D[M.rowidx[q], j] = M.values[q]
+    E = np.zeros((n, m))
+    for j in range(m):
+        rows = T.rowidx[T.colptr[j]:T.colptr[j + 1]]
+        assert np.all(np.diff(rows) > 0)
+        E[rows, j] = T.values[T.colptr[j]:T.colptr[j + 1]]
+    assert np.array_equal(E, D.T)
+    assert np.array_equal(T.values, M.values[perm])
