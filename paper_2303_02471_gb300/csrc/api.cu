@@ -54,12 +54,10 @@ spg_config normalized(const spg_config *cfg) {
 
 // Default threshold: the dense SPA pays O(m / 32) words per column (flag
 // bitmap prefix and sorted extraction), so a column goes dense once its
-// product count reaches m / 128, within [257, hash_cta_max + 1].
+// product count reaches m / 512 (the crossover measured on GB300), within
+// [257, hash_cta_max + 1]; m counts the rows the forward passes number.
 int64_t effective_t(const spg_config &c, int64_t m) {
     if (c.t >= 0) return c.t;
-    // measured crossover on GB300: the dense SPA is the faster one from
-    // Op_j of about m / 512 up (the flags cost O(m / 32) words per column;
-    // m counts the rows the forward passes number)
     int64_t t = (m + 511) / 512;
     if (t > (int64_t)c.hash_cta_max + 1) t = (int64_t)c.hash_cta_max + 1;
     if (t < 257) t = 257;

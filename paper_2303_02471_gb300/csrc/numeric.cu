@@ -9,10 +9,12 @@
 //     the touched rows are then marked in a bitmap whose prefix counts give
 //     every row its sorted position, and the column is written in row order
 //     with one table lookup per entry;
-//   * dense bin (Op_j >= t): the SPA of Algorithm 1 -- flags as a bitmap, a
-//     first walk sets them, prefix counts turn each row into its position in
-//     the sorted column, and a second walk accumulates every product at that
-//     position (shared memory up to `cap` entries, else in place in C).
+//   * dense bin (Op_j >= t): the SPA of Algorithm 1 -- flags as a bitmap
+//     (kept from the symbolic phase and staged one column ahead by a bulk
+//     copy, or set again by a first walk), prefix counts turn each row into
+//     its position in the sorted column, a walk adds every product at that
+//     position (double sums in place in C, float sums in shared memory), and
+//     a pass over the flags writes the rows in order.
 #include "columns.cuh"
 
 namespace spg {
