@@ -115,11 +115,14 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        # this rank's GPU: its LOCAL_RANK-th visible device
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        visible = [d for d in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if d]
+        dev = visible[local] if local < len(visible) else str(local)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
 
@@ -217,21 +220,46 @@ def cpu_baseline(A, B, target_s, unit):
 
 
 # ------------------------------------------------------------------ arms
+REFERENCE_BUDGET_S = 60.0  # host seconds of the whole reference run
+
+
 def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores, as the other arm: W untimed
+    and K timed steps, every step the same seeded column sample of the
+    workload, sized so that the whole run takes about a minute."""
     unit = "GFLOP/s"
     if rank != 0:
         return None
+    import oracle
     A, B = make_workload(args.workload, args.rmat_scale)
-    base = cpu_baseline(A, B, min(args.cpu_seconds, 20.0), unit)
-    line = {"impl": "reference", "metric": "SpGEMM GFLOP/s (2 x intermediate products / s)",
-            "value": base["value"], "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args)},
+    cores = len(os.sched_getaffinity(0))
+    threads = oracle.threads(cores)
+    op = oracle.op_counts(A, B)
+    small, cols = column_sample(B, 0.005, seed=1)
+    t0 = time.perf_counter()
+    oracle.spgemm(A, small, nthreads=threads)
+    rate = max(1.0, op[cols].sum()) / max(1e-3, time.perf_counter() - t0)
+    per_step = REFERENCE_BUDGET_S / max(1, args.warmup + args.steps)
+    frac = min(1.0, per_step * rate / max(1, op.sum()))
+    sample, cols = column_sample(B, frac, seed=2)
+    products = int(op[cols].sum())
+    for _ in range(args.warmup):
+        oracle.spgemm(A, sample, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.spgemm(A, sample, nthreads=threads)
+    dt = time.perf_counter() - t0
+    value = 2.0 * products * args.steps / dt / 1e9
+    base = {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+            "sample": f"{len(cols)} of {B.ncols} columns of B per step (seeded, p={frac:.4f}), "
+                      f"{products} products, {args.steps} timed steps in {dt:.2f} s"}
+    return {"impl": "reference", "metric": "SpGEMM GFLOP/s (2 x intermediate products / s)",
+            "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / max(1, args.steps), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(args)},
             "cpu_baseline": base,
-            "e2e": {"value": base["value"], "unit": unit, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    return line
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def run_ours(args, rank, world):
@@ -559,6 +587,9 @@ def run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world):
     steps = max(2, min(args.steps, 10))
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     t0.record(s_run)
     for _ in range(steps):
         n = step()
@@ -566,6 +597,11 @@ def run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world):
     t1.record(s_out)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
+    if world > 1:
+        torch.distributed.barrier()
+        tm = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tm.item())
     # the last read-back landed: spot-check it against the device copy
     o = bufs[(state["i"] - 1) % 2]
     assert torch.equal(o["hrow"][:: 1 << 16], o["row"][:: 1 << 16].cpu())
