@@ -126,6 +126,32 @@ def test_workload3_threshold_extremes_pattern(t):
     assert_matches_oracle(C, A, A, nthreads=NCPU)
 
 
+def _tall(m, n, zlo, zhi, seed):
+    """m x n with Z ~ U{zlo..zhi} distinct uniform rows per column."""
+    rng = np.random.default_rng(seed)
+    z = rng.integers(zlo, zhi + 1, size=n)
+    rows = np.concatenate([rng.choice(m, int(k), replace=False) for k in z])
+    cols = np.repeat(np.arange(n), z)
+    return synth.from_coo(m, n, rows, cols, rng.standard_normal(rows.size))
+
+
+@pytest.mark.parametrize("t", [0, None, INF])
+def test_tall_products_flags_in_global_scratch(t):
+    # m = 2^20 rows, 94 % of them holding entries (no row compaction): a
+    # dense column's flags (32,768 words, 256 KB) and a CTA table's row
+    # bitmap (128 KB) exceed shared memory and live in the per-CTA global
+    # scratch; Op_j spans the CTA bins and the global table
+    A = _tall(1 << 20, 3000, 900, 1100, seed=21)
+    B = _tall(3000, 600, 1, 12, seed=22)
+    C, plan = _run(A, B, t=t)
+    bins = plan.info()["bins"]
+    if t == 0:
+        assert bins[13] == sum(bins[1:])
+    if t == INF:
+        assert bins[12] > 0 and sum(bins[7:12]) > 0
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
 def test_identity_is_bit_exact():
     from helpers import identity
     A = synth.random_z(5000, 1, 9, seed=5)
