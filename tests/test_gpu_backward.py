@@ -61,6 +61,16 @@ def test_backward_rmat_every_bin(t):
     _check_backward(A, B, t=t, hash_cta_max=1024)
 
 
+@pytest.mark.parametrize("t", [0, INF])
+def test_backward_tall_products(t):
+    # 2^20 rows, nearly all holding entries: the backward's row bitmaps and
+    # tables live in the per-CTA global scratch
+    from test_gpu_forward import _tall
+    A = _tall(1 << 20, 3000, 900, 1100, seed=31)
+    B = _tall(3000, 400, 1, 12, seed=32)
+    _check_backward(A, B, t=t)
+
+
 def test_backward_only_one_side():
     import torch
     from paper_2303_02471_gb300 import ops

@@ -152,6 +152,13 @@ def test_tall_products_flags_in_global_scratch(t):
     assert_matches_oracle(C, A, B, nthreads=NCPU)
 
 
+def test_tall_products_float32_all_dense():
+    A = _tall(1 << 20, 3000, 900, 1100, seed=23).astype(np.float32)
+    B = _tall(3000, 600, 1, 12, seed=24).astype(np.float32)
+    C, _ = _run(A, B, dtype=np.float32, t=0)
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
 def test_identity_is_bit_exact():
     from helpers import identity
     A = synth.random_z(5000, 1, 9, seed=5)
