@@ -125,7 +125,10 @@ spg_status spgemm_workspace_size(const spg_csc *A, const spg_csc *B,
 /*
  * Symbolic phase of C = A x B (Gustavson by columns, Section 2.1).
  *
- * Steps on `stream`: (optional) input validation; Op_j of every column of B
+ * Steps on `stream`: (optional) input validation; a numbering of the rows
+ * of A that hold entries (a row of A without entries has none in C; when it
+ * saves at least a tenth of the rows, the forward passes work on these rows
+ * and map them back when C is written); Op_j of every column of B
  * (Section 3.1) and its bin (empty / hash table sized by Op_j / dense SPA,
  * Sections 3.2-3.3); per-bin column lists; nnz of every C column by the
  * bin's accumulator; exclusive scan into C_colptr.
@@ -140,7 +143,8 @@ spg_status spgemm_workspace_size(const spg_csc *A, const spg_csc *B,
  * plan     receives a new plan (host object) on success; NULL on error.
  *
  * Synchronises `stream` (it reads the bin histogram and nnz(C) back to the
- * host).  Errors: SPG_ERR_INVALID (shapes, dtypes, NULL pointers, or a
+ * host, through a small mapped pinned buffer of the calling thread, so these
+ * reads do not wait behind the caller's copies on other streams).  Errors: SPG_ERR_INVALID (shapes, dtypes, NULL pointers, or a
  * malformed input when cfg->validate), SPG_ERR_WORKSPACE, SPG_ERR_INDEX_OVERFLOW
  * (a dimension beyond int32 rows), SPG_ERR_UNSUPPORTED (a column with
  * Op_j >= 2^31 products), SPG_ERR_TABLE_OVERFLOW, SPG_ERR_CUDA.
@@ -165,8 +169,12 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B,
  *          summed in the input dtype (float inputs accumulate in float).
  *
  * Asynchronous: does not synchronise.  Kernel-side errors surface in
- * spg_plan_check.  Errors returned directly: SPG_ERR_INVALID (plan/shape
- * mismatch, NULL pointers), SPG_ERR_CUDA (launch failure).
+ * spg_plan_check: SPG_ERR_INVALID when a column's row count differs from the
+ * plan's, or when A has an entry in a row that held none when the plan was
+ * made (the plan numbers only the rows of A that hold entries; such an entry
+ * is not walked and C's contents are then unspecified).  Errors returned
+ * directly: SPG_ERR_INVALID (plan/shape mismatch, NULL pointers),
+ * SPG_ERR_CUDA (launch failure).
  */
 spg_status spgemm_numeric(spg_plan *plan, const spg_csc *A, const spg_csc *B,
                           const int64_t *C_colptr, int32_t *C_rowidx,
