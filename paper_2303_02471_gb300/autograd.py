@@ -13,7 +13,6 @@ prolongation P, differentiable in the values of P (and of A).
 """
 from __future__ import annotations
 
-import ctypes
 from typing import Optional
 
 import torch
