@@ -49,6 +49,7 @@ struct BItems {
     int32_t order[kMaxItemBins];    // bin of each item range
     int64_t nitems;
     int nranges;
+    int dense_warp;  // dense items are groups of one column per warp
 };
 
 struct BTask {
@@ -214,6 +215,119 @@ __device__ __forceinline__ ItemRef item_ref(const BItems &it, int64_t item) {
     return r;
 }
 
+// ------------------------------------------------------ warp-dense items
+// When every product's dense flags are short (at most kWarpDenseWords words),
+// a dense column is worked by one warp, with its own flags in shared memory
+// and warp-level synchronisation only: the column's fixed cost (clearing,
+// prefix, extraction) is small and no CTA barrier is paid per column.
+constexpr int64_t kWarpDenseWords = 1024;
+
+// Position of row among the flagged rows of its column: the word's prefix
+// count plus the flags below it in the word.
+__device__ __forceinline__ int32_t warp_dense_rank(const uint2 *bm, int32_t row) {
+    const uint2 e = bm[row >> 5];
+    return (int32_t)e.y + __popc(e.x & ((1u << (row & 31)) - 1u));
+}
+
+// nnz of column j: flags set by the warp's product walk, then counted.
+__device__ __forceinline__ int64_t warp_dense_symbolic(const TOps<float> &o, int32_t j, uint32_t *bm, int W) {
+    const int lane = threadIdx.x & 31;
+    for (int w = lane; w < W; w += 32) bm[w] = 0u;
+    __syncwarp();
+    group_products<32, false, float>(0xffffffffu, o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1],
+                                     [&](int32_t row, float) { atomicOr(&bm[row >> 5], 1u << (row & 31)); });
+    __syncwarp();
+    int64_t cnt = 0;
+    for (int w = lane; w < W; w += 32) cnt += __popc(bm[w]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+    return cnt;
+}
+
+// Column j by the dense SPA in one warp: flags, prefix counts (each lane a
+// contiguous run of words, one warp scan), every product added at its row's
+// position in place in C, then the rows written in order.  False on a count
+// mismatch.
+template <typename VT>
+__device__ __forceinline__ bool warp_dense_numeric(const TOps<VT> &o, int32_t j, int64_t c0, int64_t nn, uint2 *bm,
+                                                   int W, int32_t *Crow, VT *Cval) {
+    const int lane = threadIdx.x & 31;
+    for (int w = lane; w < W; w += 32) bm[w] = make_uint2(0u, 0u);
+    __syncwarp();
+    group_products<32, false, VT>(0xffffffffu, o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1],
+                                  [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
+    __syncwarp();
+    const int per = (W + 31) >> 5;
+    const int w0 = lane * per < W ? lane * per : W;
+    const int w1 = w0 + per < W ? w0 + per : W;
+    int cnt = 0;
+    for (int w = w0; w < w1; ++w) cnt += __popc(bm[w].x);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int run = incl - cnt;
+    for (int w = w0; w < w1; ++w) {
+        const uint32_t x = bm[w].x;
+        bm[w].y = (uint32_t)run;
+        run += __popc(x);
+    }
+    __syncwarp();
+    if ((int64_t)total != nn) return false;
+    VT *gacc = Cval + c0;
+    int32_t *crow = Crow + c0;
+    for (int i = lane; i < total; i += 32) gacc[i] = VT(0);
+    __syncwarp();
+    group_products<32, true, VT>(0xffffffffu, o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1],
+                                 [&](int32_t row, VT prod) { atomicAdd(&gacc[warp_dense_rank(bm, row)], prod); });
+    for (int w = lane; w < W; w += 32) {
+        uint32_t bits = bm[w].x;
+        int32_t r = (int32_t)bm[w].y;
+        while (bits) {
+            const int q = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            crow[r++] = (w << 5) + q;
+        }
+    }
+    return true;
+}
+
+// Item idx of the dense bin in warp form: warp w of the CTA takes dense
+// column idx * (warps per CTA) + w.
+template <int phase>
+__device__ __noinline__ void bdense_warp_item(const BTask &b, int64_t idx, unsigned char *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t k = idx * nw + warp;
+    if (k >= (int64_t)b.hist[BIN_DENSE]) return;
+    const int64_t g = b.cols[b.boff.v[BIN_DENSE] + k];
+    const int p = find_prob(b.col0s, b.nb, g);
+    const BProb &P = b.prob[p];
+    const int64_t j = g - P.col0;
+    const int W = (int)((P.m + 31) / 32);
+    if (phase == 0) {
+        uint32_t *bm = reinterpret_cast<uint32_t *>(smem + (size_t)warp * al16((size_t)b.Wmax * 4));
+        const TOps<float> o{P.Acp, P.Arow, nullptr, P.Bcp, P.Brow, nullptr};
+        const int64_t cnt = warp_dense_symbolic(o, (int32_t)j, bm, W);
+        if (lane == 0) {
+            P.Ccp[j + 1] = cnt;
+            atomicMax(&b.ctrl->maxnnz[BIN_DENSE], (unsigned long long)cnt);
+            atomicAdd(&b.ctrl->binnnz[BIN_DENSE], (unsigned long long)cnt);
+        }
+    } else {
+        uint2 *bm = reinterpret_cast<uint2 *>(smem + (size_t)warp * al16((size_t)b.Wmax * 8));
+        const int64_t c0 = P.Ccp[j], nn = P.Ccp[j + 1] - c0;
+        const bool ok = P.dtype == SPG_F64
+                            ? warp_dense_numeric<double>(prob_ops<double>(P), (int32_t)j, c0, nn, bm, W, P.Crow,
+                                                         static_cast<double *>(P.Cval))
+                            : warp_dense_numeric<float>(prob_ops<float>(P), (int32_t)j, c0, nn, bm, W, P.Crow,
+                                                        static_cast<float *>(P.Cval));
+        if (!ok && lane == 0) set_error(b.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + BIN_DENSE, j);
+    }
+}
+
 template <int G, int R, typename VT>
 __device__ __forceinline__ void bnum_group(const BTask &b, const BProb &P, int64_t j, unsigned char *smem,
                                            int bin) {
@@ -352,6 +466,8 @@ __global__ void __launch_bounds__(512, 2) k_batched(BTask b, BItems it) {
         const ItemRef r = item_ref(it, item);
         if (r.bin >= BIN_WARP0 && r.bin < BIN_CTA0) {
             bgroup_dispatch(b, r.bin, r.idx, smem, phase);
+        } else if (phase < 2 && r.bin == BIN_DENSE && it.dense_warp) {
+            if constexpr (phase < 2) bdense_warp_item<phase>(b, r.idx, smem);
         } else {
             const int64_t g = b.cols[b.boff.v[r.bin] + r.idx];
             const int p = find_prob(b.col0s, b.nb, g);
@@ -512,8 +628,14 @@ struct spg_bplan {
 
 namespace {
 
+// Dense columns of the forward phases are worked one per warp when every
+// product's flags fit kWarpDenseWords words.
+bool warp_dense(const spg_bplan &P, int phase) {
+    return phase < 2 && P.host.hist[BIN_DENSE] != 0 && P.Wmax <= kWarpDenseWords;
+}
+
 // Items of a phase, heaviest first.
-BItems make_items(const spg_bplan &P, int threads) {
+BItems make_items(const spg_bplan &P, int threads, int phase) {
     BItems it{};
     int k = 0;
     int64_t acc = 0;
@@ -524,7 +646,9 @@ BItems make_items(const spg_bplan &P, int threads) {
         acc += n;
         it.off[++k] = acc;
     };
-    add(BIN_DENSE, (int64_t)P.host.hist[BIN_DENSE]);
+    it.dense_warp = warp_dense(P, phase) ? 1 : 0;
+    add(BIN_DENSE, it.dense_warp ? ceil_div((int64_t)P.host.hist[BIN_DENSE], threads / 32)
+                                 : (int64_t)P.host.hist[BIN_DENSE]);
     for (int c = kNumCtaBins - 1; c >= 0; --c) add(BIN_CTA0 + c, (int64_t)P.host.hist[BIN_CTA0 + c]);
     for (int w = kNumWarpBins - 1; w >= 0; --w) {
         const int NG = threads / warp_bin_G(w);
@@ -553,7 +677,9 @@ size_t phase_smem(const spg_bplan &P, int phase, int threads, int64_t &cap_cta, 
             maxop = std::max<int64_t>(maxop, (int64_t)P.host.maxop[BIN_CTA0 + c]);
             maxnnz = std::max<int64_t>(maxnnz, (int64_t)P.host.maxnnz[BIN_CTA0 + c]);
         }
-    const bool dense = P.host.hist[BIN_DENSE] != 0;
+    const bool wd = warp_dense(P, phase);
+    const bool dense = P.host.hist[BIN_DENSE] != 0 && !wd;
+    if (wd) need = std::max(need, (size_t)(threads / 32) * al16((size_t)P.Wmax * (phase == 0 ? 4 : 8)));
     cap_sym = cta ? global_sym_slots(maxop, P.mmax) : 0;
     cap_cta = cta ? num_slots(maxnnz) : 0;
     if (phase == 0) {
@@ -604,7 +730,7 @@ spg_status prepare_phase(spg_bplan &P, int phase, PhaseLaunch &L) {
     L.b.cap_cta = cap_cta;
     L.b.cap_dense = cap_dense;
     L.b.cap_sym = cap_sym;
-    L.it = make_items(P, threads);
+    L.it = make_items(P, threads, phase);
     const void *kfn = batched_kernel(phase);
     if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)std::max<size_t>(L.smem, 1)) != cudaSuccess)

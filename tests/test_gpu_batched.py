@@ -99,6 +99,27 @@ def test_batched_small_ctas_match_oracle(threads):
         assert_matches_oracle(C, A, B)
 
 
+@pytest.mark.parametrize("tall", [False, True])
+@pytest.mark.parametrize("t", [0, None])
+def test_batched_dense_columns_per_warp_and_per_cta(tall, t):
+    # flags of at most 1024 words: dense columns of the forward phases are
+    # worked one per warp; a product with more than 32768 rows switches the
+    # launch to one column per CTA
+    from paper_2303_02471_gb300 import ops
+    rng = np.random.default_rng(11)
+    pairs = synth.batch_pairs(12, seed=10, n_scale=0.05)
+    pairs += [(synth.random_pattern(rng, 2000, 90, 0.04, dtype=np.float32, dense_col=True),
+               synth.random_pattern(rng, 90, 70, 0.3, dtype=np.float32))]
+    if tall:
+        pairs += [(synth.random_pattern(rng, 40000, 60, 0.002), synth.random_pattern(rng, 60, 40, 0.3))]
+    As, Bs = _upload_pairs(pairs)
+    Cs, plan = ops.spgemm_batched(As, Bs, ops.Config(t=t))
+    plan.check()
+    assert plan.info()["bins"][13] > 0
+    for (A, B), C in zip(pairs, Cs):
+        assert_matches_oracle(C, A, B)
+
+
 def test_batched_backward_matches_plain():
     import torch
     from paper_2303_02471_gb300 import ops
