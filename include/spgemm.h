@@ -275,8 +275,9 @@ spg_status spg_csc_transpose(const spg_csc *M, int64_t *T_colptr,
  * nb independent products C_i = A_i x B_i (uneven sizes, each pair with its
  * own dtype).  The columns of all products are binned together by Op_j and
  * each phase runs as one persistent kernel whose blocks take work items
- * (one column of a CTA-level bin, or a tile of columns of a warp-group bin)
- * heaviest first.  The paper has no batched form; the per-column work is the
+ * (one column of a CTA-level bin, or a tile of columns of a warp-group bin;
+ * in the symbolic and numeric phases of a batch whose products all have at
+ * most 32768 rows, a tile of dense columns, one per warp) heaviest first.  The paper has no batched form; the per-column work is the
  * method of the single product (H-HASH(t), Section 3.3).  In the batched
  * kernels t is at most hash_cta_max + 1 (no global-memory hash tables), and
  * every product's bitmaps must fit shared memory (m_i up to ~2^20 rows);

@@ -4,7 +4,10 @@
 // over that space, and each phase runs as ONE persistent kernel whose blocks
 // pop work items from a global counter:
 //   * a CTA item is one column of a CTA hash bin or of the dense bin;
-//   * a group item is blockDim / G columns of a warp-group bin.
+//   * a group item is blockDim / G columns of a warp-group bin;
+//   * in the symbolic and numeric phases, when no product has more than
+//     32 * kWarpDenseWords rows, a dense item is blockDim / 32 columns of
+//     the dense bin, one per warp.
 // Items are ordered heaviest first (dense, then CTA bins from the largest,
 // then the group bins), the GPU form of processing columns by decreasing
 // Op_j (Section 3.1).  Per-column work is the same device code as the
