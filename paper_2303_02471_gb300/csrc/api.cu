@@ -128,6 +128,9 @@ spg_status check_csc(const spg_csc *M, bool need_values) {
 
 spg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SPG_OK : SPG_ERR_CUDA; }
 
+// Side streams a numeric call spreads the lane-group bins over.
+constexpr int kNumSideStreams = 2;
+
 }  // namespace
 
 struct spg_plan {
@@ -155,12 +158,29 @@ struct spg_plan {
     bool timed = false;
     cudaEvent_t ev0[NBINS] = {}, ev1[NBINS] = {};
     int64_t sym_launches = 0;
+    // numeric: the lane-group bins run on side streams, forked from and
+    // joined back to the caller's stream (created on first use)
+    cudaStream_t side[kNumSideStreams] = {};
+    cudaEvent_t fork = nullptr, join[kNumSideStreams] = {};
 
     ~spg_plan() {
         for (int b = 0; b < NBINS; ++b) {
             if (ev0[b]) cudaEventDestroy(ev0[b]);
             if (ev1[b]) cudaEventDestroy(ev1[b]);
         }
+        for (int i = 0; i < kNumSideStreams; ++i) {
+            if (side[i]) cudaStreamDestroy(side[i]);
+            if (join[i]) cudaEventDestroy(join[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+    }
+    bool side_streams() {
+        if (fork) return true;
+        for (int i = 0; i < kNumSideStreams; ++i)
+            if (cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess)
+                return false;
+        return cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
     }
     int64_t nonempty_bins() const {
         int64_t n = 0;
@@ -407,12 +427,37 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
     }
     Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, A->values, B->colptr, B->rowidx, B->values,
                P->compact ? P->rinv() : nullptr};
-    for (int b = 1; b < NBINS; ++b) {
-        if (!P->host.hist[b]) continue;
-        if (P->timing && cudaEventRecord(P->ev0[b], s) != cudaSuccess) return SPG_ERR_CUDA;
-        cudaError_t e = launch_numeric_bin(P->task(b), o, C_colptr, C_rowidx, C_values, P->dtype, P->num_geo[b], s);
+    // The bins write disjoint columns of C.  Next to a dense bin, the
+    // lane-group bins (shared memory only, no work counter) run on side
+    // streams: the dense kernel is launched first and keeps every SM, the
+    // group kernels fill SMs as its CTAs finish and overlap one another.
+    bool groups = false;
+    for (int b = BIN_WARP0; b < BIN_CTA0; ++b) groups |= P->host.hist[b] != 0;
+    const bool fork = groups && P->host.hist[BIN_DENSE] != 0;
+    if (fork && !P->side_streams()) return SPG_ERR_CUDA;
+    auto launch = [&](int b, cudaStream_t sb) -> spg_status {
+        if (P->timing && cudaEventRecord(P->ev0[b], sb) != cudaSuccess) return SPG_ERR_CUDA;
+        cudaError_t e = launch_numeric_bin(P->task(b), o, C_colptr, C_rowidx, C_values, P->dtype, P->num_geo[b], sb);
         if (e != cudaSuccess) return SPG_ERR_CUDA;
-        if (P->timing && cudaEventRecord(P->ev1[b], s) != cudaSuccess) return SPG_ERR_CUDA;
+        if (P->timing && cudaEventRecord(P->ev1[b], sb) != cudaSuccess) return SPG_ERR_CUDA;
+        return SPG_OK;
+    };
+    if (fork) {
+        if (cudaEventRecord(P->fork, s) != cudaSuccess) return SPG_ERR_CUDA;
+        for (int i = 0; i < kNumSideStreams; ++i)
+            if (cudaStreamWaitEvent(P->side[i], P->fork, 0) != cudaSuccess) return SPG_ERR_CUDA;
+        for (int b = BIN_CTA0; b < NBINS; ++b)
+            if (P->host.hist[b] && (st = launch(b, s)) != SPG_OK) return st;
+        // heaviest group bin first, bins dealt round-robin to the side streams
+        for (int b = BIN_CTA0 - 1, i = 0; b >= BIN_WARP0; --b)
+            if (P->host.hist[b] && (st = launch(b, P->side[i++ % kNumSideStreams])) != SPG_OK) return st;
+        for (int i = 0; i < kNumSideStreams; ++i)
+            if (cudaEventRecord(P->join[i], P->side[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(s, P->join[i], 0) != cudaSuccess)
+                return SPG_ERR_CUDA;
+    } else {
+        for (int b = 1; b < NBINS; ++b)
+            if (P->host.hist[b] && (st = launch(b, s)) != SPG_OK) return st;
     }
     P->timed = P->timing;
     return SPG_OK;

@@ -193,6 +193,39 @@ def test_repeat_numeric_is_stable():
     assert_matches_oracle(C2, A, A, ref=ref)
 
 
+@pytest.mark.parametrize("stream", ["default", "side", "graph"])
+def test_numeric_forks_group_bins_and_joins(stream):
+    """Dense and lane-group bins together: the group bins run on streams
+    forked from the caller's and joined back before the call's later work,
+    on the legacy default stream, a side stream, and inside a CUDA graph."""
+    import torch
+    from paper_2303_02471_gb300 import ops
+    A = synth.rmat(12, seed=12, col_cap=400)
+    dA = upload(A)
+    _, _, plan = ops.spgemm_symbolic(dA, dA, ops.Config(t=64))
+    bins = plan.info()["bins"]
+    assert bins[13] > 0 and sum(bins[1:7]) > 0
+    ref = oracle.spgemm(A, A)
+    if stream == "default":
+        C = ops.spgemm_numeric(plan, dA, dA)
+        total = C.values.double().abs().sum().item()  # later work on the caller's stream
+    else:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            C = ops.spgemm_numeric(plan, dA, dA)
+            if stream == "graph":
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    ops.spgemm_numeric(plan, dA, dA, C.rowidx, C.values)
+                C.values.zero_()
+                g.replay()
+            total = C.values.double().abs().sum().item()
+    plan.check()
+    C_ref, absC = ref
+    assert abs(total - float(np.abs(C_ref.values).sum())) <= 1e-9 * float(absC.sum())
+    assert_matches_oracle(C, A, A, ref=ref)
+
+
 # ----------------------------------------------------------- errors
 def _status(fn):
     from paper_2303_02471_gb300._native import SpgError
