@@ -23,7 +23,7 @@ from .ops import Config
 
 INF = (1 << 63) - 1
 DEFAULT_GRID = {
-    "t": [65, 129, 257, 513, 1025, None],
+    "t": [33, 65, 129, 257, 513, 1025, None],
     "hash_cta_max": [2048, 8192],
     "cta_threads": [128, 256, 512],
 }
