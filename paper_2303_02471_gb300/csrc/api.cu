@@ -427,13 +427,18 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
     }
     Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, A->values, B->colptr, B->rowidx, B->values,
                P->compact ? P->rinv() : nullptr};
-    // The bins write disjoint columns of C.  Next to a dense bin, the
-    // lane-group bins (shared memory only, no work counter) run on side
-    // streams: the dense kernel is launched first and keeps every SM, the
-    // group kernels fill SMs as its CTAs finish and overlap one another.
-    bool groups = false;
-    for (int b = BIN_WARP0; b < BIN_CTA0; ++b) groups |= P->host.hist[b] != 0;
-    const bool fork = groups && P->host.hist[BIN_DENSE] != 0;
+    // The bins write disjoint columns of C.  Next to a dense bin, the bins
+    // that use no workspace scratch (the lane-group bins, and CTA hash bins
+    // whose table and flags fit shared memory) run on side streams: the
+    // dense kernel is launched first and keeps every SM, the others fill
+    // SMs as its CTAs finish and overlap one another.
+    auto on_side = [&](int b) {
+        if (b >= BIN_WARP0 && b < BIN_CTA0) return true;
+        return b >= BIN_CTA0 && b < BIN_GLOBAL && P->num_geo[b].cap == 0 && !P->num_geo[b].bm_global;
+    };
+    bool sides = false;
+    for (int b = 1; b < BIN_DENSE; ++b) sides |= P->host.hist[b] != 0 && on_side(b);
+    const bool fork = sides && P->host.hist[BIN_DENSE] != 0;
     if (fork && !P->side_streams()) return SPG_ERR_CUDA;
     auto launch = [&](int b, cudaStream_t sb) -> spg_status {
         if (P->timing && cudaEventRecord(P->ev0[b], sb) != cudaSuccess) return SPG_ERR_CUDA;
@@ -446,11 +451,12 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
         if (cudaEventRecord(P->fork, s) != cudaSuccess) return SPG_ERR_CUDA;
         for (int i = 0; i < kNumSideStreams; ++i)
             if (cudaStreamWaitEvent(P->side[i], P->fork, 0) != cudaSuccess) return SPG_ERR_CUDA;
-        for (int b = BIN_CTA0; b < NBINS; ++b)
-            if (P->host.hist[b] && (st = launch(b, s)) != SPG_OK) return st;
-        // heaviest group bin first, bins dealt round-robin to the side streams
-        for (int b = BIN_CTA0 - 1, i = 0; b >= BIN_WARP0; --b)
-            if (P->host.hist[b] && (st = launch(b, P->side[i++ % kNumSideStreams])) != SPG_OK) return st;
+        for (int b = 1; b < NBINS; ++b)
+            if (P->host.hist[b] && !on_side(b) && (st = launch(b, s)) != SPG_OK) return st;
+        // heaviest side bin first, bins dealt round-robin to the side streams
+        for (int b = BIN_DENSE - 1, i = 0; b >= 1; --b)
+            if (P->host.hist[b] && on_side(b) && (st = launch(b, P->side[i++ % kNumSideStreams])) != SPG_OK)
+                return st;
         for (int i = 0; i < kNumSideStreams; ++i)
             if (cudaEventRecord(P->join[i], P->side[i]) != cudaSuccess ||
                 cudaStreamWaitEvent(s, P->join[i], 0) != cudaSuccess)
