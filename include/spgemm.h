@@ -99,7 +99,9 @@ typedef struct {
      * the symbolic phase builds for dense-SPA columns, so that the numeric
      * phase reuses them instead of walking the column's products twice.
      * Columns beyond the budget rebuild their flags.  0 disables;
-     * default 2 GiB. */
+     * default 2 GiB.  The batched calls keep flags the same way for dense
+     * columns worked one per warp (every product at most 32768 rows), and
+     * their workspace grows by up to this budget. */
     int64_t dense_cache_bytes;
 } spg_config;
 

@@ -71,6 +71,12 @@ struct BTask {
     const int64_t *op;     // Op of every global column
     int shrink;
     unsigned long long *counter;
+    // flags of per-warp dense columns kept from the symbolic phase: column k
+    // of the dense list owns words [coff[k], coff[k] + W) of `cache` when
+    // they end within cache_words (cache null: nothing kept)
+    const int64_t *coff;
+    uint32_t *cache;
+    int64_t cache_words;
 };
 
 __device__ __forceinline__ int find_prob(const int64_t *col0s, int nb, int64_t g) {
@@ -119,6 +125,18 @@ __global__ void k_bcount(BTask b, int64_t ntot, int64_t *op) {
         atomicAdd(&b.ctrl->binprod[threadIdx.x], s_prod[threadIdx.x]);
         atomicAdd(&b.ctrl->binnnzb[threadIdx.x], s_nb[threadIdx.x]);
         atomicAdd(&b.ctrl->products, s_prod[threadIdx.x]);
+    }
+}
+
+// Flag words of every dense-list column (coff[k + 1]; coff[0] = 0): a scan
+// then gives each column its place in the kept-flag cache.
+__global__ void k_bcache_words(BTask b, int64_t ndense, int64_t *coff) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ndense; k += stride) {
+        const int64_t g = b.cols[b.boff.v[BIN_DENSE] + k];
+        const BProb &P = b.prob[find_prob(b.col0s, b.nb, g)];
+        coff[k + 1] = (P.m + 31) / 32;
+        if (k == 0) coff[0] = 0;
     }
 }
 
@@ -232,8 +250,10 @@ __device__ __forceinline__ int32_t warp_dense_rank(const uint2 *bm, int32_t row)
     return (int32_t)e.y + __popc(e.x & ((1u << (row & 31)) - 1u));
 }
 
-// nnz of column j: flags set by the warp's product walk, then counted.
-__device__ __forceinline__ int64_t warp_dense_symbolic(const TOps<float> &o, int32_t j, uint32_t *bm, int W) {
+// nnz of column j: flags set by the warp's product walk, then counted (and
+// copied to `keep` when it is not null).
+__device__ __forceinline__ int64_t warp_dense_symbolic(const TOps<float> &o, int32_t j, uint32_t *bm, int W,
+                                                       uint32_t *keep) {
     const int lane = threadIdx.x & 31;
     for (int w = lane; w < W; w += 32) bm[w] = 0u;
     __syncwarp();
@@ -241,24 +261,33 @@ __device__ __forceinline__ int64_t warp_dense_symbolic(const TOps<float> &o, int
                                      [&](int32_t row, float) { atomicOr(&bm[row >> 5], 1u << (row & 31)); });
     __syncwarp();
     int64_t cnt = 0;
-    for (int w = lane; w < W; w += 32) cnt += __popc(bm[w]);
+    for (int w = lane; w < W; w += 32) {
+        const uint32_t x = bm[w];
+        cnt += __popc(x);
+        if (keep) keep[w] = x;
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
     return cnt;
 }
 
-// Column j by the dense SPA in one warp: flags, prefix counts (each lane a
-// contiguous run of words, one warp scan), every product added at its row's
-// position in place in C, then the rows written in order.  False on a count
-// mismatch.
+// Column j by the dense SPA in one warp: flags (read from `keep` when the
+// symbolic phase kept them, else set by a product walk), prefix counts (each
+// lane a contiguous run of words, one warp scan), every product added at its
+// row's position in place in C, then the rows written in order.  False on a
+// count mismatch.
 template <typename VT>
 __device__ __forceinline__ bool warp_dense_numeric(const TOps<VT> &o, int32_t j, int64_t c0, int64_t nn, uint2 *bm,
-                                                   int W, int32_t *Crow, VT *Cval) {
+                                                   int W, const uint32_t *keep, int32_t *Crow, VT *Cval) {
     const int lane = threadIdx.x & 31;
-    for (int w = lane; w < W; w += 32) bm[w] = make_uint2(0u, 0u);
-    __syncwarp();
-    group_products<32, false, VT>(0xffffffffu, o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1],
-                                  [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
+    if (keep) {
+        for (int w = lane; w < W; w += 32) bm[w] = make_uint2(keep[w], 0u);
+    } else {
+        for (int w = lane; w < W; w += 32) bm[w] = make_uint2(0u, 0u);
+        __syncwarp();
+        group_products<32, false, VT>(0xffffffffu, o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1],
+                                      [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
+    }
     __syncwarp();
     const int per = (W + 31) >> 5;
     const int w0 = lane * per < W ? lane * per : W;
@@ -310,10 +339,12 @@ __device__ __noinline__ void bdense_warp_item(const BTask &b, int64_t idx, unsig
     const BProb &P = b.prob[p];
     const int64_t j = g - P.col0;
     const int W = (int)((P.m + 31) / 32);
+    uint32_t *keep = nullptr;
+    if (b.cache && b.coff[k] + W <= b.cache_words) keep = b.cache + b.coff[k];
     if (phase == 0) {
         uint32_t *bm = reinterpret_cast<uint32_t *>(smem + (size_t)warp * al16((size_t)b.Wmax * 4));
         const TOps<float> o{P.Acp, P.Arow, nullptr, P.Bcp, P.Brow, nullptr};
-        const int64_t cnt = warp_dense_symbolic(o, (int32_t)j, bm, W);
+        const int64_t cnt = warp_dense_symbolic(o, (int32_t)j, bm, W, keep);
         if (lane == 0) {
             P.Ccp[j + 1] = cnt;
             atomicMax(&b.ctrl->maxnnz[BIN_DENSE], (unsigned long long)cnt);
@@ -323,10 +354,10 @@ __device__ __noinline__ void bdense_warp_item(const BTask &b, int64_t idx, unsig
         uint2 *bm = reinterpret_cast<uint2 *>(smem + (size_t)warp * al16((size_t)b.Wmax * 8));
         const int64_t c0 = P.Ccp[j], nn = P.Ccp[j + 1] - c0;
         const bool ok = P.dtype == SPG_F64
-                            ? warp_dense_numeric<double>(prob_ops<double>(P), (int32_t)j, c0, nn, bm, W, P.Crow,
-                                                         static_cast<double *>(P.Cval))
-                            : warp_dense_numeric<float>(prob_ops<float>(P), (int32_t)j, c0, nn, bm, W, P.Crow,
-                                                        static_cast<float *>(P.Cval));
+                            ? warp_dense_numeric<double>(prob_ops<double>(P), (int32_t)j, c0, nn, bm, W, keep,
+                                                         P.Crow, static_cast<double *>(P.Cval))
+                            : warp_dense_numeric<float>(prob_ops<float>(P), (int32_t)j, c0, nn, bm, W, keep,
+                                                        P.Crow, static_cast<float *>(P.Cval));
         if (!ok && lane == 0) set_error(b.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + BIN_DENSE, j);
     }
 }
@@ -547,10 +578,23 @@ namespace {
 size_t al256b(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct BLayout {
-    size_t ctrl, prob, col0s, segs, base, nnz, aoff, boffe, vA, vB, acol0, op, cols, tiles, total;
+    size_t ctrl, prob, col0s, segs, base, nnz, aoff, boffe, vA, vB, acol0, op, cols, tiles, coff, cache, total;
 };
 
-BLayout blayout(int nb, int64_t ntot, int64_t ntotA, int64_t ncp) {
+// Bytes of kept dense flags of a batch: only when its dense columns run one
+// per warp (every product at most 32 * kWarpDenseWords rows), at most the
+// flags of every column, at most cfg.dense_cache_bytes.
+size_t batch_cache_bytes(int nb, const spg_csc *A, const spg_csc *B, const spg_config &c) {
+    int64_t mmax = 0, words = 0;
+    for (int i = 0; i < nb; ++i) {
+        mmax = std::max<int64_t>(mmax, A[i].nrows);
+        words += B[i].ncols * ceil_div(A[i].nrows, 32);
+    }
+    if (c.dense_cache_bytes <= 0 || ceil_div(mmax, 32) > kWarpDenseWords) return 0;
+    return (size_t)std::min<int64_t>(words, c.dense_cache_bytes / 4) * 4;
+}
+
+BLayout blayout(int nb, int64_t ntot, int64_t ntotA, int64_t ncp, size_t cache_bytes) {
     BLayout L{};
     size_t off = 0;
     L.ctrl = off; off = al256b(off + sizeof(Ctrl));
@@ -567,6 +611,8 @@ BLayout blayout(int nb, int64_t ntot, int64_t ntotA, int64_t ncp) {
     L.op = off; off = al256b(off + (size_t)ntot * 8);
     L.cols = off; off = al256b(off + (size_t)ntot * 4);
     L.tiles = off; off = al256b(off + (size_t)scan_tile_count(ncp) * 8);
+    L.coff = off; off = al256b(off + (cache_bytes ? (size_t)(ntot + 1) * 8 : 0));
+    L.cache = off; off = al256b(off + cache_bytes);
     L.total = off;
     (void)ntotA;
     return L;
@@ -599,6 +645,7 @@ struct spg_bplan {
     Ctrl host{};
     BinOffsets off{};
     int64_t Wmax = 0, mmax = 0;
+    int64_t cache_words = 0;  // kept dense flags (0: none)
     int threads = 256;
     bool any_f64 = false;
     // numeric graph
@@ -625,6 +672,11 @@ struct spg_bplan {
         b.shrink = cfg.table_shrink;
         b.counter = &ctrl()->work[0];
         b.Wmax = Wmax;
+        if (cache_words > 0) {
+            b.coff = reinterpret_cast<const int64_t *>(ws + L.coff);
+            b.cache = reinterpret_cast<uint32_t *>(ws + L.cache);
+            b.cache_words = cache_words;
+        }
         return b;
     }
 };
@@ -784,14 +836,16 @@ spg_status spgemm_batched_workspace_size(int32_t nb, const spg_csc *A, const spg
     if (!bytes) return SPG_ERR_INVALID;
     spg_status st = check_batch(nb, A, B);
     if (st != SPG_OK) return st;
-    (void)cfg;
+    spg_config c;
+    spg_config_default(&c);
+    if (cfg) c = *cfg;
     int64_t ntot = 0, ntotA = 0, ncp = 0;
     for (int i = 0; i < nb; ++i) {
         ntot += B[i].ncols;
         ntotA += A[i].ncols;
         ncp += B[i].ncols + 1;
     }
-    *bytes = blayout(nb, ntot, ntotA, ncp).total;
+    *bytes = blayout(nb, ntot, ntotA, ncp, batch_cache_bytes(nb, A, B, c)).total;
     return SPG_OK;
 }
 
@@ -854,7 +908,9 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
     col0s[nb] = ntot; segs[nb] = ncp; aoff[nb] = na; boffe[nb] = nbe; acol0[nb] = ntotA;
     P->ntot = ntot; P->ncp = ncp; P->na = na; P->nbe = nbe;
     P->Wmax = ceil_div(P->mmax, 32);
-    P->L = blayout(nb, ntot, ntotA, ncp);
+    if (c.dense_cache_bytes < 0) { delete P; return SPG_ERR_INVALID; }
+    const size_t cache_bytes = batch_cache_bytes(nb, A, B, c);
+    P->L = blayout(nb, ntot, ntotA, ncp, cache_bytes);
     if (ws_bytes < P->L.total) { delete P; return SPG_ERR_WORKSPACE; }
     P->ws = static_cast<unsigned char *>(workspace);
     P->nnz.assign(nb, 0);
@@ -898,6 +954,17 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
     b = P->task();
     if (ntot > 0) k_bscatter<<<(unsigned)ceil_div(ntot, 256), 256, 0, s>>>(b, ntot, op, reinterpret_cast<int32_t *>(ws + P->L.cols));
     CK(cudaGetLastError());
+    // places of the dense columns' kept flags (per-warp dense columns only)
+    const int64_t ndense = (int64_t)P->host.hist[BIN_DENSE];
+    if (cache_bytes > 0 && ndense > 0) {
+        int64_t *coff = reinterpret_cast<int64_t *>(ws + P->L.coff);
+        k_bcache_words<<<(unsigned)std::min<int64_t>(ceil_div(ndense, 256), 16 * (int64_t)sms), 256, 0, s>>>(
+            b, ndense, coff);
+        CK(cudaGetLastError());
+        CK(launch_inclusive_scan(coff, ndense + 1, reinterpret_cast<int64_t *>(ws + P->L.tiles), s));
+        P->cache_words = (int64_t)(cache_bytes / 4);
+        P->launches_sym += 4;
+    }
     st = launch_phase(*P, 0, s);
     if (st != SPG_OK) { delete P; return st; }
     int64_t *ccp = C_colptr;
@@ -911,7 +978,7 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
 #undef CK
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     for (int i = 0; i < nb; ++i) nnzC[i] = P->nnz[i];
-    P->launches_sym = (c.validate ? 2 : 0) + 2 + 1 + 3 + 2;
+    P->launches_sym += (c.validate ? 2 : 0) + 2 + 1 + 3 + 2;
     *plan_out = P;
     return SPG_OK;
 }

@@ -120,6 +120,28 @@ def test_batched_dense_columns_per_warp_and_per_cta(tall, t):
         assert_matches_oracle(C, A, B)
 
 
+@pytest.mark.parametrize("cache", [0, 4 * 700, None])
+def test_batched_kept_dense_flags(cache):
+    # dense columns one per warp keep their flags from the symbolic phase
+    # for the numeric one: none kept, the first few columns, all of them
+    import torch
+    from paper_2303_02471_gb300 import ops
+    pairs = synth.batch_pairs(20, seed=13, n_scale=0.05)
+    As, Bs = _upload_pairs(pairs)
+    cfg = ops.Config(t=0, dense_cache_bytes=cache)
+    plan = ops.spgemm_batched_symbolic(As, Bs, cfg)
+    assert plan.info()["bins"][13] > 0
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        first = [(C.rowidx.clone(), C.values.clone()) for C in ops.spgemm_batched_numeric(plan, As, Bs, True)]
+        Cs = ops.spgemm_batched_numeric(plan, As, Bs, True)  # replay reads the kept flags again
+    s.synchronize()
+    plan.check()
+    for (A, B), C, (r0, v0) in zip(pairs, Cs, first):
+        assert (C.rowidx == r0).all()
+        assert_matches_oracle(C, A, B)
+
+
 def test_batched_backward_matches_plain():
     import torch
     from paper_2303_02471_gb300 import ops
