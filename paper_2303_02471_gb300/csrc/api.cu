@@ -372,14 +372,33 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     }
     CK(cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s));
     Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, nullptr, B->colptr, B->rowidx, nullptr};
-    for (int b = 1; b < NBINS; ++b) {
-        if (!P->host.hist[b]) continue;
+    // as in the numeric phase: beside a dense bin, the lane-group bins (shared
+    // memory only) run on the side streams, launched after the dense kernel
+    bool groups = false;
+    for (int b = BIN_WARP0; b < BIN_CTA0; ++b) groups |= P->host.hist[b] != 0;
+    const bool fork = groups && P->host.hist[BIN_DENSE] != 0;
+    if (fork) {
+        if (!P->side_streams()) { delete P; return SPG_ERR_CUDA; }
+        CK(cudaEventRecord(P->fork, s));
+        for (int i = 0; i < kNumSideStreams; ++i) CK(cudaStreamWaitEvent(P->side[i], P->fork, 0));
+    }
+    auto sym_bin = [&](int b, cudaStream_t sb) {
         // the symbolic CTA kernels carry no values: CTAs of up to 256 threads,
         // several per SM, overlap one another's barriers (measured faster)
-        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mC, std::min(c.cta_threads, kSymCtaThreads), P->dev.sms,
-                                  P->dev.smem_optin,
-                                  (int64_t)P->host.maxop[b], c.table_shrink, P->L.scratch_ctas);
-        CK(launch_symbolic_bin(P->task(b), o, C_colptr, g, s));
+        Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mC, std::min(c.cta_threads, kSymCtaThreads),
+                                  P->dev.sms, P->dev.smem_optin, (int64_t)P->host.maxop[b], c.table_shrink,
+                                  P->L.scratch_ctas);
+        return launch_symbolic_bin(P->task(b), o, C_colptr, g, sb);
+    };
+    for (int b = 1; b < NBINS; ++b)
+        if (P->host.hist[b] && !(fork && b >= BIN_WARP0 && b < BIN_CTA0)) CK(sym_bin(b, s));
+    if (fork) {
+        for (int b = BIN_CTA0 - 1, i = 0; b >= BIN_WARP0; --b)
+            if (P->host.hist[b]) CK(sym_bin(b, P->side[i++ % kNumSideStreams]));
+        for (int i = 0; i < kNumSideStreams; ++i) {
+            CK(cudaEventRecord(P->join[i], P->side[i]));
+            CK(cudaStreamWaitEvent(s, P->join[i], 0));
+        }
     }
     CK(launch_inclusive_scan(C_colptr + 1, P->nB, P->tiles(), s));
     CK(readback(&P->nnzC, C_colptr + P->nB, sizeof(int64_t), &P->host, ctrl, sizeof(Ctrl), s));
