@@ -70,3 +70,36 @@ def test_host_only_calls(lib):
     assert lib.spg_plan_check(None, None) == 1
     assert lib.spg_permute_values(None, None, None, 0, 0, 0, None) == 0
     assert lib.spg_permute_values(None, None, None, 5, 0, 0, None) == 1
+
+
+def _batch_bytes(lib, shapes, cache):
+    # shapes only: the pointers are never dereferenced on the host
+    from paper_2303_02471_gb300 import _native as N
+    As = (N.SpgCsc * len(shapes))()
+    Bs = (N.SpgCsc * len(shapes))()
+    for i, (m, k, n) in enumerate(shapes):
+        As[i] = N.SpgCsc(m, k, 4 * k, 16, 16, 16, 0)
+        Bs[i] = N.SpgCsc(k, n, 4 * n, 16, 16, 16, 0)
+    c = N.SpgConfig()
+    lib.spg_config_default(ctypes.byref(c))
+    if cache is not None:
+        c.dense_cache_bytes = cache
+    nbytes = ctypes.c_size_t()
+    assert lib.spgemm_batched_workspace_size(len(shapes), As, Bs, ctypes.byref(c), ctypes.byref(nbytes)) == 0
+    return nbytes.value
+
+
+def test_batched_workspace_holds_the_kept_dense_flags(lib):
+    """Kept flags of per-warp dense columns: every column's flags (n_i words
+    of ceil(m_i / 32)) up to dense_cache_bytes, and none when a product has
+    more than 32768 rows (its dense columns run one per CTA)."""
+    small = [(1000, 300, 500), (32768, 200, 90)]
+    words = 500 * 32 + 90 * 1024
+    base = _batch_bytes(lib, small, 0)
+    full = _batch_bytes(lib, small, None)
+    # the cache and the column offsets, each padded to 256 bytes
+    assert words * 4 <= full - base <= words * 4 + (590 + 1) * 8 + 512
+    capped = _batch_bytes(lib, small, 4096)
+    assert 4096 <= capped - base <= 4096 + (590 + 1) * 8 + 512
+    tall = small + [(32769, 10, 10)]
+    assert _batch_bytes(lib, tall, None) == _batch_bytes(lib, tall, 0)
