@@ -88,8 +88,10 @@ __global__ void __launch_bounds__(1024, 1) k_sym_cta(BinTask t, Operands o, int6
 // scratch); nnz(C_j) is the number of set bits.  Columns with a cache slot
 // keep their flags for the numeric phase.
 template <bool BSM>
-// launched with at most kSymCtaThreads threads (the host caps them)
-__global__ void __launch_bounds__(kSymCtaThreads, 5) k_sym_dense(BinTask t, Operands o, int64_t *Ccp) {
+// launched with at most kSymCtaThreads threads (the host caps them); the
+// walk issues an instruction on most cycles, so the kernel is built for a
+// full SM of warps (eight CTAs of 256 threads, 32 registers, no spills)
+__global__ void __launch_bounds__(kSymCtaThreads, 8) k_sym_dense(BinTask t, Operands o, int64_t *Ccp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_col;
     __shared__ unsigned long long s_cnt, s_max, s_sum;
