@@ -170,7 +170,13 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B,
  * C_values device values[nnzC] of the plan's dtype, written.  Values are
  *          summed in the input dtype (float inputs accumulate in float).
  *
- * Asynchronous: does not synchronise.  Kernel-side errors surface in
+ * Asynchronous: does not synchronise.  When the plan has a dense bin and
+ * lane-group bins, the group bins run on two streams the plan owns (created
+ * on first use, released with the plan), forked from `stream` by an event
+ * and joined back to it before the call returns, so later work on `stream`
+ * sees all of C; the pattern is legal on the legacy default stream and
+ * under stream capture.  The symbolic call does the same for its group
+ * bins.  Kernel-side errors surface in
  * spg_plan_check: SPG_ERR_INVALID when a column's row count differs from the
  * plan's, or when A has an entry in a row that held none when the plan was
  * made (the plan numbers only the rows of A that hold entries; such an entry
