@@ -176,9 +176,10 @@ struct spg_plan {
     }
     bool side_streams() {
         if (fork) return true;
+        // (what a failed attempt created is kept and not created again)
         for (int i = 0; i < kNumSideStreams; ++i)
-            if (cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess)
+            if ((!side[i] && cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking) != cudaSuccess) ||
+                (!join[i] && cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess))
                 return false;
         return cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
     }
