@@ -183,6 +183,14 @@ def bin_bytes(st, b, w):
             + 16 * cols + st["nnz"][b] * (4 + w))
 
 
+def dominant_bin(st, w):
+    """The bin kernel the roofline reports: the non-empty bin with the most
+    algorithmic bytes (not the longest event time: bins on side streams
+    start timing with the pass and include waiting for SMs)."""
+    nbins = len(st["count"])
+    return int(np.argmax([bin_bytes(st, b, w) if b and st["count"][b] else 0 for b in range(nbins)]))
+
+
 def column_sample(B, frac, seed=0):
     """Every column of B kept with probability `frac` (a CSC of the subset)."""
     from types import SimpleNamespace
@@ -357,7 +365,7 @@ def run_ours(args, rank, world):
     # pass and include waiting for SMs, so they do not pick the kernel.
     peak, peak_kind = peaks()
     bms = np.mean(np.array(bin_ms), axis=0)
-    top = int(np.argmax([bin_bytes(st, b, w) if st["count"][b] and b else 0 for b in range(len(bms))]))
+    top = dominant_bin(st, w)
     side = bool(st["count"][13]) and any(st["count"][b] for b in range(1, 7))
     top_bytes = bin_bytes(st, top, w)
     top_ach = top_bytes / (bms[top] * 1e-3) / 1e9

@@ -59,3 +59,17 @@ def test_traffic_is_reported_only_for_the_captured_kernel_and_case(monkeypatch):
 def test_workload_names_match_sizes(k):
     name = bench.workload_name(_args(workload=k))
     assert isinstance(name, str) and name
+
+
+def test_roofline_kernel_is_the_bin_with_most_bytes():
+    nb = 14
+    st = {k: [0] * nb for k in ("count", "nnz_b", "products", "nnz")}
+    # a lane-group bin and the dense bin: the dense one moves more bytes
+    st["count"][6], st["nnz_b"][6], st["products"][6], st["nnz"][6] = 12742, 60000, 2060514, 2053110
+    st["count"][13], st["nnz_b"][13], st["products"][13], st["nnz"][13] = 90338, 1500000, 669840362, 387843925
+    assert bench.dominant_bin(st, 8) == 13
+    st["count"][13] = st["nnz_b"][13] = st["products"][13] = st["nnz"][13] = 0
+    assert bench.dominant_bin(st, 8) == 6
+    # the empty-column bin never counts
+    st["count"][0] = 10 ** 6
+    assert bench.dominant_bin(st, 8) == 6
