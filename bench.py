@@ -2,12 +2,16 @@
 
 A step is one pass of the whole hot path over the workload: input
 validation, Op_j and binning, symbolic pass, scan, numeric pass with sorted
-output (spgemm_symbolic + spgemm_numeric through the C ABI).  Default
-workload: C = A x A with A an R-MAT power-law matrix (2^18 rows, a,b,c,d =
-0.57,0.19,0.19,0.05, 8 edges per row drawn, columns capped at 2000 entries,
-FP64 values U[-1,1]), the largest single product of the workload set.
+output (spgemm_symbolic + spgemm_numeric through the C ABI, a new plan every
+step).  Default workload: C = A x A with A an R-MAT power-law matrix (2^18
+rows, a,b,c,d = 0.57,0.19,0.19,0.05, 8 edges per row drawn, columns capped at
+2000 entries, FP64 values U[-1,1]), the largest single product of the
+workload set.  The line also carries the random 2^20 product (the hash
+regime), the 512-product batch, the Galerkin backward and a sweep of the
+threshold t, each with its own roofline figures.
 
-Metric: GFLOP/s = 2 x sum_j Op_j / step time (Op_j = products of column j).
+Metric: GFLOP/s = 2 x sum_j Op_j / step time (Op_j = products of column j);
+the step time is the median of K CUDA-event timed steps.
 Roofline: the binned numeric pass, algorithmic bytes over its event-timed
 duration against the measured HBM copy bandwidth.
 
@@ -35,9 +39,17 @@ WORKLOADS = {
     1: "C=AxA 2D 5-point Laplacian 32x32, FP64",
 }
 L2_FLUSH_BYTES = 512 << 20
+METRIC = "SpGEMM GFLOP/s (2 x intermediate products / s)"
+INF = (1 << 63) - 1
+BIN_NAMES = (["empty"] + [f"hash_group_op<={o}" for o in (8, 16, 32, 64, 128, 256)]
+             + [f"hash_cta_op<={o}" for o in (512, 1024, 2048, 4096, 8192)] + ["hash_global", "dense_spa"])
+DENSE_BIN = 13
+# thresholds of the sweep (Section 5.4 varies t the same way; t = 0 sends
+# every column to the dense SPA, t = infinity every column to hash tables)
+SWEEP_T = [0, 20, 30, 40, 50, 60, INF]
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
@@ -47,7 +59,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-aux", action="store_true",
-                   help="skip the batched (512 products) and backward (Galerkin 40^3) measurements")
+                   help="skip the other workloads (random 2^20, batch, backward) and the t sweep")
+    p.add_argument("--no-sweep", action="store_true", help="skip the sweep of the threshold t")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU seconds of the oracle sample")
     p.add_argument("--t", type=int, default=None,
@@ -58,7 +71,7 @@ def parse():
                    help="bytes of workspace for dense-column SPA flags kept between phases")
     p.add_argument("--rmat-scale", type=int, default=18,
                    help="log2 size of the R-MAT workload (smaller for profiler captures)")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def peaks():
@@ -70,27 +83,35 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# DRAM bytes (read + write) of one launch of the dominant kernel, R-MAT 2^18
-# default configuration, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, 1 pass; profiles/k_num_dense_rmat18_traffic.md).
-# Valid only for the kernel sources it was taken with: the hash below covers
-# the files that define that kernel, and any change there reports null.
-MEASURED_TRAFFIC = {"bin": 13, "scale": 18, "bytes": 2.12e9 + 6.43e9, "sources_sha256_16": "364fef5be9c87077",
-                    "sources": ("spgemm_internal.cuh", "kernels.cuh", "columns.cuh", "numeric.cu")}
+# DRAM bytes (read + write) of one launch of the dominant kernel from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the
+# R-MAT workload at `scale`, with the algorithmic bytes of that launch; a
+# launch of another size reports the captured bytes scaled by its
+# algorithmic bytes.  Valid only for the kernel sources it was taken with:
+# the hash below covers the files that define that kernel, and any change
+# there reports null.
+MEASURED_TRAFFIC = None
 
 
-def measured_traffic(top_bin, args):
+def measured_traffic(top_bin, top_bytes, args):
+    """(bytes, source) of the dominant kernel's DRAM traffic, or (None, why)."""
     import hashlib
     t = MEASURED_TRAFFIC
+    if t is None:
+        return None, "no capture of the current kernel sources"
     default_cfg = args.t is None and args.cta_threads is None and args.dense_cache is None
-    if args.workload != 3 or args.rmat_scale != t["scale"] or top_bin != t["bin"] or not default_cfg:
-        return None
+    if args.workload != 3 or top_bin != t["bin"] or not default_cfg:
+        return None, "no capture of this kernel, workload or configuration"
     h = hashlib.sha256()
-    root = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2303_02471_gb300", "csrc")
+    root = os.path.join(ROOT, "paper_2303_02471_gb300", "csrc")
     for f in t["sources"]:
         with open(os.path.join(root, f), "rb") as fh:
             h.update(fh.read())
-    return int(t["bytes"]) if h.hexdigest()[:16] == t["sources_sha256_16"] else None
+    if h.hexdigest()[:16] != t["sources_sha256_16"]:
+        return None, "kernel sources changed since the capture"
+    scaled = int(round(t["bytes"] * top_bytes / t["algorithmic_bytes"]))
+    return scaled, (f"ncu capture (one pass) of R-MAT 2^{t['scale']}, {t['bytes']:.4g} B per launch, "
+                    f"scaled by algorithmic bytes {top_bytes:.4g} / {t['algorithmic_bytes']:.4g}")
 
 
 def algorithmic_bytes(A, B, products, nnzC, w):
@@ -101,6 +122,17 @@ def algorithmic_bytes(A, B, products, nnzC, w):
     nnzB = int(B.colptr[-1])
     return (8 * (nB + 1) + nnzB * (4 + w) + 16 * nnzB + products * (4 + w)
             + 8 * (nB + 1) + nnzC * (4 + w))
+
+
+def backward_bytes(A, B, products, nnzC, w, need_dA=True, need_dB=True):
+    """Backward of one product, per launch set: B columns (colptr, rows,
+    values), the gathered A column pointers and A entries (row and value) of
+    every product, C's pattern and dC read once, dA and dB written once."""
+    nB = B.ncols
+    nnzA = int(A.colptr[-1])
+    nnzB = int(B.colptr[-1])
+    return (8 * (nB + 1) + nnzB * (4 + w) + 16 * nnzB + products * (4 + w)
+            + 8 * (nB + 1) + nnzC * (4 + w) + (nnzA * w if need_dA else 0) + (nnzB * w if need_dB else 0))
 
 
 # ------------------------------------------------------------------ clocks
@@ -205,36 +237,45 @@ def column_sample(B, frac, seed=0):
                            values=B.values[idx]), cols
 
 
-def cpu_baseline(A, B, target_s, unit):
-    """The oracle as it stands, on a bounded column sample, all host cores."""
+def oracle_rate(A, B, op, threads, target_s, seed):
+    """GFLOP/s of the oracle on `threads` host threads over a seeded column
+    sample of B sized for about target_s seconds (whole product when it fits)."""
     import oracle
-    cores = len(os.sched_getaffinity(0))
-    op = oracle.op_counts(A, B)
-    threads = oracle.threads(cores)
-    # estimate the rate on a small sample, then size the timed one
-    small, cols = column_sample(B, 0.005, seed=1)
+    small, cols = column_sample(B, 0.005, seed=seed)
     t0 = time.perf_counter()
     oracle.spgemm(A, small, nthreads=threads)
     rate = max(1.0, op[cols].sum()) / max(1e-3, time.perf_counter() - t0)
     frac = min(1.0, target_s * rate / max(1, op.sum()))
-    sample, cols = column_sample(B, frac, seed=2)
+    sample, cols = column_sample(B, frac, seed=seed + 1)
     products = int(op[cols].sum())
     t0 = time.perf_counter()
     oracle.spgemm(A, sample, nthreads=threads)
     dt = time.perf_counter() - t0
-    return {"value": 2.0 * products / dt / 1e9, "unit": unit, "cores": threads, "kind": "oracle",
-            "sample": f"{len(cols)} of {B.ncols} columns of B (seeded, p={frac:.4f}), "
-                      f"{products} products, {dt:.2f} s"}
+    return 2.0 * products / dt / 1e9, (f"{len(cols)} of {B.ncols} columns of B (seeded, p={frac:.4f}), "
+                                       f"{products} products, {dt:.2f} s")
+
+
+def cpu_baseline(A, B, target_s, unit):
+    """The oracle as it stands on all host cores (bounded column sample),
+    and on one thread (a smaller sample)."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    op = oracle.op_counts(A, B)
+    threads = oracle.threads(cores)
+    value, sample = oracle_rate(A, B, op, threads, target_s, seed=1)
+    v1, s1 = oracle_rate(A, B, op, 1, max(1.0, target_s / 4), seed=3)
+    return {"value": value, "unit": unit, "cores": threads, "kind": "oracle", "sample": sample,
+            "single_thread": {"value": v1, "unit": unit, "cores": 1, "sample": s1}}
 
 
 # ------------------------------------------------------------------ arms
-REFERENCE_BUDGET_S = 60.0  # host seconds of the whole reference run
+REFERENCE_BUDGET_S = 240.0  # host seconds of the whole reference run at most
 
 
 def run_reference(args, rank, world):
     """The oracle as it stands on the host cores, as the other arm: W untimed
-    and K timed steps, every step the same seeded column sample of the
-    workload, sized so that the whole run takes about a minute."""
+    and K timed steps, every step the whole workload product (a seeded
+    column sample only if the whole product would not fit the budget)."""
     unit = "GFLOP/s"
     if rank != 0:
         return None
@@ -248,148 +289,227 @@ def run_reference(args, rank, world):
     oracle.spgemm(A, small, nthreads=threads)
     rate = max(1.0, op[cols].sum()) / max(1e-3, time.perf_counter() - t0)
     per_step = REFERENCE_BUDGET_S / max(1, args.warmup + args.steps)
-    frac = min(1.0, per_step * rate / max(1, op.sum()))
-    sample, cols = column_sample(B, frac, seed=2)
+    frac = 1.0 if op.sum() <= per_step * rate else per_step * rate / max(1, op.sum())
+    if frac >= 1.0:
+        sample, cols = B, np.arange(B.ncols)
+    else:
+        sample, cols = column_sample(B, frac, seed=2)
     products = int(op[cols].sum())
     for _ in range(args.warmup):
         oracle.spgemm(A, sample, nthreads=threads)
-    t0 = time.perf_counter()
+    times = []
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         oracle.spgemm(A, sample, nthreads=threads)
-    dt = time.perf_counter() - t0
-    value = 2.0 * products * args.steps / dt / 1e9
+        times.append(time.perf_counter() - t0)
+    dt = float(np.median(times))
+    value = 2.0 * products / dt / 1e9
+    what = ("the whole product" if frac >= 1.0 else
+            f"{len(cols)} of {B.ncols} columns of B (seeded, p={frac:.4f})")
     base = {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
-            "sample": f"{len(cols)} of {B.ncols} columns of B per step (seeded, p={frac:.4f}), "
-                      f"{products} products, {args.steps} timed steps in {dt:.2f} s"}
-    return {"impl": "reference", "metric": "SpGEMM GFLOP/s (2 x intermediate products / s)",
+            "sample": f"{what} per step, {products} products, median of {args.steps} timed steps "
+                      f"{dt:.3f} s"}
+    return {"impl": "reference", "metric": METRIC,
             "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / max(1, args.steps), 3),
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(args)},
+            "data": "synthetic", "config": {"workload": workload_name(args), "same_config": frac >= 1.0},
             "cpu_baseline": base,
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+class Product:
+    """One workload product on the device, stepped through the C ABI."""
+
+    def __init__(self, A_h, B_h, dev, cfg):
+        import torch
+        from paper_2303_02471_gb300 import _native as N
+        from paper_2303_02471_gb300 import ops
+        self.N, self.ops, self.torch = N, ops, torch
+        self.A_h, self.B_h = A_h, B_h
+        self.A = ops.CscMatrix.from_host(A_h, device=dev)
+        self.B = self.A if B_h is A_h else ops.CscMatrix.from_host(B_h, device=dev)
+        self.cfg = cfg
+        self.ncfg = cfg.native()
+        self.lib = N.lib()
+        self.hd = ops.handle(dev)
+        self.stream = torch.cuda.current_stream()
+        self.sp = ctypes.c_void_p(self.stream.cuda_stream)
+        self.cA, self.cB = ops._csc(self.A), ops._csc(self.B)
+        self.ws = torch.empty(ops.workspace_size(self.A, self.B, cfg), dtype=torch.uint8, device=dev)
+        self.colptr = torch.empty(self.B.ncols + 1, dtype=torch.int64, device=dev)
+        plan = self.plan()
+        info = plan.info()
+        self.stats = plan.bin_stats()
+        self.stats["count"] = info["bins"]
+        self.products = info["products"]
+        self.t = info["t"]
+        self.nnz = plan.nnz
+        self.side = plan.bin_streams()
+        lc = plan.launch_count()
+        self.launches = lc["symbolic"] + lc["numeric"]
+        plan.destroy()
+        self.rowidx = torch.empty(self.nnz, dtype=torch.int32, device=dev)
+        self.values = torch.empty(self.nnz, dtype=self.A.dtype, device=dev)
+
+    def plan(self):
+        N, ops = self.N, self.ops
+        nnz, h = ctypes.c_int64(), ctypes.c_void_p()
+        N.check(self.lib.spgemm_symbolic(self.hd.ptr, ctypes.byref(self.cA), ctypes.byref(self.cB),
+                                         ctypes.byref(self.ncfg), ctypes.c_void_p(self.ws.data_ptr()),
+                                         self.ws.numel(), ctypes.c_void_p(self.colptr.data_ptr()),
+                                         ctypes.byref(nnz), ctypes.byref(h), self.sp), "spgemm_symbolic")
+        return ops.Plan(h, self.ws, self.A, self.B, self.colptr, nnz.value, self.cfg, self.hd)
+
+    def numeric(self, plan):
+        self.N.check(self.lib.spgemm_numeric(plan.handle, ctypes.byref(self.cA), ctypes.byref(self.cB),
+                                             ctypes.c_void_p(self.colptr.data_ptr()),
+                                             ctypes.c_void_p(self.rowidx.data_ptr()),
+                                             ctypes.c_void_p(self.values.data_ptr()), self.sp),
+                     "spgemm_numeric")
+
+
+def time_steps(prod, steps, warmup, flush, world=1, clocks=None, bin_timing=True):
+    """W untimed and K timed steps (a new plan every step); per-step events
+    (whole step, symbolic, numeric) and the bin times of every step."""
+    import torch
+    stream = prod.stream
+    for _ in range(warmup):
+        plan = prod.plan()
+        prod.numeric(plan)
+        plan.check()
+        plan.destroy()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    bin_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    for i in range(steps):
+        flush.fill_(i & 0xff)  # evict A and B from L2 between steps
+        ev[i][0].record(stream)
+        plan = prod.plan()
+        if bin_timing:
+            plan.set_timing(True)
+        ev[i][1].record(stream)
+        prod.numeric(plan)
+        ev[i][2].record(stream)
+        plan.check()
+        if bin_timing:
+            bin_ms.append(plan.bin_times())
+        plan.destroy()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    step = [a.elapsed_time(c) for a, b, c in ev]
+    sym = [a.elapsed_time(b) for a, b, c in ev]
+    num = [b.elapsed_time(c) for a, b, c in ev]
+    return {"step": step, "sym": sym, "num": num, "bins": bin_ms, "clocks": clk}
+
+
+def serial_bin_times(A_h, B_h, dev, cfg, flush, repeats=3):
+    """Every bin kernel of the numeric pass timed on its own: a plan whose
+    bins all run in order on the caller's stream (no side streams), median
+    of `repeats` timed numeric calls."""
+    from dataclasses import replace
+    import torch
+    prod = Product(A_h, B_h, dev, replace(cfg, side_streams=False))
+    plan = prod.plan()
+    plan.set_timing(True)
+    prod.numeric(plan)
+    plan.check()
+    out = []
+    for i in range(repeats):
+        flush.fill_(i & 0xff)
+        prod.numeric(plan)
+        out.append(plan.bin_times())
+    plan.check()
+    plan.destroy()
+    torch.cuda.synchronize()
+    return np.median(np.array(out), axis=0)
+
+
+def product_report(prod, res, serial, peak, peak_kind, args, w=8):
+    """Roofline of the dominant bin kernel and of the whole numeric pass,
+    phase medians and per-bin figures of one product."""
+    st = prod.stats
+    top = dominant_bin(st, w)
+    top_bytes = bin_bytes(st, top, w)
+    live = np.median(np.array(res["bins"]), axis=0) if res["bins"] else serial
+    # a bin on a side stream has event times that include waiting for SMs:
+    # its roofline takes the serialised time
+    top_ms = float(serial[top] if prod.side[top] else live[top])
+    top_ach = top_bytes / (top_ms * 1e-3) / 1e9
+    alg = algorithmic_bytes(prod.A_h, prod.B_h, prod.products, prod.nnz, w)
+    num_ms = float(np.median(res["num"]))
+    achieved = alg / (num_ms * 1e-3) / 1e9
+    traffic, tsrc = measured_traffic(top, top_bytes, args) if args is not None else (None, "not captured")
+    roof = {"bound": "hbm", "achieved": round(top_ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(top_ach / peak, 4), "traffic": traffic, "traffic_source": tsrc,
+            "kernel": f"numeric bin {top} ({BIN_NAMES[top]})", "ms": round(top_ms, 4),
+            "ms_source": "serialised pass" if prod.side[top] else "bench steps (caller's stream)",
+            "algorithmic_bytes": int(top_bytes), "peak_kind": peak_kind,
+            "numeric_pass": {"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
+                             "ms": round(num_ms, 4), "algorithmic_bytes": int(alg)}}
+    per_bin = {BIN_NAMES[b]: {"ms_alone": round(float(serial[b]), 4), "cols": st["count"][b],
+                              "products": st["products"][b], "nnz": st["nnz"][b],
+                              "GBps_alone": round(bin_bytes(st, b, w) / (serial[b] * 1e-3) / 1e9, 1)
+                              if serial[b] > 0 else None,
+                              "stream_in_steps": "side" if prod.side[b] else "caller"}
+               for b in range(1, len(serial)) if st["count"][b]}
+    return roof, per_bin
+
+
+def measure_workload(k, args, dev, flush, steps, warmup, peak, peak_kind, cfg=None):
+    """Steps, roofline and per-bin figures of workload k (a side entry)."""
+    from paper_2303_02471_gb300 import ops
+    A_h, B_h = make_workload(k)
+    cfg = cfg or ops.Config()
+    prod = Product(A_h, B_h, dev, cfg)
+    res = time_steps(prod, steps, warmup, flush)
+    serial = serial_bin_times(A_h, B_h, dev, cfg, flush)
+    roof, per_bin = product_report(prod, res, serial, peak, peak_kind, None)
+    ms = float(np.median(res["step"]))
+    out = {"workload": WORKLOADS[k], "products": int(prod.products), "nnz_C": int(prod.nnz), "t": prod.t,
+           "value": round(2.0 * prod.products / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+           "ms_per_step": round(ms, 4),
+           "phases_ms": {"symbolic": round(float(np.median(res["sym"])), 4),
+                         "numeric": round(float(np.median(res["num"])), 4)},
+           "roofline": roof, "numeric_bins": per_bin, "launches_per_step": prod.launches}
+    del prod
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
-    from paper_2303_02471_gb300 import _native as N
     from paper_2303_02471_gb300 import ops
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     A_h, B_h = make_workload(args.workload, args.rmat_scale)
     w = 8
-    A = ops.CscMatrix.from_host(A_h, device=dev)
-    B = A if B_h is A_h else ops.CscMatrix.from_host(B_h, device=dev)
     cfg = ops.Config(t=args.t, dense_cache_bytes=args.dense_cache, cta_threads=args.cta_threads)
-    ncfg = cfg.native()
-    lib = N.lib()
-    stream = torch.cuda.current_stream()
-    sp = ctypes.c_void_p(stream.cuda_stream)
-    cA, cB = ops._csc(A), ops._csc(B)
-    ws = torch.empty(ops.workspace_size(A, B, cfg), dtype=torch.uint8, device=dev)
-    colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=dev)
+    prod = Product(A_h, B_h, dev, cfg)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    def symbolic():
-        nnz, h = ctypes.c_int64(), ctypes.c_void_p()
-        N.check(lib.spgemm_symbolic(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(ncfg),
-                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(),
-                                    ctypes.c_void_p(colptr.data_ptr()), ctypes.byref(nnz),
-                                    ctypes.byref(h), sp), "spgemm_symbolic")
-        return h, nnz.value
-
-    h, nnz = symbolic()
-    first = ops.Plan(h, ws, A, B, colptr, nnz, cfg)
-    info = first.info()
-    st = first.bin_stats()
-    st["count"] = info["bins"]
-    products = info["products"]
-    lc = first.launch_count()
-    launches_per_step = lc["symbolic"] + lc["numeric"]
-    first.destroy()
-    rowidx = torch.empty(nnz, dtype=torch.int32, device=dev)
-    values = torch.empty(nnz, dtype=torch.float64, device=dev)
-
-    def numeric(plan):
-        N.check(lib.spgemm_numeric(plan.handle, ctypes.byref(cA), ctypes.byref(cB),
-                                   ctypes.c_void_p(colptr.data_ptr()),
-                                   ctypes.c_void_p(rowidx.data_ptr()),
-                                   ctypes.c_void_p(values.data_ptr()), sp), "spgemm_numeric")
-
-    def plan_of(hh, n):
-        return ops.Plan(hh, ws, A, B, colptr, n, cfg)
-
-    for _ in range(args.warmup):
-        plan = plan_of(*symbolic())
-        numeric(plan)
-        plan.check()
-        plan.destroy()
-    torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    bin_ms = []
-    clocks = ClockSampler()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    for i in range(args.steps):
-        flush.fill_(i & 0xff)  # evict A and B from L2 between steps
-        ev[i][0].record(stream)
-        plan = plan_of(*symbolic())
-        plan.set_timing(True)
-        ev[i][1].record(stream)
-        numeric(plan)
-        ev[i][2].record(stream)
-        plan.check()
-        bin_ms.append(plan.bin_times())
-        plan.destroy()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    num_ms = [b.elapsed_time(c) for a, b, c in ev]
-    ms = float(np.mean(step_ms))
+    res = time_steps(prod, args.steps, args.warmup, flush, world, ClockSampler())
+    ms = float(np.median(res["step"]))
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
+    products = prod.products
     value = world * 2.0 * products / (ms * 1e-3) / 1e9
-
-    # roofline: the dominant kernel (the bin kernel with the most algorithmic
-    # bytes) and the whole binned numeric pass.  Beside a dense bin the
-    # lane-group bins run on side streams: their event times start with the
-    # pass and include waiting for SMs, so they do not pick the kernel.
     peak, peak_kind = peaks()
-    bms = np.mean(np.array(bin_ms), axis=0)
-    top = dominant_bin(st, w)
-    side = bool(st["count"][13]) and any(st["count"][b] for b in range(1, 7))
-    top_bytes = bin_bytes(st, top, w)
-    top_ach = top_bytes / (bms[top] * 1e-3) / 1e9
-    alg = algorithmic_bytes(A_h, B_h, products, nnz, w)
-    num_avg = float(np.mean(num_ms))
-    achieved = alg / (num_avg * 1e-3) / 1e9
-    names = ["empty"] + [f"hash_group_op<={o}" for o in (8, 16, 32, 64, 128, 256)] + \
-        [f"hash_cta_op<={o}" for o in (512, 1024, 2048, 4096, 8192)] + ["hash_global", "dense_spa"]
-    roof = {"bound": "hbm", "achieved": round(top_ach, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(top_ach / peak, 4), "traffic": measured_traffic(top, args),
-            "kernel": f"numeric bin {top} ({names[top]})", "ms": round(float(bms[top]), 4),
-            "algorithmic_bytes": int(top_bytes), "peak_kind": peak_kind,
-            "numeric_pass": {"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
-                             "ms": round(num_avg, 4), "algorithmic_bytes": int(alg)}}
-    per_bin = {names[b]: {"ms": round(float(bms[b]), 4), "cols": st["count"][b],
-                          "products": st["products"][b], "nnz": st["nnz"][b],
-                          "GBps": round(bin_bytes(st, b, w) / (bms[b] * 1e-3) / 1e9, 1),
-                          "stream": "side" if side and 1 <= b <= 6 else "caller"}
-               for b in range(1, len(bms)) if st["count"][b]}
+    serial = serial_bin_times(A_h, B_h, dev, cfg, flush)
+    roof, per_bin = product_report(prod, res, serial, peak, peak_kind, args, w)
 
     # end to end through host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world)
+        e2e = run_e2e(args, A_h, B_h, products, prod, dev, world)
 
     line = None
     if rank == 0:
@@ -398,19 +518,29 @@ def run_ours(args, rank, world):
             base = cpu_baseline(A_h, B_h, args.cpu_seconds, "GFLOP/s")
         aux = {}
         if not args.no_aux:
-            aux = {"batched": run_batched(args, dev), "backward": run_backward(args, dev)}
-        line = {"metric": "SpGEMM GFLOP/s (2 x intermediate products / s)", "value": round(value, 3),
+            peak_w = (peak, peak_kind)
+            others = {}
+            for k in (2, 3):
+                if k != args.workload:
+                    others[str(k)] = measure_workload(k, args, dev, flush, max(3, min(args.steps, 10)), 3, *peak_w)
+            aux = {"workloads": others, "batched": run_batched(args, dev, *peak_w),
+                   "backward": run_backward(args, dev, *peak_w)}
+            if not args.no_sweep:
+                aux["t_sweep"] = run_t_sweep(args, dev, flush)
+        line = {"metric": METRIC, "value": round(value, 3),
                 "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": round(ms, 4), "ms_per_step_mean": round(float(np.mean(res["step"])), 4),
+                "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name(args), "t": info["t"], "products": int(products),
-                           "nnz_C": int(nnz), "l2": "512 MiB buffer written between timed steps",
+                "config": {"workload": workload_name(args), "t": prod.t, "products": int(products),
+                           "nnz_C": int(prod.nnz), "l2": "512 MiB buffer written between timed steps",
+                           "timing": "median of per-step CUDA events",
                            "parallelism": f"replicas x{world}"},
-                "phases_ms": {"symbolic": round(float(np.mean([a.elapsed_time(b) for a, b, c in ev])), 4),
-                              "numeric": round(num_avg, 4)},
+                "phases_ms": {"symbolic": round(float(np.median(res["sym"])), 4),
+                              "numeric": round(float(np.median(res["num"])), 4)},
                 "roofline": roof, "numeric_bins": per_bin, "cpu_baseline": base, "e2e": e2e, **aux,
-                "gpu_launches": launches_per_step * args.steps,
-                "clocks": clk}
+                "gpu_launches": prod.launches * args.steps,
+                "clocks": res["clocks"]}
     return line
 
 
@@ -419,10 +549,12 @@ def _events(n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
-def run_batched(args, dev):
+def run_batched(args, dev, peak, peak_kind):
     """The 512-product batch: autotuned persistent launches (symbolic + numeric,
-    numeric replayed from a CUDA graph) against the plain per-matrix calls."""
+    numeric replayed from a CUDA graph) against the plain per-matrix calls
+    through the C ABI with preallocated workspaces and outputs."""
     import torch
+    from paper_2303_02471_gb300 import _native as N
     from paper_2303_02471_gb300 import autotune, ops, synth
     pairs = synth.batch_pairs(512, seed=0)
     As = [ops.CscMatrix.from_host(A, device=dev) for A, _ in pairs]
@@ -431,50 +563,112 @@ def run_batched(args, dev):
     cfg, rep = autotune.tune(As, Bs, repeats=1)
     side = torch.cuda.Stream(device=dev)
     steps = max(3, min(args.steps, 10))
+    lib = N.lib()
+    hd = ops.handle(dev)
     with torch.cuda.stream(side):
         plan = ops.spgemm_batched_symbolic(As, Bs, cfg)
         ops.spgemm_batched_numeric(plan, As, Bs, use_graph=True)
         ops.spgemm_batched_numeric(plan, As, Bs, use_graph=True)
         plan.check()
-        ev = _events(2)
-        ev[0].record(side)
+        ms = []
         for _ in range(steps):
+            ev = _events(2)
+            ev[0].record(side)
             ops.spgemm_batched_numeric(plan, As, Bs, use_graph=True)
-        ev[1].record(side)
-        side.synchronize()
-        num_ms = ev[0].elapsed_time(ev[1]) / steps
-        ev = _events(2)
-        ev[0].record(side)
+            ev[1].record(side)
+            side.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        num_ms = float(np.median(ms))
+        ms = []
         for _ in range(steps):
+            ev = _events(2)
+            ev[0].record(side)
             p2 = ops.spgemm_batched_symbolic(As, Bs, cfg)
             ops.spgemm_batched_numeric(p2, As, Bs)
+            ev[1].record(side)
+            side.synchronize()
             p2.destroy()
-        ev[1].record(side)
-        side.synchronize()
-        step_ms = ev[0].elapsed_time(ev[1]) / steps
+            ms.append(ev[0].elapsed_time(ev[1]))
+        step_ms = float(np.median(ms))
         plan.check()
-        # plain per-matrix calls, same products
-        for A, B in zip(As[:8], Bs[:8]):
-            ops.spgemm(A, B, cfg)
+        nnzs = plan.nnz
+        # the plain per-matrix calls through the C ABI, every buffer allocated
+        # beforehand: per product a symbolic call (it synchronises to read
+        # nnz back) and a numeric call
+        sp = ctypes.c_void_p(side.cuda_stream)
+        prep = []
+        for A, B, n in zip(As, Bs, nnzs):
+            cA, cB = ops._csc(A), ops._csc(B)
+            ncfg = cfg.native()
+            ws = torch.empty(ops.workspace_size(A, B, cfg), dtype=torch.uint8, device=dev)
+            cp = torch.empty(B.ncols + 1, dtype=torch.int64, device=dev)
+            row = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+            val = torch.empty(max(n, 1), dtype=A.dtype, device=dev)
+            prep.append((cA, cB, ncfg, ws, cp, row, val))
+
+        def plain_symbolic(x):
+            cA, cB, ncfg, ws, cp, row, val = x
+            nnz, h = ctypes.c_int64(), ctypes.c_void_p()
+            N.check(lib.spgemm_symbolic(hd.ptr, ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(ncfg),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(cp.data_ptr()),
+                                        ctypes.byref(nnz), ctypes.byref(h), sp), "spgemm_symbolic")
+            return h
+
+        def plain_numeric(x, h):
+            cA, cB, ncfg, ws, cp, row, val = x
+            N.check(lib.spgemm_numeric(h, ctypes.byref(cA), ctypes.byref(cB), ctypes.c_void_p(cp.data_ptr()),
+                                       ctypes.c_void_p(row.data_ptr()), ctypes.c_void_p(val.data_ptr()), sp),
+                    "spgemm_numeric")
+
+        for x in prep[:8]:
+            h = plain_symbolic(x)
+            plain_numeric(x, h)
+            lib.spg_plan_destroy(h)
+        side.synchronize()
         ev = _events(2)
         ev[0].record(side)
-        for A, B in zip(As, Bs):
-            C, pl = ops.spgemm(A, B, cfg)
-            pl.destroy()
+        for x in prep:
+            h = plain_symbolic(x)
+            plain_numeric(x, h)
+            lib.spg_plan_destroy(h)
         ev[1].record(side)
         side.synchronize()
         plain_ms = ev[0].elapsed_time(ev[1])
+        # the plain numeric calls alone, the plans made beforehand (the same
+        # work as the batched numeric launch, one launch set per product)
+        hs = [plain_symbolic(x) for x in prep]
+        side.synchronize()
+        ev = _events(2)
+        ev[0].record(side)
+        for x, h in zip(prep, hs):
+            plain_numeric(x, h)
+        ev[1].record(side)
+        side.synchronize()
+        plain_num_ms = ev[0].elapsed_time(ev[1])
+        for h in hs:
+            N.check(lib.spg_plan_check(h, sp), "spg_plan_check")
+            lib.spg_plan_destroy(h)
+        del prep
     launches = plan.info()["launches"]
+    alg = sum(algorithmic_bytes(A, B, A.ncols * (A.colptr[1] - A.colptr[0]) ** 2, n,
+                                8 if A.values.dtype == np.float64 else 4)
+              for (A, B), n in zip(pairs, nnzs))
+    ach = alg / (num_ms * 1e-3) / 1e9
     gf = lambda ms: round(2.0 * products / (ms * 1e-3) / 1e9, 3)
     return {"workload": "512 products C_i = A_i x B_i, n_i log-uniform 500..20000, Z_i ~ U{2..40}, "
-                        "half f64 half f32", "products": products,
+                        "half f64 half f32", "products": products, "nnz_C": int(sum(nnzs)),
             "config": rep["config"], "GFLOPs_batched_step": gf(step_ms), "ms_batched_step": round(step_ms, 3),
             "GFLOPs_batched_numeric_graph": gf(num_ms), "ms_batched_numeric_graph": round(num_ms, 3),
             "GFLOPs_plain_per_matrix": gf(plain_ms), "ms_plain_per_matrix": round(plain_ms, 3),
+            "GFLOPs_plain_numeric_only": gf(plain_num_ms), "ms_plain_numeric_only": round(plain_num_ms, 3),
+            "plain": "512 x (spgemm_symbolic + spgemm_numeric) through the C ABI, buffers preallocated",
+            "roofline": {"bound": "hbm", "kernel": "k_batched numeric (one persistent launch, graph replay)",
+                         "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "algorithmic_bytes": int(alg), "ms": round(num_ms, 4), "peak_kind": peak_kind},
             "launches_symbolic_numeric": launches[:2]}
 
 
-def run_backward(args, dev):
+def run_backward(args, dev, peak, peak_kind):
     """Galerkin product P^T (A P) on the 40^3 Laplacian: forward (two products
     and the transpose) against the backward (two masked-product passes)."""
     import torch
@@ -504,25 +698,88 @@ def run_backward(args, dev):
         backward()
     torch.cuda.synchronize()
     steps = max(3, min(args.steps, 20))
-    ev = _events(4)
-    ev[0].record(stream)
+    fw, bw = [], []
     for _ in range(steps):
+        ev = _events(4)
+        ev[0].record(stream)
         forward()
-    ev[1].record(stream)
-    ev[2].record(stream)
-    for _ in range(steps):
+        ev[1].record(stream)
+        ev[2].record(stream)
         backward()
-    ev[3].record(stream)
-    torch.cuda.synchronize()
-    f_ms = ev[0].elapsed_time(ev[1]) / steps
-    b_ms = ev[2].elapsed_time(ev[3]) / steps
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        fw.append(ev[0].elapsed_time(ev[1]))
+        bw.append(ev[2].elapsed_time(ev[3]))
+    f_ms, b_ms = float(np.median(fw)), float(np.median(bw))
+    Mh, Pth = M.to_host(), Pt.to_host()
+    alg = (backward_bytes(Pth, Mh, pc.info()["products"], C.nnz, 8)
+           + backward_bytes(A_h, P_h, pm.info()["products"], M.nnz, 8, need_dA=False))
+    ach = alg / (b_ms * 1e-3) / 1e9
     gf = lambda ms: round(2.0 * products / (ms * 1e-3) / 1e9, 3)
     return {"workload": "Galerkin P^T (A P), A 40^3 7-point Laplacian, P 64000 x 8000 aggregation",
             "products": int(products), "ms_forward": round(f_ms, 4), "ms_backward": round(b_ms, 4),
-            "GFLOPs_forward": gf(f_ms), "GFLOPs_backward": gf(b_ms)}
+            "GFLOPs_forward": gf(f_ms), "GFLOPs_backward": gf(b_ms),
+            "forward": "two spgemm calls (symbolic + numeric, synchronising) and the transpose of P",
+            "roofline_backward": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                                  "frac": round(ach / peak, 4), "algorithmic_bytes": int(alg),
+                                  "ms": round(b_ms, 4), "peak_kind": peak_kind,
+                                  "note": "about 1.2M products: launch-bound, not bandwidth-bound"}}
 
 
-def run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world):
+def run_t_sweep(args, dev, flush):
+    """GFLOP/s of a whole step for t in SWEEP_T and the library's default t,
+    on the random 2^20 product and the R-MAT 2^18 product; and of a batched
+    step (symbolic + numeric) on the 512-product batch for the same t and the
+    autotuner's choice; with the speed-up over t = 0 (every column in the
+    dense SPA, Section 3.3)."""
+    import torch
+    from paper_2303_02471_gb300 import autotune, ops, synth
+    out = {}
+    for k in (2, 3):
+        A_h, B_h = make_workload(k)
+        row = {}
+        for t in SWEEP_T + [None]:
+            prod = Product(A_h, B_h, dev, ops.Config(t=t))
+            res = time_steps(prod, 3, 1, flush, bin_timing=False)
+            ms = float(np.median(res["step"]))
+            key = "inf" if t == INF else ("default(%d)" % prod.t if t is None else str(t))
+            row[key] = round(2.0 * prod.products / (ms * 1e-3) / 1e9, 3)
+            del prod
+        base = row["0"]
+        out[str(k)] = {"GFLOPs": row, "speedup_vs_t0": {k2: round(v / base, 3) for k2, v in row.items()}}
+    pairs = synth.batch_pairs(512, seed=0)
+    As = [ops.CscMatrix.from_host(A, device=dev) for A, _ in pairs]
+    Bs = [ops.CscMatrix.from_host(B, device=dev) for _, B in pairs]
+    products = int(sum(A.ncols * (A.colptr[1] - A.colptr[0]) ** 2 for A, _ in pairs))
+    tuned, _ = autotune.tune(As, Bs, repeats=1)
+    row = {}
+    stream = torch.cuda.current_stream()
+    for name, cfg in [(("inf" if t == INF else str(t)), ops.Config(t=t)) for t in SWEEP_T] + [
+            ("autotuned", tuned)]:
+        try:
+            ms = []
+            for i in range(4):
+                ev = _events(2)
+                ev[0].record(stream)
+                p = ops.spgemm_batched_symbolic(As, Bs, cfg)
+                ops.spgemm_batched_numeric(p, As, Bs)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                p.destroy()
+                if i:
+                    ms.append(ev[0].elapsed_time(ev[1]))
+            row[name] = round(2.0 * products / (float(np.median(ms)) * 1e-3) / 1e9, 3)
+        except RuntimeError as e:  # a threshold the batched kernels do not take
+            row[name] = str(e)
+    base = row.get("0")
+    out["4"] = {"GFLOPs": row, "speedup_vs_t0": {k2: round(v / base, 3) for k2, v in row.items()
+                                                  if isinstance(v, float) and isinstance(base, float)},
+                "autotuned_config": {"t": tuned.t, "hash_cta_max": tuned.hash_cta_max,
+                                     "cta_threads": tuned.cta_threads}}
+    return out
+
+
+def run_e2e(args, A_h, B_h, products, prod, dev, world):
     """Same metric with host inputs and outputs, through the C ABI: every step
     copies its inputs from pinned host memory, runs both phases and reads C
     (colptr, rows, values) back into pinned host memory.  Steps are pipelined
@@ -532,6 +789,7 @@ def run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world):
     import torch
     from paper_2303_02471_gb300 import _native as N
     from paper_2303_02471_gb300 import ops
+    lib, ncfg, cfg, hd = prod.lib, prod.ncfg, prod.cfg, prod.hd
 
     def pin(x):
         return torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
@@ -564,7 +822,7 @@ def run_e2e(args, A_h, B_h, products, lib, ncfg, cfg, dev, stream, world):
                 for d, hsrc in zip(dB, hB):
                     d.copy_(hsrc, non_blocking=True)
             nnz, h = ctypes.c_int64(), ctypes.c_void_p()
-            N.check(lib.spgemm_symbolic(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(ncfg),
+            N.check(lib.spgemm_symbolic(hd.ptr, ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(ncfg),
                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                         ctypes.c_void_p(o["colptr"].data_ptr()), ctypes.byref(nnz),
                                         ctypes.byref(h), sp), "spgemm_symbolic")

@@ -18,8 +18,10 @@
  *     double or float[nnz].  Rows inside an input column may come in any
  *     order but must not repeat.  All matrix arrays are DEVICE pointers.
  *   - The caller owns all device memory (inputs, outputs, workspace); the
- *     library never allocates device memory.  It owns only the host-side
- *     plan object (spg_plan), freed by spg_plan_destroy.
+ *     library never allocates device memory.  It owns only host-side
+ *     objects: plans (spg_plan, freed by spg_plan_destroy) and handles
+ *     (spg_handle: side streams, events and a small pinned host buffer,
+ *     freed by spg_destroy).
  *   - Every call returns spg_status; no C++ exception crosses the ABI.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Kernels
  *     are enqueued on it; calls documented as synchronising wait for it.
@@ -103,9 +105,48 @@ typedef struct {
      * columns worked one per warp (every product at most 32768 rows), and
      * their workspace grows by up to this budget. */
     int64_t dense_cache_bytes;
+    /* Nonzero (default): next to a dense bin, the bins that use no workspace
+     * scratch run on the side streams, overlapping the dense kernel's tail.
+     * 0: every bin runs in order on the caller's stream (then the per-bin
+     * event times of spg_plan_bin_times measure each kernel on its own). */
+    int32_t side_streams;
+    /* Test knob, normally 0: nonzero makes the dense numeric kernel give up
+     * its first wait for a column's kept flags at once, as if the bounded
+     * wait had run out.  The copy it waited for still lands (the kernel
+     * waits for it, bounded, before it exits), the columns left are not
+     * written, and spg_plan_check reports SPG_ERR_TIMEOUT: the time-out path
+     * runs without any fault. */
+    int32_t test_wait_timeout;
 } spg_config;
 
 typedef struct spg_plan spg_plan;
+
+/*
+ * Library handle: the state that outlives single products on one device.
+ * It holds the two side streams and three events onto which the symbolic
+ * and numeric calls fork their lane-group bins (joined back to the caller's
+ * stream before each call returns), and the 64 KiB mapped pinned host buffer
+ * through which the synchronising calls read small results (bin histogram,
+ * nnz(C), error word) back.  spg_create makes all of them at once for the
+ * current device, so no later call made with the handle creates a stream,
+ * an event or a host buffer; spg_destroy releases them.
+ *   - Plans made with a handle use it until they are destroyed: destroy the
+ *     plans first.
+ *   - Calls made with one handle share its side streams, so their lane-group
+ *     bins run in order; products meant to run concurrently on different
+ *     caller streams take one handle each.
+ *   - The read-back buffer is taken under a lock: a handle may be used by
+ *     several host threads.
+ *   - Every call that takes a handle also accepts NULL: the plan then
+ *     creates its own side streams on its first forked call (released with
+ *     the plan) and reads back through a buffer of the calling host thread.
+ * The paper has no counterpart (it is the GPU form of process-wide state).
+ * Errors: SPG_ERR_INVALID (NULL out pointer), SPG_ERR_CUDA (stream, event or
+ * pinned allocation failed; nothing is left allocated).
+ */
+typedef struct spg_handle spg_handle;
+spg_status spg_create(spg_handle **handle);
+spg_status spg_destroy(spg_handle *handle);
 
 /* Fill `cfg` with the defaults. */
 spg_status spg_config_default(spg_config *cfg);
@@ -135,6 +176,8 @@ spg_status spgemm_workspace_size(const spg_csc *A, const spg_csc *B,
  * Sections 3.2-3.3); per-bin column lists; nnz of every C column by the
  * bin's accumulator; exclusive scan into C_colptr.
  *
+ * handle   from spg_create on the current device, or NULL (see spg_create);
+ *          kept by the plan for its numeric, backward and check calls.
  * A, B     device CSC; values are not read.  A->ncols == B->nrows,
  *          A->dtype == B->dtype.
  * cfg      tuning (NULL = defaults); copied into the plan.
@@ -151,8 +194,9 @@ spg_status spgemm_workspace_size(const spg_csc *A, const spg_csc *B,
  * (a dimension beyond int32 rows), SPG_ERR_UNSUPPORTED (a column with
  * Op_j >= 2^31 products), SPG_ERR_TABLE_OVERFLOW, SPG_ERR_CUDA.
  */
-spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B,
-                           const spg_config *cfg, void *workspace,
+spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A,
+                           const spg_csc *B, const spg_config *cfg,
+                           void *workspace,
                            size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC,
                            spg_plan **plan, spg_stream stream);
 
@@ -171,12 +215,13 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B,
  *          summed in the input dtype (float inputs accumulate in float).
  *
  * Asynchronous: does not synchronise.  When the plan has a dense bin and
- * lane-group bins, the group bins run on two streams the plan owns (created
- * on first use, released with the plan), forked from `stream` by an event
- * and joined back to it before the call returns, so later work on `stream`
- * sees all of C; the pattern is legal on the legacy default stream and
- * under stream capture.  The symbolic call does the same for its group
- * bins.  Kernel-side errors surface in
+ * lane-group bins, the group bins run on the two side streams of the plan's
+ * handle (or, without a handle, two streams the plan creates on first use
+ * and releases with the plan), forked from `stream` by an event and joined
+ * back to it before the call returns, also when a launch fails, so later
+ * work on `stream` sees all of C; the pattern is legal on the legacy default
+ * stream and under stream capture.  The symbolic call does the same for its
+ * group bins.  Kernel-side errors surface in
  * spg_plan_check: SPG_ERR_INVALID when a column's row count differs from the
  * plan's, or when A has an entry in a row that held none when the plan was
  * made (the plan numbers only the rows of A that hold entries; such an entry
@@ -245,6 +290,11 @@ spg_status spg_plan_bin_stats(const spg_plan *plan, int64_t *bin_products,
 spg_status spg_plan_launch_count(const spg_plan *plan, int64_t *symbolic,
                                  int64_t *numeric, int64_t *backward);
 
+/* Where each bin's numeric kernel runs (host int32[nbins]): 1 on a side
+ * stream of the fork (its event times then include waiting for SMs held by
+ * the dense kernel), 0 on the caller's stream.  No device work. */
+spg_status spg_plan_bin_streams(const spg_plan *plan, int32_t *side);
+
 /* Enable (nonzero) or disable event timing of every bin kernel in later
  * spgemm_numeric calls of this plan (CUDA events, no device memory). */
 spg_status spg_plan_set_timing(spg_plan *plan, int32_t enable);
@@ -304,9 +354,12 @@ spg_status spgemm_batched_workspace_size(int32_t nb, const spg_csc *A,
 
 /* Symbolic phase of the whole batch: validation (cfg->validate), Op_j and
  * bins over all columns, one persistent kernel for nnz(C_i[:, j]), a
- * segmented scan into C_colptr.  nnzC: host int64[nb].  Synchronises. */
-spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A,
-                                   const spg_csc *B, const spg_config *cfg,
+ * segmented scan into C_colptr.  nnzC: host int64[nb].  handle: as for
+ * spgemm_symbolic (its read-back buffer serves the batch's synchronising
+ * reads), or NULL.  Synchronises. */
+spg_status spgemm_batched_symbolic(spg_handle *handle, int32_t nb,
+                                   const spg_csc *A, const spg_csc *B,
+                                   const spg_config *cfg,
                                    void *workspace, size_t ws_bytes,
                                    int64_t *C_colptr, int64_t *nnzC,
                                    spg_bplan **plan, spg_stream stream);
@@ -371,7 +424,9 @@ spg_status spg_permute_values(const void *src, const int64_t *idx, void *dst,
  *     larger ones are rejected with SPG_ERR_WORKSPACE before any device work.
  *   - The first call on a device looks up the array's device address on the
  *     current device (cudaGetSymbolAddress); make that first call before any
- *     stream capture on that device.
+ *     stream capture on that device.  The address is kept per device and
+ *     CUDA context: after a device reset, or in another context, the next
+ *     call looks it up again (so make that call outside a capture too).
  *   - All calls on a device share the array, which keeps the last call's
  *     contents (the parts that must start at zero are cleared by every
  *     call); calls whose work overlaps on the GPU race on it, so order them,

@@ -29,7 +29,8 @@ class SpgCsc(ctypes.Structure):
 
 class SpgConfig(ctypes.Structure):
     _fields_ = [("t", i64), ("hash_cta_max", i32), ("cta_threads", i32), ("validate", i32),
-                ("table_shrink", i32), ("scratch_cap_bytes", i64), ("dense_cache_bytes", i64)]
+                ("table_shrink", i32), ("scratch_cap_bytes", i64), ("dense_cache_bytes", i64),
+                ("side_streams", i32), ("test_wait_timeout", i32)]
 
 
 class SpgError(RuntimeError):
@@ -44,7 +45,9 @@ SIGNATURES = {
     "spg_config_default": (i32, [vp]),
     "spg_status_string": (ctypes.c_char_p, [i32]),
     "spgemm_workspace_size": (i32, [vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
-    "spgemm_symbolic": (i32, [vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(i64),
+    "spg_create": (i32, [ctypes.POINTER(vp)]),
+    "spg_destroy": (i32, [vp]),
+    "spgemm_symbolic": (i32, [vp, vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(i64),
                               ctypes.POINTER(vp), vp]),
     "spgemm_numeric": (i32, [vp, vp, vp, vp, vp, vp, vp]),
     "spgemm_backward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -54,6 +57,7 @@ SIGNATURES = {
     "spg_plan_op_counts": (i32, [vp, vp, vp]),
     "spg_plan_bin_stats": (i32, [vp, vp, vp, vp, vp, vp]),
     "spg_plan_launch_count": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+    "spg_plan_bin_streams": (i32, [vp, vp]),
     "spg_plan_set_timing": (i32, [vp, i32]),
     "spg_plan_bin_times": (i32, [vp, vp]),
     "spg_transpose_workspace_size": (i32, [vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -61,7 +65,8 @@ SIGNATURES = {
     "spg_permute_values": (i32, [vp, vp, vp, i64, i32, i32, vp]),
     "spg_csc_transpose_noalloc": (i32, [vp, vp, vp, vp, vp, vp]),
     "spgemm_batched_workspace_size": (i32, [i32, vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
-    "spgemm_batched_symbolic": (i32, [i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(vp), vp]),
+    "spgemm_batched_symbolic": (i32, [vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(vp),
+                                      vp]),
     "spgemm_batched_numeric": (i32, [vp, vp, vp, vp, vp, vp, i32, vp]),
     "spgemm_batched_backward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "spg_bplan_check": (i32, [vp, vp]),

@@ -7,7 +7,7 @@
 #include <mutex>
 #include <new>
 
-#include "kernels.cuh"
+#include "handle.cuh"
 
 using namespace spg;
 
@@ -128,9 +128,6 @@ spg_status check_csc(const spg_csc *M, bool need_values) {
 
 spg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SPG_OK : SPG_ERR_CUDA; }
 
-// Side streams a numeric call spreads the lane-group bins over.
-constexpr int kNumSideStreams = 2;
-
 }  // namespace
 
 struct spg_plan {
@@ -158,30 +155,24 @@ struct spg_plan {
     bool timed = false;
     cudaEvent_t ev0[NBINS] = {}, ev1[NBINS] = {};
     int64_t sym_launches = 0;
-    // numeric: the lane-group bins run on side streams, forked from and
-    // joined back to the caller's stream (created on first use)
-    cudaStream_t side[kNumSideStreams] = {};
-    cudaEvent_t fork = nullptr, join[kNumSideStreams] = {};
+    // the lane-group bins run on side streams, forked from and joined back
+    // to the caller's stream: the handle's, or (no handle) the plan's own,
+    // created on first use
+    spg_handle *h = nullptr;
+    SideStreams own;
 
     ~spg_plan() {
         for (int b = 0; b < NBINS; ++b) {
             if (ev0[b]) cudaEventDestroy(ev0[b]);
             if (ev1[b]) cudaEventDestroy(ev1[b]);
         }
-        for (int i = 0; i < kNumSideStreams; ++i) {
-            if (side[i]) cudaStreamDestroy(side[i]);
-            if (join[i]) cudaEventDestroy(join[i]);
-        }
-        if (fork) cudaEventDestroy(fork);
+        own.release();
     }
-    bool side_streams() {
-        if (fork) return true;
-        // (what a failed attempt created is kept and not created again)
-        for (int i = 0; i < kNumSideStreams; ++i)
-            if ((!side[i] && cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking) != cudaSuccess) ||
-                (!join[i] && cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess))
-                return false;
-        return cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    SideStreams &ss() { return h ? h->streams : own; }
+    bool side_streams() { return ss().ready() || ss().create(); }
+    cudaError_t read(void *dst0, const void *src0, size_t n0, void *dst1, const void *src1, size_t n1,
+                     cudaStream_t s) {
+        return handle_readback(h, dst0, src0, n0, dst1, src1, n1, s);
     }
     int64_t nonempty_bins() const {
         int64_t n = 0;
@@ -218,7 +209,24 @@ struct spg_plan {
         t.cache_cols = b == BIN_DENSE && fwd && t.W > 0
                            ? std::min<int64_t>(nB, (int64_t)(L.cache_bytes / ((size_t)t.W * 4)))
                            : 0;
+        t.wait_cycles = cfg.test_wait_timeout ? 0 : kBulkWaitCycles;
         return t;
+    }
+
+    // The bins write disjoint columns of C.  Next to a dense bin, the bins
+    // that use no workspace scratch (the lane-group bins, and CTA hash bins
+    // whose table and flags fit shared memory) run on side streams: the
+    // dense kernel is launched first and keeps every SM, the others fill SMs
+    // as its CTAs finish and overlap one another.
+    bool side_rule(int b) const {
+        if (b >= BIN_WARP0 && b < BIN_CTA0) return true;
+        return b >= BIN_CTA0 && b < BIN_GLOBAL && num_geo[b].cap == 0 && !num_geo[b].bm_global;
+    }
+    bool numeric_fork() const {
+        if (!cfg.side_streams || !host.hist[BIN_DENSE]) return false;
+        for (int b = 1; b < BIN_DENSE; ++b)
+            if (host.hist[b] && side_rule(b)) return true;
+        return false;
     }
 };
 
@@ -233,6 +241,8 @@ spg_status spg_config_default(spg_config *cfg) {
     cfg->table_shrink = 0;
     cfg->scratch_cap_bytes = (int64_t)1 << 30;
     cfg->dense_cache_bytes = (int64_t)2 << 30;
+    cfg->side_streams = 1;
+    cfg->test_wait_timeout = 0;
     return SPG_OK;
 }
 
@@ -280,8 +290,29 @@ spg_status spgemm_workspace_size(const spg_csc *A, const spg_csc *B, const spg_c
     return SPG_OK;
 }
 
-spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config *cfg, void *workspace,
-                           size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC, spg_plan **plan_out,
+spg_status spg_create(spg_handle **handle) {
+    if (!handle) return SPG_ERR_INVALID;
+    *handle = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPG_ERR_CUDA;
+    spg_handle *h = new (std::nothrow) spg_handle();
+    if (!h) return SPG_ERR_INVALID;
+    h->device = dev;
+    if (!h->streams.create() || h->mirror.reserve(0) != cudaSuccess) {
+        delete h;
+        return SPG_ERR_CUDA;
+    }
+    *handle = h;
+    return SPG_OK;
+}
+
+spg_status spg_destroy(spg_handle *handle) {
+    delete handle;
+    return SPG_OK;
+}
+
+spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *B, const spg_config *cfg,
+                           void *workspace, size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC, spg_plan **plan_out,
                            spg_stream stream) {
     if (plan_out) *plan_out = nullptr;
     if (!C_colptr || !nnzC || !plan_out) return SPG_ERR_INVALID;
@@ -292,10 +323,12 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return SPG_ERR_WORKSPACE;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SPG_ERR_CUDA;
+    if (handle && handle->device != dev) return SPG_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     spg_plan *P = new (std::nothrow) spg_plan();
     if (!P) return SPG_ERR_INVALID;
+    P->h = handle;
     P->device = dev;
     P->dev = device_info(dev);
     P->mA = A->nrows; P->nA = A->ncols; P->nB = B->ncols;
@@ -342,7 +375,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     }
     // one read: the validation outcome (a malformed colptr would make the
     // walks read out of bounds: stop here) and the count of rows with entries
-    CK(readback(&P->host, ctrl, sizeof(Ctrl), try_compact ? &mC : nullptr,
+    CK(P->read(&P->host, ctrl, sizeof(Ctrl), try_compact ? &mC : nullptr,
                 try_compact ? P->rmark() + (P->mA - 1) : nullptr, try_compact ? sizeof(int64_t) : 0, s));
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     P->compact = try_compact && mC > 0 && mC * 10 <= P->mA * 9;
@@ -355,7 +388,7 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     } else {
         CK(cudaMemsetAsync(C_colptr, 0, sizeof(int64_t), s));
     }
-    CK(readback(&P->host, ctrl, sizeof(Ctrl), nullptr, nullptr, 0, s));
+    CK(P->read(&P->host, ctrl, sizeof(Ctrl), nullptr, nullptr, 0, s));
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     // the walks index a column's products with 32-bit offsets
     for (int b = 0; b < NBINS; ++b)
@@ -377,11 +410,10 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
     // memory only) run on the side streams, launched after the dense kernel
     bool groups = false;
     for (int b = BIN_WARP0; b < BIN_CTA0; ++b) groups |= P->host.hist[b] != 0;
-    const bool fork = groups && P->host.hist[BIN_DENSE] != 0;
+    const bool fork = groups && P->host.hist[BIN_DENSE] != 0 && c.side_streams;
     if (fork) {
         if (!P->side_streams()) { delete P; return SPG_ERR_CUDA; }
-        CK(cudaEventRecord(P->fork, s));
-        for (int i = 0; i < kNumSideStreams; ++i) CK(cudaStreamWaitEvent(P->side[i], P->fork, 0));
+        CK(cudaEventRecord(P->ss().fork, s));
     }
     auto sym_bin = [&](int b, cudaStream_t sb) {
         // the symbolic CTA kernels carry no values: CTAs of up to 256 threads,
@@ -391,18 +423,29 @@ spg_status spgemm_symbolic(const spg_csc *A, const spg_csc *B, const spg_config 
                                   P->L.scratch_ctas);
         return launch_symbolic_bin(P->task(b), o, C_colptr, g, sb);
     };
-    for (int b = 1; b < NBINS; ++b)
-        if (P->host.hist[b] && !(fork && b >= BIN_WARP0 && b < BIN_CTA0)) CK(sym_bin(b, s));
-    if (fork) {
-        for (int b = BIN_CTA0 - 1, i = 0; b >= BIN_WARP0; --b)
-            if (P->host.hist[b]) CK(sym_bin(b, P->side[i++ % kNumSideStreams]));
-        for (int i = 0; i < kNumSideStreams; ++i) {
-            CK(cudaEventRecord(P->join[i], P->side[i]));
-            CK(cudaStreamWaitEvent(s, P->join[i], 0));
+    {
+        // once forked, the side streams are joined back to `stream` even when
+        // a call fails, so a capture of `stream` is never left unjoined
+        cudaError_t first = cudaSuccess;
+        auto keep = [&](cudaError_t e) {
+            if (first == cudaSuccess) first = e;
+        };
+        if (fork)
+            for (int i = 0; i < kNumSideStreams; ++i) keep(cudaStreamWaitEvent(P->ss().side[i], P->ss().fork, 0));
+        for (int b = 1; b < NBINS && first == cudaSuccess; ++b)
+            if (P->host.hist[b] && !(fork && b >= BIN_WARP0 && b < BIN_CTA0)) keep(sym_bin(b, s));
+        if (fork) {
+            for (int b = BIN_CTA0 - 1, i = 0; b >= BIN_WARP0 && first == cudaSuccess; --b)
+                if (P->host.hist[b]) keep(sym_bin(b, P->ss().side[i++ % kNumSideStreams]));
+            for (int i = 0; i < kNumSideStreams; ++i) {
+                keep(cudaEventRecord(P->ss().join[i], P->ss().side[i]));
+                keep(cudaStreamWaitEvent(s, P->ss().join[i], 0));
+            }
         }
+        CK(first);
     }
     CK(launch_inclusive_scan(C_colptr + 1, P->nB, P->tiles(), s));
-    CK(readback(&P->nnzC, C_colptr + P->nB, sizeof(int64_t), &P->host, ctrl, sizeof(Ctrl), s));
+    CK(P->read(&P->nnzC, C_colptr + P->nB, sizeof(int64_t), &P->host, ctrl, sizeof(Ctrl), s));
 #undef CK
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     for (int b = 1; b < NBINS; ++b) {
@@ -447,18 +490,8 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
     }
     Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, A->values, B->colptr, B->rowidx, B->values,
                P->compact ? P->rinv() : nullptr};
-    // The bins write disjoint columns of C.  Next to a dense bin, the bins
-    // that use no workspace scratch (the lane-group bins, and CTA hash bins
-    // whose table and flags fit shared memory) run on side streams: the
-    // dense kernel is launched first and keeps every SM, the others fill
-    // SMs as its CTAs finish and overlap one another.
-    auto on_side = [&](int b) {
-        if (b >= BIN_WARP0 && b < BIN_CTA0) return true;
-        return b >= BIN_CTA0 && b < BIN_GLOBAL && P->num_geo[b].cap == 0 && !P->num_geo[b].bm_global;
-    };
-    bool sides = false;
-    for (int b = 1; b < BIN_DENSE; ++b) sides |= P->host.hist[b] != 0 && on_side(b);
-    const bool fork = sides && P->host.hist[BIN_DENSE] != 0;
+    auto on_side = [&](int b) { return P->side_rule(b); };
+    const bool fork = P->numeric_fork();
     if (fork && !P->side_streams()) return SPG_ERR_CUDA;
     auto launch = [&](int b, cudaStream_t sb) -> spg_status {
         if (P->timing && cudaEventRecord(P->ev0[b], sb) != cudaSuccess) return SPG_ERR_CUDA;
@@ -468,19 +501,26 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
         return SPG_OK;
     };
     if (fork) {
-        if (cudaEventRecord(P->fork, s) != cudaSuccess) return SPG_ERR_CUDA;
+        if (cudaEventRecord(P->ss().fork, s) != cudaSuccess) return SPG_ERR_CUDA;
+        // from here on the side streams are joined back to `stream` whatever
+        // fails, so a capture of `stream` is never left unjoined; the first
+        // error is returned
+        spg_status first = SPG_OK;
+        auto keep = [&](spg_status x) {
+            if (first == SPG_OK) first = x;
+        };
         for (int i = 0; i < kNumSideStreams; ++i)
-            if (cudaStreamWaitEvent(P->side[i], P->fork, 0) != cudaSuccess) return SPG_ERR_CUDA;
-        for (int b = 1; b < NBINS; ++b)
-            if (P->host.hist[b] && !on_side(b) && (st = launch(b, s)) != SPG_OK) return st;
+            if (cudaStreamWaitEvent(P->ss().side[i], P->ss().fork, 0) != cudaSuccess) keep(SPG_ERR_CUDA);
+        for (int b = 1; b < NBINS && first == SPG_OK; ++b)
+            if (P->host.hist[b] && !on_side(b)) keep(launch(b, s));
         // heaviest side bin first, bins dealt round-robin to the side streams
-        for (int b = BIN_DENSE - 1, i = 0; b >= 1; --b)
-            if (P->host.hist[b] && on_side(b) && (st = launch(b, P->side[i++ % kNumSideStreams])) != SPG_OK)
-                return st;
+        for (int b = BIN_DENSE - 1, i = 0; b >= 1 && first == SPG_OK; --b)
+            if (P->host.hist[b] && on_side(b)) keep(launch(b, P->ss().side[i++ % kNumSideStreams]));
         for (int i = 0; i < kNumSideStreams; ++i)
-            if (cudaEventRecord(P->join[i], P->side[i]) != cudaSuccess ||
-                cudaStreamWaitEvent(s, P->join[i], 0) != cudaSuccess)
-                return SPG_ERR_CUDA;
+            if (cudaEventRecord(P->ss().join[i], P->ss().side[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(s, P->ss().join[i], 0) != cudaSuccess)
+                keep(SPG_ERR_CUDA);
+        if (first != SPG_OK) return first;
     } else {
         for (int b = 1; b < NBINS; ++b)
             if (P->host.hist[b] && (st = launch(b, s)) != SPG_OK) return st;
@@ -527,7 +567,7 @@ spg_status spg_plan_check(spg_plan *P, spg_stream stream) {
     if (!P) return SPG_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int32_t err = 0;
-    if (readback(&err, &P->ctrl()->err, sizeof(err), nullptr, nullptr, 0, s) != cudaSuccess) return SPG_ERR_CUDA;
+    if (P->read(&err, &P->ctrl()->err, sizeof(err), nullptr, nullptr, 0, s) != cudaSuccess) return SPG_ERR_CUDA;
     return (spg_status)err;
 }
 
@@ -565,6 +605,13 @@ spg_status spg_plan_launch_count(const spg_plan *P, int64_t *symbolic, int64_t *
     if (symbolic) *symbolic = P->sym_launches;
     if (numeric) *numeric = P->nonempty_bins() + (P->compact ? 1 : 0);
     if (backward) *backward = P->nonempty_bins();
+    return SPG_OK;
+}
+
+spg_status spg_plan_bin_streams(const spg_plan *P, int32_t *side) {
+    if (!P || !side) return SPG_ERR_INVALID;
+    const bool fork = P->numeric_fork();
+    for (int b = 0; b < NBINS; ++b) side[b] = fork && P->host.hist[b] && P->side_rule(b) ? 1 : 0;
     return SPG_OK;
 }
 

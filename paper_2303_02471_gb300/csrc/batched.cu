@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "columns.cuh"
+#include "handle.cuh"
 
 namespace spg {
 
@@ -632,6 +633,7 @@ int64_t prob_t(const spg_config &c, int64_t m) {
 }  // namespace
 
 struct spg_bplan {
+    spg_handle *h = nullptr;  // read-backs through the handle's buffer (NULL: the thread's)
     int nb = 0;
     int device = 0;
     int sms = 1;
@@ -849,9 +851,9 @@ spg_status spgemm_batched_workspace_size(int32_t nb, const spg_csc *A, const spg
     return SPG_OK;
 }
 
-spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *B, const spg_config *cfg,
-                                   void *workspace, size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC,
-                                   spg_bplan **plan_out, spg_stream stream) {
+spg_status spgemm_batched_symbolic(spg_handle *handle, int32_t nb, const spg_csc *A, const spg_csc *B,
+                                   const spg_config *cfg, void *workspace, size_t ws_bytes, int64_t *C_colptr,
+                                   int64_t *nnzC, spg_bplan **plan_out, spg_stream stream) {
     if (plan_out) *plan_out = nullptr;
     if (!plan_out || (nb > 0 && (!C_colptr || !nnzC))) return SPG_ERR_INVALID;
     spg_status st = check_batch(nb, A, B);
@@ -865,8 +867,12 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
         return SPG_ERR_INVALID;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return SPG_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return SPG_ERR_CUDA;
+    if (handle && handle->device != cur) return SPG_ERR_INVALID;
     spg_bplan *P = new (std::nothrow) spg_bplan();
     if (!P) return SPG_ERR_INVALID;
+    P->h = handle;
     P->nb = nb;
     P->cfg = c;
     // the persistent kernel is built for at most 512 threads (register budget)
@@ -938,14 +944,14 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
         if (ntot > 0)
             k_bvalidate<<<vg, 256, 0, s>>>(reinterpret_cast<const VMat *>(ws + P->L.vB), nb,
                                            reinterpret_cast<const int64_t *>(ws + P->L.col0s), ntot, 1, P->ctrl());
-        CK(readback(&P->host, P->ctrl(), sizeof(Ctrl), nullptr, nullptr, 0, s));
+        CK(handle_readback(P->h, &P->host, P->ctrl(), sizeof(Ctrl), nullptr, nullptr, 0, s));
         if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     }
     BTask b = P->task();
     int64_t *op = reinterpret_cast<int64_t *>(ws + P->L.op);
     if (ntot > 0) k_bcount<<<vg, 256, 0, s>>>(b, ntot, op);
     CK(cudaGetLastError());
-    CK(readback(&P->host, P->ctrl(), sizeof(Ctrl), nullptr, nullptr, 0, s));
+    CK(handle_readback(P->h, &P->host, P->ctrl(), sizeof(Ctrl), nullptr, nullptr, 0, s));
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     for (int k = 0; k < NBINS; ++k)
         if (P->host.maxop[k] >= (1ULL << 31)) { delete P; return SPG_ERR_UNSUPPORTED; }
@@ -974,7 +980,7 @@ spg_status spgemm_batched_symbolic(int32_t nb, const spg_csc *A, const spg_csc *
         b, ccp, ncp, reinterpret_cast<const int64_t *>(ws + P->L.base), reinterpret_cast<const int64_t *>(ws + P->L.segs),
         reinterpret_cast<int64_t *>(ws + P->L.nnz));
     CK(cudaGetLastError());
-    CK(readback(P->nnz.data(), ws + P->L.nnz, (size_t)nb * 8, &P->host, P->ctrl(), sizeof(Ctrl), s));
+    CK(handle_readback(P->h, P->nnz.data(), ws + P->L.nnz, (size_t)nb * 8, &P->host, P->ctrl(), sizeof(Ctrl), s));
 #undef CK
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     for (int i = 0; i < nb; ++i) nnzC[i] = P->nnz[i];
@@ -1079,7 +1085,7 @@ spg_status spg_bplan_check(spg_bplan *P, spg_stream stream) {
     if (P->nb == 0) return SPG_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int32_t err = 0;
-    if (readback(&err, &P->ctrl()->err, sizeof(err), nullptr, nullptr, 0, s) != cudaSuccess) return SPG_ERR_CUDA;
+    if (handle_readback(P->h, &err, &P->ctrl()->err, sizeof(err), nullptr, nullptr, 0, s) != cudaSuccess) return SPG_ERR_CUDA;
     return (spg_status)err;
 }
 

@@ -700,8 +700,10 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                  : "memory");
 }
 
-// Waits for the phase of the given parity to complete; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// Waits for the phase of the given parity to complete; false once `limit`
+// cycles have passed (at once, without polling, when limit <= 0).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit = kBulkWaitCycles) {
+    if (limit <= 0) return false;
     const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
     const long long t0 = clock64();
     for (;;) {
@@ -714,7 +716,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
             : "r"(b), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > kBulkWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -730,12 +732,23 @@ __global__ void k_row_map(const int64_t *incl, int64_t m, int32_t *map, int32_t 
 __global__ void k_row_remap(const int32_t *Arow, int64_t nnz, const int32_t *map, int64_t m, int32_t *out,
                             Ctrl *ctrl);
 
+// Mapped pinned host buffer of small device -> host reads, grown on demand
+// (at least 64 KiB).
+struct Mirror {
+    void *host = nullptr;
+    void *dev = nullptr;
+    size_t cap = 0;
+    ~Mirror();
+    cudaError_t reserve(size_t need);
+};
+
 // Small device -> host reads (control blocks, counts): a one-CTA kernel
-// copies src0[0..n0) and src1[0..n1) into a mapped pinned mirror of the
-// calling host thread, the stream is synchronised and the bytes are copied to
-// dst0 / dst1.  No copy engine is used, so these reads are not queued behind
-// large copies that the caller has in flight on other streams.
-cudaError_t readback(void *dst0, const void *src0, size_t n0, void *dst1, const void *src1, size_t n1,
+// copies src0[0..n0) and src1[0..n1) into the mapped pinned mirror `m` (NULL:
+// one of the calling host thread for the current device), the stream is
+// synchronised and the bytes are copied to dst0 / dst1.  No copy engine is
+// used, so these reads are not queued behind large copies that the caller
+// has in flight on other streams.
+cudaError_t readback(Mirror *m, void *dst0, const void *src0, size_t n0, void *dst1, const void *src1, size_t n1,
                      cudaStream_t s);
 cudaError_t launch_inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t s);
 int64_t scan_tile_count(int64_t n);
@@ -772,6 +785,7 @@ struct BinTask {
     Ctrl *ctrl;
     uint32_t *flag_cache;    // dense bin: W words per listed column, for the
     int64_t cache_cols;      //   first cache_cols columns of the bin's list
+    long long wait_cycles;   // dense bin: limit of a wait for kept flags (<= 0: give up at once)
 };
 
 struct Operands {

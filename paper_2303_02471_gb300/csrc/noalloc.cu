@@ -20,24 +20,62 @@ constexpr size_t kNoallocScratchBytes = SPG_NOALLOC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Device address of the array, resolved once per device with that device
-// current (in host code the array's name is only a host-side stand-in).
+// Id of the calling thread's current CUDA context (driver entry points taken
+// through the runtime, so the library needs no link to the driver library);
+// false when there is none or the driver does not offer them.
+bool current_context_id(unsigned long long &id) {
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    void *ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, &id) == 0;
+}
+
+// Device address of the array, resolved with the device current (in host
+// code the array's name is only a host-side stand-in).  It is looked up once
+// per device and context: a reset of the device, or another primary context,
+// loads the module again, possibly at another address, so the cached address
+// is kept only while the context it was taken in is still the current one.
 void *scratch_address(int device, cudaError_t &err) {
+    struct Entry {
+        void *addr = nullptr;
+        unsigned long long ctx = 0;
+        bool known = false;  // ctx holds the id of the context addr was taken in
+    };
     static std::mutex mu;
-    static void *addr[64] = {};
-    std::lock_guard<std::mutex> lock(mu);
+    static Entry cache[64];
     err = cudaSuccess;
     if (device < 0 || device >= 64) {
         err = cudaErrorInvalidDevice;
         return nullptr;
     }
-    if (!addr[device]) {
-        void *p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (err != cudaSuccess) return nullptr;
-        addr[device] = p;
-    }
-    return addr[device];
+    unsigned long long id = 0;
+    const bool have = current_context_id(id);
+    std::lock_guard<std::mutex> lock(mu);
+    Entry &e = cache[device];
+    if (e.addr && have && e.known && e.ctx == id) return e.addr;
+    void *p = nullptr;
+    err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (err != cudaSuccess) return nullptr;
+    // the lookup made the device's primary context current if none was
+    e.addr = p;
+    e.known = current_context_id(id);
+    e.ctx = e.known ? id : 0;
+    return p;
 }
 
 }  // namespace

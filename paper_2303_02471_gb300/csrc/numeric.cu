@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, co
         const int64_t nn = Ccp[j + 1] - c0;
         const uint32_t *keep = ci < t.cache_cols ? t.flag_cache + (size_t)ci * t.W : nullptr;
         if (prefetch && keep) {
-            const bool arrived = mbar_wait(&s_bar, phase);
+            const bool arrived = mbar_wait(&s_bar, phase, t.wait_cycles);
             if (__syncthreads_or(!arrived)) {
                 if (threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_TIMEOUT, t.bin, j);
                 timed_out = true;
@@ -167,9 +167,10 @@ __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, co
                                              Cval, next);
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
     }
-    // a copy is in flight only after a time-out: wait for it (bounded)
-    // before the CTA's shared memory goes away
-    if (timed_out) mbar_wait(&s_bar, phase);
+    // a copy is in flight only after a time-out: wait for it (bounded, at
+    // full length whatever the first wait's limit) before the CTA's shared
+    // memory goes away
+    if (timed_out) mbar_wait(&s_bar, phase, kBulkWaitCycles);
 }
 
 // ------------------------------------------------------------- launches

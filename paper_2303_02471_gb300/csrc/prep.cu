@@ -240,41 +240,43 @@ __global__ void k_readback(const unsigned char *s0, size_t n0, const unsigned ch
     for (size_t i = threadIdx.x; i < n1; i += blockDim.x) dst[off1 + i] = s1[i];
 }
 
-// Mapped pinned staging of one host thread on one device.
-struct Mirror {
-    void *host = nullptr;
-    void *dev = nullptr;
-    size_t cap = 0;
-    ~Mirror() {
-        if (host) cudaFreeHost(host);
-    }
-};
 constexpr int kMaxDevices = 64;
 thread_local Mirror t_mirror[kMaxDevices];
 
 }  // namespace
 
-cudaError_t readback(void *dst0, const void *src0, size_t n0, void *dst1, const void *src1, size_t n1,
-                     cudaStream_t s) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    Mirror &m = t_mirror[dev];
-    const size_t off1 = (n0 + 15) & ~size_t(15);
-    const size_t need = off1 + n1;
-    if (m.cap < need) {
-        if (m.host) cudaFreeHost(m.host);
-        m.host = m.dev = nullptr;
-        m.cap = 0;
-        const size_t cap = need > (size_t(64) << 10) ? need : (size_t(64) << 10);
-        if ((e = cudaHostAlloc(&m.host, cap, cudaHostAllocMapped)) != cudaSuccess) {
-            m.host = nullptr;
-            return e;
-        }
-        if ((e = cudaHostGetDevicePointer(&m.dev, m.host, 0)) != cudaSuccess) return e;
-        m.cap = cap;
+Mirror::~Mirror() {
+    if (host) cudaFreeHost(host);
+}
+
+cudaError_t Mirror::reserve(size_t need) {
+    if (cap >= need) return cudaSuccess;
+    if (host) cudaFreeHost(host);
+    host = dev = nullptr;
+    cap = 0;
+    const size_t want = need > (size_t(64) << 10) ? need : (size_t(64) << 10);
+    cudaError_t e = cudaHostAlloc(&host, want, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        host = nullptr;
+        return e;
     }
+    if ((e = cudaHostGetDevicePointer(&dev, host, 0)) != cudaSuccess) return e;
+    cap = want;
+    return cudaSuccess;
+}
+
+cudaError_t readback(Mirror *mp, void *dst0, const void *src0, size_t n0, void *dst1, const void *src1, size_t n1,
+                     cudaStream_t s) {
+    cudaError_t e;
+    if (!mp) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+        mp = &t_mirror[dev];
+    }
+    Mirror &m = *mp;
+    const size_t off1 = (n0 + 15) & ~size_t(15);
+    if ((e = m.reserve(off1 + n1)) != cudaSuccess) return e;
     k_readback<<<1, 256, 0, s>>>(static_cast<const unsigned char *>(src0), n0,
                                  static_cast<const unsigned char *>(src1), n1,
                                  static_cast<unsigned char *>(m.dev), off1);

@@ -82,6 +82,8 @@ class Config:
     table_shrink: Optional[int] = None
     scratch_cap_bytes: Optional[int] = None
     dense_cache_bytes: Optional[int] = None
+    side_streams: Optional[bool] = None
+    test_wait_timeout: Optional[bool] = None
 
     def native(self) -> N.SpgConfig:
         c = N.SpgConfig()
@@ -91,8 +93,10 @@ class Config:
             v = getattr(self, f)
             if v is not None:
                 setattr(c, f, int(v))
-        if self.validate is not None:
-            c.validate = int(bool(self.validate))
+        for f in ("validate", "side_streams", "test_wait_timeout"):
+            v = getattr(self, f)
+            if v is not None:
+                setattr(c, f, int(bool(v)))
         return c
 
 
@@ -121,12 +125,60 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+class Handle:
+    """An spg_handle of one device: the side streams, events and pinned
+    read-back buffer that the calls made with it use (created at once)."""
+
+    def __init__(self, device: int):
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            N.check(N.lib().spg_create(ctypes.byref(h)), "spg_create")
+        self._h = h
+        self.device = device
+
+    @property
+    def ptr(self):
+        if self._h is None:
+            raise RuntimeError("handle destroyed")
+        return self._h
+
+    def destroy(self) -> None:
+        if self._h is not None:
+            N.lib().spg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+_HANDLES = {}
+
+
+def handle(device=None) -> Handle:
+    """The shared handle of a CUDA device (default: the current one), created
+    on first use.  Calls made with one handle run their side-stream bins in
+    order; give concurrent products on different streams a Handle each."""
+    if device is None:
+        idx = torch.cuda.current_device()
+    else:
+        d = torch.device(device)
+        idx = d.index if d.index is not None else torch.cuda.current_device()
+    h = _HANDLES.get(idx)
+    if h is None:
+        h = _HANDLES[idx] = Handle(idx)
+    return h
+
+
 class Plan:
     """Host plan of one product plus the device workspace that holds its state."""
 
     def __init__(self, handle: ctypes.c_void_p, workspace: torch.Tensor, A: CscMatrix,
-                 B: CscMatrix, colptr: torch.Tensor, nnz: int, config: Config):
+                 B: CscMatrix, colptr: torch.Tensor, nnz: int, config: Config, lib_handle=None):
         self._h = handle
+        self._lib_handle = lib_handle  # kept alive while the plan is
         self.workspace = workspace
         self.shape = (A.nrows, B.ncols)
         self.dtype = A.dtype
@@ -161,6 +213,12 @@ class Plan:
         N.check(N.lib().spg_plan_launch_count(self.handle, ctypes.byref(s), ctypes.byref(n),
                                               ctypes.byref(b)), "spg_plan_launch_count")
         return {"symbolic": s.value, "numeric": n.value, "backward": b.value}
+
+    def bin_streams(self):
+        """Per bin: True when its numeric kernel runs on a side stream."""
+        side = (ctypes.c_int32 * 64)()
+        N.check(N.lib().spg_plan_bin_streams(self.handle, side), "spg_plan_bin_streams")
+        return [bool(x) for x in side[:len(self.info()["bins"])]]
 
     def set_timing(self, enable: bool = True) -> None:
         N.check(N.lib().spg_plan_set_timing(self.handle, int(bool(enable))), "spg_plan_set_timing")
@@ -200,9 +258,11 @@ def workspace_size(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None) 
 
 
 def spgemm_symbolic(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None,
-                    workspace: Optional[torch.Tensor] = None):
-    """Column pointers of C = A B, nnz(C) and the plan (synchronises)."""
+                    workspace: Optional[torch.Tensor] = None, lib_handle: Optional[Handle] = None):
+    """Column pointers of C = A B, nnz(C) and the plan (synchronises).
+    lib_handle: the Handle to use (default: the device's shared one)."""
     config = config or Config()
+    hd = lib_handle if lib_handle is not None else handle(A.device)
     cfg = config.native()
     cA, cB = _csc(A), _csc(B, A.dtype)
     need = workspace_size(A, B, config)
@@ -211,11 +271,11 @@ def spgemm_symbolic(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None,
     colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=A.device)
     nnz = ctypes.c_int64()
     h = ctypes.c_void_p()
-    N.check(N.lib().spgemm_symbolic(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(cfg),
+    N.check(N.lib().spgemm_symbolic(hd.ptr, ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(cfg),
                                     _ptr(workspace), workspace.numel(), _ptr(colptr),
                                     ctypes.byref(nnz), ctypes.byref(h), _stream()),
             "spgemm_symbolic")
-    return colptr, nnz.value, Plan(h, workspace, A, B, colptr, nnz.value, config)
+    return colptr, nnz.value, Plan(h, workspace, A, B, colptr, nnz.value, config, hd)
 
 
 def spgemm_numeric(plan: Plan, A: CscMatrix, B: CscMatrix, rowidx: Optional[torch.Tensor] = None,
@@ -270,8 +330,9 @@ def csc_transpose(M: CscMatrix, with_perm: bool = True):
 class BatchedPlan:
     """Host plan of a batch plus the device workspace and concatenated colptr."""
 
-    def __init__(self, handle, workspace, colptr, nnz, segs, shapes, config):
+    def __init__(self, handle, workspace, colptr, nnz, segs, shapes, config, lib_handle=None):
         self._h = handle
+        self._lib_handle = lib_handle  # kept alive while the plan is
         self.workspace = workspace
         self.colptr = colptr        # concatenated int64 column pointers
         self.nnz = nnz              # list of nnz(C_i)
@@ -338,10 +399,12 @@ def spgemm_batched_symbolic(As, Bs, config: Optional[Config] = None) -> BatchedP
     colptr = torch.empty(max(off, 1), dtype=torch.int64, device=dev)
     nnz = (ctypes.c_int64 * max(1, nb))()
     h = ctypes.c_void_p()
-    N.check(N.lib().spgemm_batched_symbolic(nb, cA, cB, ctypes.byref(cfg), _ptr(ws), ws.numel(), _ptr(colptr),
-                                            nnz, ctypes.byref(h), _stream()), "spgemm_batched_symbolic")
+    hd = handle(dev)
+    N.check(N.lib().spgemm_batched_symbolic(hd.ptr, nb, cA, cB, ctypes.byref(cfg), _ptr(ws), ws.numel(),
+                                            _ptr(colptr), nnz, ctypes.byref(h), _stream()),
+            "spgemm_batched_symbolic")
     shapes = [(A.nrows, B.ncols) for A, B in zip(As, Bs)]
-    return BatchedPlan(h, ws, colptr, list(nnz[:nb]), segs, shapes, config)
+    return BatchedPlan(h, ws, colptr, list(nnz[:nb]), segs, shapes, config, hd)
 
 
 def spgemm_batched_numeric(plan: BatchedPlan, As, Bs, use_graph: bool = False):

@@ -26,8 +26,9 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("spgemm_symbolic", "spgemm_numeric", "spgemm_backward", "spgemm_batched_symbolic",
-                     "spgemm_batched_numeric", "spgemm_batched_backward", "spgemm_workspace_size"):
+    for required in ("spg_create", "spg_destroy", "spgemm_symbolic", "spgemm_numeric", "spgemm_backward",
+                     "spgemm_batched_symbolic", "spgemm_batched_numeric", "spgemm_batched_backward",
+                     "spgemm_workspace_size", "spg_plan_destroy", "spg_status_string"):
         assert required in names
 
 
@@ -43,8 +44,9 @@ def test_struct_layouts():
     from paper_2303_02471_gb300 import _native as N
     assert ctypes.sizeof(N.SpgCsc) == 56
     assert N.SpgCsc.values.offset == 40 and N.SpgCsc.dtype.offset == 48
-    assert ctypes.sizeof(N.SpgConfig) == 40
+    assert ctypes.sizeof(N.SpgConfig) == 48
     assert N.SpgConfig.dense_cache_bytes.offset == 32
+    assert N.SpgConfig.side_streams.offset == 40 and N.SpgConfig.test_wait_timeout.offset == 44
 
 
 def test_status_strings_and_defaults(lib):
@@ -54,6 +56,7 @@ def test_status_strings_and_defaults(lib):
     c = N.SpgConfig()
     assert lib.spg_config_default(ctypes.byref(c)) == 0
     assert c.t == -1 and c.validate == 1 and c.hash_cta_max == 8192
+    assert c.side_streams == 1 and c.test_wait_timeout == 0
     assert lib.spg_config_default(None) == 1
 
 
@@ -66,6 +69,8 @@ def test_host_only_calls(lib):
     bad = N.SpgCsc(-1, 7, 30, None, None, None, 0)
     assert lib.spg_transpose_workspace_size(ctypes.byref(bad), ctypes.byref(nbytes)) == 1
     assert lib.spg_plan_destroy(None) == 0
+    assert lib.spg_destroy(None) == 0
+    assert lib.spg_create(None) == 1
     assert lib.spg_bplan_destroy(None) == 0
     assert lib.spg_plan_check(None, None) == 1
     assert lib.spg_permute_values(None, None, None, 0, 0, 0, None) == 0

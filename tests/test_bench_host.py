@@ -41,18 +41,39 @@ def test_column_sample_keeps_whole_columns():
     assert np.array_equal(cols, cols2)
 
 
+def _sources_hash(files):
+    import hashlib
+    import os
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(bench.ROOT, "paper_2303_02471_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def test_traffic_is_reported_only_for_the_captured_kernel_and_case(monkeypatch):
-    t = bench.MEASURED_TRAFFIC
-    got = bench.measured_traffic(t["bin"], _args())
-    assert got == int(t["bytes"])  # the committed sources are the captured ones
-    assert bench.measured_traffic(t["bin"] - 1, _args()) is None
-    assert bench.measured_traffic(t["bin"], _args(rmat_scale=17)) is None
-    assert bench.measured_traffic(t["bin"], _args(t=100)) is None
-    assert bench.measured_traffic(t["bin"], _args(cta_threads=256)) is None
-    assert bench.measured_traffic(t["bin"], _args(workload=2)) is None
-    changed = dict(t, sources_sha256_16="0" * 16)
-    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", changed)
-    assert bench.measured_traffic(t["bin"], _args()) is None
+    files = ("kernels.cuh", "numeric.cu")
+    rec = {"bin": 13, "scale": 17, "bytes": 4.0e9, "algorithmic_bytes": 5.0e9, "sources": files,
+           "sources_sha256_16": _sources_hash(files)}
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", rec)
+    got, src = bench.measured_traffic(13, 10.0e9, _args())
+    assert got == 8 * 10 ** 9 and "scaled" in src  # scaled by the algorithmic bytes
+    assert bench.measured_traffic(12, 10.0e9, _args())[0] is None
+    assert bench.measured_traffic(13, 10.0e9, _args(t=100))[0] is None
+    assert bench.measured_traffic(13, 10.0e9, _args(cta_threads=256))[0] is None
+    assert bench.measured_traffic(13, 10.0e9, _args(workload=2))[0] is None
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", dict(rec, sources_sha256_16="0" * 16))
+    assert bench.measured_traffic(13, 10.0e9, _args())[0] is None
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", None)
+    assert bench.measured_traffic(13, 10.0e9, _args())[0] is None
+
+
+def test_backward_bytes_count_each_array_once():
+    A = synth.random_z(50, 2, 2, seed=1)
+    B = synth.random_z(50, 3, 3, seed=2)
+    full = bench.backward_bytes(A, B, 300, 280, 8)
+    no_da = bench.backward_bytes(A, B, 300, 280, 8, need_dA=False)
+    assert full - no_da == 100 * 8  # dA: nnz(A) values written once
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])

@@ -81,8 +81,10 @@ def test_backward_only_one_side():
     dc = torch.ones(C.nnz, dtype=torch.float64, device="cuda")
     gA, gB = ops.spgemm_backward(plan, dA_, dB_, C, dc, need_dA=False)
     assert gA is None and gB is not None
-    rA, rB = oracle.backward(A, B, C.to_host(), np.ones(C.nnz))
-    assert np.allclose(gB.cpu().numpy(), rB, rtol=1e-12, atol=1e-12)
+    Ch = C.to_host()
+    rA, rB = oracle.backward(A, B, Ch, np.ones(C.nnz))
+    _, sB = oracle.backward(_abs(A), _abs(B), Ch, np.ones(C.nnz))
+    _within(gB.cpu().numpy(), rB, sB, 1e-12, "dB")
 
 
 # ---------------------------------------------------------------- transpose
@@ -113,7 +115,21 @@ def test_transpose_matches_oracle(case):
 
 
 # ----------------------------------------------------------------- autograd
+def _abs(M):
+    return M.with_values(np.abs(np.asarray(M.values, dtype=np.float64))) if hasattr(M, "with_values") else \
+        synth.CSC(M.nrows, M.ncols, M.colptr, M.rowidx, np.abs(np.asarray(M.values, dtype=np.float64)))
+
+
+def _within(got, want, scale, tau, what):
+    err = np.abs(np.asarray(got, dtype=np.float64) - want)
+    bad = err > tau * scale
+    assert not bad.any(), f"{what}: {int(bad.sum())} entries off, worst excess {np.max(err - tau * scale)}"
+
+
 def test_autograd_matches_oracle():
+    """Gradients through the autograd Function: per stored entry within
+    tau * (sum of |terms|) of the oracle, the sums taken by the oracle on
+    absolute values (dC = w exactly, so nothing propagates)."""
     import torch
     from paper_2303_02471_gb300 import autograd as ag
     A = synth.rmat(11, seed=5, col_cap=200)
@@ -124,9 +140,12 @@ def test_autograd_matches_oracle():
     C = ag.spgemm(dA_.with_values(a), dB_.with_values(b))
     w = torch.as_tensor(np.random.default_rng(7).standard_normal(C.nnz), device="cuda")
     (C.values * w).sum().backward()
-    rA, rB = oracle.backward(A, B, C.to_host(), w.cpu().numpy())
-    assert np.allclose(a.grad.cpu().numpy(), rA, rtol=1e-11, atol=1e-12)
-    assert np.allclose(b.grad.cpu().numpy(), rB, rtol=1e-11, atol=1e-12)
+    Ch = C.to_host()
+    wh = w.cpu().numpy()
+    rA, rB = oracle.backward(A, B, Ch, wh)
+    sA, sB = oracle.backward(_abs(A), _abs(B), Ch, np.abs(wh))
+    _within(a.grad.cpu().numpy(), rA, sA, 1e-12, "dA")
+    _within(b.grad.cpu().numpy(), rB, sB, 1e-12, "dB")
 
 
 def _galerkin_problem(g):
@@ -141,22 +160,79 @@ def _galerkin_problem(g):
     return A, P, T, Pv
 
 
+def _with(M, values):
+    return synth.CSC(M.nrows, M.ncols, np.asarray(M.colptr), np.asarray(M.rowidx), np.asarray(values, np.float64))
+
+
 @pytest.mark.parametrize("g", [8, 40])
 def test_galerkin_gradient_vs_oracle(g):
+    """C = P^T (A P), loss ||C - T||^2 and dL/dP against the oracle, entry by entry.
+
+    Every intermediate x of the GPU chain is held to |x - x_ref| <= tau * s_x
+    (tau = 1e-12) with s_x the oracle's sum of |terms| carried through the
+    chain (each step adds the error its inputs bring to its own rounding):
+      M = A P            s_M  = sum |A||P|                       (a plain product)
+      C = P^T M          s_C  = 2 sum |P^T| s_M                  (own rounding + M's error)
+      G = 2 (C - T)      s_G  = |G| + 2 s_C
+      dM = (P^T)^T G     s_dM = 2 sum |P^T| s_G                  (on pattern(M))
+      dP^T = G M^T       s_dPt = 3 sum s_G s_M                   (on pattern(P^T))
+      dP1 = A^T dM       s_dP1 = 2 sum |A| s_dM                  (on pattern(P))
+      dP = dP1 + dP^T scattered back:   s_dP = s_dP1 + s_dPt[perm] + |dP|
+    The second product is also compared on its own: the GPU's C against the
+    oracle applied to the GPU's M, under the plain rule tau * sum |P^T||M|."""
     import torch
     from paper_2303_02471_gb300 import autograd as ag
+    from paper_2303_02471_gb300 import ops
+    tau = 1e-12
     A, P, T, Pv = _galerkin_problem(g)
+    P1 = P.with_values(Pv)
     dA_ = upload(A)
-    dP = upload(P.with_values(Pv))
+    dP = upload(P1)
+    # the two products and the transpose one by one
+    M, _ = ops.spgemm(dA_, dP)
+    Mref, sM = oracle.spgemm(A, P1, nthreads=NCPU)
+    Mh = M.to_host()
+    assert np.array_equal(Mh.colptr, Mref.colptr) and np.array_equal(Mh.rowidx, Mref.rowidx)
+    _within(Mh.values, Mref.values, sM, tau, "M = A P")
+    Pt, perm = ops.csc_transpose(dP)
+    Ptref, pref = oracle.transpose(P1)
+    assert np.array_equal(Pt.colptr.cpu().numpy(), Ptref.colptr)
+    assert np.array_equal(Pt.rowidx.cpu().numpy(), Ptref.rowidx)
+    assert np.array_equal(Pt.values.cpu().numpy(), Ptref.values)
+    C2, _ = ops.spgemm(Pt, M)
+    C2h = C2.to_host()
+    Cg, absCg = oracle.spgemm(Ptref, Mh, nthreads=NCPU)
+    assert np.array_equal(C2h.colptr, Cg.colptr) and np.array_equal(C2h.rowidx, Cg.rowidx)
+    _within(C2h.values, Cg.values, absCg, tau, "C = P^T M (oracle on the GPU's M)")
+    # the differentiable chain
     p = dP.values.clone().requires_grad_(True)
     C = ag.galerkin(dA_, dP.with_values(p))
     Tt = torch.as_tensor(T, device="cuda")
     loss = ((C.values - Tt) ** 2).sum()
     loss.backward()
-    L, Cr, _, gP = oracle.galerkin(A, P.with_values(Pv), T_values=T)
-    assert np.array_equal(C.rowidx.cpu().numpy(), Cr.rowidx)
-    assert abs(loss.item() - L) <= 1e-10 * max(1.0, abs(L))
-    assert np.allclose(p.grad.cpu().numpy(), gP, rtol=1e-9, atol=1e-9 * np.abs(gP).max())
+    L, Cr, _, gP = oracle.galerkin(A, P1, T_values=T)
+    Ch = C.to_host()
+    assert np.array_equal(Ch.colptr, Cr.colptr) and np.array_equal(Ch.rowidx, Cr.rowidx)
+    # error scales of the chain (oracle sums on absolute values)
+    absPt = _with(Ptref, np.abs(Ptref.values))
+    sC = 2 * oracle.spgemm(absPt, _with(Mref, sM), nthreads=NCPU)[0].values
+    _within(Ch.values, Cr.values, sC, tau, "C = P^T (A P)")
+    Gref = 2 * (Cr.values - T)
+    sG = np.abs(Gref) + 2 * sC
+    _, s_dM = oracle.backward(absPt, _with(Mref, sM), Cr, sG, want_dA=False)
+    s_dM = 2 * s_dM
+    s_dPt, _ = oracle.backward(absPt, _with(Mref, sM), Cr, sG, want_dB=False)
+    s_dPt = 3 * s_dPt
+    _, s_dP1 = oracle.backward(_abs(A), _with(P1, np.abs(Pv)), Mref, s_dM, want_dA=False)
+    s_dP = 2 * s_dP1 + np.abs(gP)
+    np.add.at(s_dP, pref, s_dPt)
+    # the loss sums |C - T|^2 over pattern(C): its error is at most
+    # sum 2 |C - T| tau s_C (first order) plus the rounding of n squares
+    # and their sum, n u sum |C - T|^2
+    R = np.abs(Cr.values - T)
+    n = Cr.values.shape[0]
+    assert abs(loss.item() - L) <= tau * np.sum(2 * R * sC) + 2 * n * np.finfo(np.float64).eps * np.sum(R * R)
+    _within(p.grad.cpu().numpy(), gP, s_dP, tau, "dL/dP")
 
 
 def test_galerkin_finite_differences_workload5():

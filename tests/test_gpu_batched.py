@@ -1,5 +1,7 @@
 """Batched products (one persistent launch, CUDA-graph replay, autotuner)
 against the per-matrix calls and the CPU oracle."""
+import os
+
 import numpy as np
 import pytest
 
@@ -11,6 +13,7 @@ from gpu_helpers import TAU, assert_matches_oracle, upload
 pytestmark = pytest.mark.gpu
 
 INF = (1 << 63) - 1
+NCPU = len(os.sched_getaffinity(0))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -175,10 +178,12 @@ def test_batched_rejects_bad_input():
     assert e.value.name == "SPG_ERR_INVALID"
 
 
-def test_workload4_full_batch_sampled():
+def test_workload4_full_batch_every_product():
     """The 512-product batch (n_i log-uniform 500..20000, Z_i ~ U{2..40}, half
-    float64 and half float32): sampled products against the oracle, all
-    against the closed form of their product count (Op_j = Z_i^2)."""
+    float64 and half float32), every product against the oracle: structure
+    bit-exact, values within tau * sum|a b| (tau = 1e-12 for the float64
+    half, 1e-5 for the float32 half); the total product count against its
+    closed form (every column of A_i holds Z_i entries, so Op_j = Z_i^2)."""
     from paper_2303_02471_gb300 import ops
     pairs = synth.batch_pairs(512, seed=0)
     As, Bs = _upload_pairs(pairs)
@@ -186,9 +191,9 @@ def test_workload4_full_batch_sampled():
     plan.check()
     want = sum(A.ncols * (A.colptr[1] - A.colptr[0]) ** 2 for A, _ in pairs)
     assert plan.info()["products"] == want
-    for i in list(range(0, 512, 43)) + [255, 256, 511]:
-        A, B = pairs[i]
-        assert_matches_oracle(Cs[i], A, B, nthreads=8)
+    for i, ((A, B), C) in enumerate(zip(pairs, Cs)):
+        assert C.values.dtype == (As[i].values.dtype)
+        assert_matches_oracle(C, A, B, nthreads=NCPU)
 
 
 def test_autotune_chooses_and_caches(tmp_path):

@@ -285,7 +285,7 @@ def test_workspace_too_small():
     cp = torch.empty(A.ncols + 1, dtype=torch.int64, device="cuda")
     nnz, h = ctypes.c_int64(), ctypes.c_void_p()
     cA = ops._csc(A)
-    rc = N.lib().spgemm_symbolic(ctypes.byref(cA), ctypes.byref(cA), None, ctypes.c_void_p(ws.data_ptr()),
+    rc = N.lib().spgemm_symbolic(None, ctypes.byref(cA), ctypes.byref(cA), None, ctypes.c_void_p(ws.data_ptr()),
                                  ws.numel(), ctypes.c_void_p(cp.data_ptr()), ctypes.byref(nnz),
                                  ctypes.byref(h), ops._stream())
     assert N.STATUS[rc] == "SPG_ERR_WORKSPACE"
@@ -303,3 +303,63 @@ def test_empty_shapes():
         A, B = synth.fuzz_pair(seed)
         C, _ = _run(A, B)
         assert_matches_oracle(C, A, B)
+
+
+def test_bulk_wait_time_out_is_reported_without_a_fault():
+    """The dense kernel's wait for a column's kept flags gives up at once
+    (test knob): the copy it waited for still lands before the CTA exits, the
+    call reports SPG_ERR_TIMEOUT, and the next product runs clean.  4096 rows
+    that all hold entries give 128-word flags, which the kernel stages by a
+    bulk copy."""
+    from paper_2303_02471_gb300 import ops
+    A = synth.random_z(4096, 30, 60, seed=21)
+    assert np.unique(A.rowidx).size == A.nrows
+    dA = upload(A)
+    _, _, plan = ops.spgemm_symbolic(dA, dA, ops.Config(t=64, test_wait_timeout=True))
+    assert plan.info()["bins"][13] == A.ncols
+    ops.spgemm_numeric(plan, dA, dA)
+    assert _status(plan.check) == "SPG_ERR_TIMEOUT"
+    plan.destroy()
+    C, plan2 = _run(A, A, t=64)
+    assert_matches_oracle(C, A, A, nthreads=NCPU)
+
+
+def test_handle_serves_several_plans():
+    """Plans made with one handle fork onto its side streams (dense and
+    lane-group bins together) and read back through its buffer; the handle
+    is released after them."""
+    import torch
+    from paper_2303_02471_gb300 import ops
+    h = ops.Handle(torch.cuda.current_device())
+    A = synth.rmat(12, seed=12, col_cap=400)
+    B = synth.rmat(12, seed=13, col_cap=400)
+    dA, dB = upload(A), upload(B)
+    plans, outs = [], []
+    for X, Y in ((dA, dA), (dA, dB), (dB, dA)):
+        _, _, plan = ops.spgemm_symbolic(X, Y, ops.Config(t=64), lib_handle=h)
+        assert any(plan.bin_streams())
+        outs.append(ops.spgemm_numeric(plan, X, Y))
+        plans.append(plan)
+    for plan in plans:
+        plan.check()
+    for (X, Y), C in zip(((A, A), (A, B), (B, A)), outs):
+        assert_matches_oracle(C, X, Y)
+    for plan in plans:
+        plan.destroy()
+    h.destroy()
+
+
+def test_serial_bins_match_forked_bins():
+    # side_streams = 0 runs every bin in order on the caller's stream: same C
+    from paper_2303_02471_gb300 import ops
+    A = synth.rmat(12, seed=14, col_cap=400)
+    dA = upload(A)
+    C1, p1 = ops.spgemm(dA, dA, ops.Config(t=64))
+    C2, p2 = ops.spgemm(dA, dA, ops.Config(t=64, side_streams=False))
+    assert any(p1.bin_streams()) and not any(p2.bin_streams())
+    p1.check()
+    p2.check()
+    assert (C1.rowidx == C2.rowidx).all()
+    ref = oracle.spgemm(A, A)
+    assert_matches_oracle(C1, A, A, ref=ref)
+    assert_matches_oracle(C2, A, A, ref=ref)
