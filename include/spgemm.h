@@ -117,7 +117,17 @@ typedef struct {
      * written, and spg_plan_check reports SPG_ERR_TIMEOUT: the time-out path
      * runs without any fault. */
     int32_t test_wait_timeout;
+    /* Accumulator of the lane-group bins (columns with Op_j <= 256):
+     * SPG_ACC_HASH, the hash tables of Section 3.2; SPG_ACC_ESC, the ESC
+     * algorithm of Section 4 (the products of a tile of columns are expanded
+     * into shared memory, radix-sorted by (column, row) and compressed); a
+     * bin whose (column, row) keys do not fit 32 bits keeps hash tables.
+     * Both give the same C (the ESC sums do not depend on timing).  Only the
+     * single products use it; the batched calls keep hash tables. */
+    int32_t small_accumulator;
 } spg_config;
+
+enum { SPG_ACC_HASH = 0, SPG_ACC_ESC = 1 };
 
 typedef struct spg_plan spg_plan;
 

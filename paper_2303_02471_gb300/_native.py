@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libspgemm.so")
 i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
 
 SPG_F64, SPG_F32 = 0, 1
+SPG_ACC_HASH, SPG_ACC_ESC = 0, 1
 STATUS = {
     0: "SPG_OK", 1: "SPG_ERR_INVALID", 2: "SPG_ERR_WORKSPACE", 3: "SPG_ERR_TABLE_OVERFLOW",
     4: "SPG_ERR_TIMEOUT", 5: "SPG_ERR_CUDA", 6: "SPG_ERR_UNSUPPORTED", 7: "SPG_ERR_INDEX_OVERFLOW",
@@ -30,7 +31,7 @@ class SpgCsc(ctypes.Structure):
 class SpgConfig(ctypes.Structure):
     _fields_ = [("t", i64), ("hash_cta_max", i32), ("cta_threads", i32), ("validate", i32),
                 ("table_shrink", i32), ("scratch_cap_bytes", i64), ("dense_cache_bytes", i64),
-                ("side_streams", i32), ("test_wait_timeout", i32)]
+                ("side_streams", i32), ("test_wait_timeout", i32), ("small_accumulator", i32)]
 
 
 class SpgError(RuntimeError):

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 
+#include "esc.cuh"
 #include "handle.cuh"
 
 using namespace spg;
@@ -160,6 +161,9 @@ struct spg_plan {
     // created on first use
     spg_handle *h = nullptr;
     SideStreams own;
+    // lane-group bins worked by the ESC accumulator (and their tile shapes)
+    bool esc[NBINS] = {};
+    EscShape esc_shape_of[NBINS];
 
     ~spg_plan() {
         for (int b = 0; b < NBINS; ++b) {
@@ -243,6 +247,7 @@ spg_status spg_config_default(spg_config *cfg) {
     cfg->dense_cache_bytes = (int64_t)2 << 30;
     cfg->side_streams = 1;
     cfg->test_wait_timeout = 0;
+    cfg->small_accumulator = SPG_ACC_HASH;
     return SPG_OK;
 }
 
@@ -274,6 +279,7 @@ static spg_status check_config(const spg_config &c) {
     if (c.cta_threads < 128 || c.cta_threads > 1024 || c.cta_threads % 32) return SPG_ERR_INVALID;
     if (c.table_shrink < 0 || c.table_shrink > 30) return SPG_ERR_INVALID;
     if (c.dense_cache_bytes < 0 || c.scratch_cap_bytes < 0) return SPG_ERR_INVALID;
+    if (c.small_accumulator != SPG_ACC_HASH && c.small_accumulator != SPG_ACC_ESC) return SPG_ERR_INVALID;
     return SPG_OK;
 }
 
@@ -415,7 +421,12 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
         if (!P->side_streams()) { delete P; return SPG_ERR_CUDA; }
         CK(cudaEventRecord(P->ss().fork, s));
     }
+    if (c.small_accumulator == SPG_ACC_ESC)
+        for (int b = BIN_WARP0; b < BIN_CTA0; ++b) P->esc[b] = esc_shape(b, P->mC, P->esc_shape_of[b]);
     auto sym_bin = [&](int b, cudaStream_t sb) {
+        if (P->esc[b])
+            return launch_esc_bin(P->task(b), o, C_colptr, C_colptr, nullptr, nullptr, false, P->dtype,
+                                  P->esc_shape_of[b], P->dev.sms, sb);
         // the symbolic CTA kernels carry no values: CTAs of up to 256 threads,
         // several per SM, overlap one another's barriers (measured faster)
         Geo g = symbolic_geometry(b, (int64_t)P->host.hist[b], P->mC, std::min(c.cta_threads, kSymCtaThreads),
@@ -495,7 +506,10 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
     if (fork && !P->side_streams()) return SPG_ERR_CUDA;
     auto launch = [&](int b, cudaStream_t sb) -> spg_status {
         if (P->timing && cudaEventRecord(P->ev0[b], sb) != cudaSuccess) return SPG_ERR_CUDA;
-        cudaError_t e = launch_numeric_bin(P->task(b), o, C_colptr, C_rowidx, C_values, P->dtype, P->num_geo[b], sb);
+        cudaError_t e = P->esc[b] ? launch_esc_bin(P->task(b), o, C_colptr, nullptr, C_rowidx, C_values, true,
+                                                   P->dtype, P->esc_shape_of[b], P->dev.sms, sb)
+                                  : launch_numeric_bin(P->task(b), o, C_colptr, C_rowidx, C_values, P->dtype,
+                                                       P->num_geo[b], sb);
         if (e != cudaSuccess) return SPG_ERR_CUDA;
         if (P->timing && cudaEventRecord(P->ev1[b], sb) != cudaSuccess) return SPG_ERR_CUDA;
         return SPG_OK;

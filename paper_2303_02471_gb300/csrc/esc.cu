@@ -1,0 +1,331 @@
+// ESC accumulator (Expand, Sort, Compress; Section 4) for the light columns
+// of C = A x B: the lane-group bins, Op_j <= 256.
+//
+// A warp works a tile of kEscTile products: the columns of a bin list are cut
+// into tiles of kEscTile / opmax columns (opmax = the bin's largest Op_j, so
+// every tile fits), one column per lane.  Per tile:
+//   Expand    every product A_ik * B_kj of the tile's columns is gathered
+//             into the warp's shared memory as the key (c << rb) | i (c the
+//             column's place in the tile, i the row, rb the row bits) and
+//             its value;
+//   Sort      a stable LSD radix sort of the keys (digits of kEscRadixBits
+//             bits; a lane's place among the lanes with the same digit comes
+//             from __match_any_sync), which orders the products by column
+//             and, inside a column, by row;
+//   Compress  equal keys are neighbours: the first of each run sums the run
+//             in sorted order and writes one entry of C at its column's
+//             pointer plus its rank among the column's runs.
+// The sums do not depend on timing (no atomics on values).
+//
+// Modes: with values and no count output it is the numeric phase (C's
+// column pointers come from the symbolic phase; a column whose run count
+// differs is reported); without values it counts the runs of each column
+// into cnt_out[j + 1] (the symbolic phase); with values and a count output it
+// writes each column at base[j] and its count into cnt_out[j + 1] (the
+// single-pass form, where base holds slots sized by Op_j).
+//
+// Keys are 32-bit: the forward passes' rows and the tile's column places must
+// fit (rb + log2(columns per tile) <= 32); the host keeps hash tables
+// otherwise.
+#include "columns.cuh"
+#include "esc.cuh"
+
+namespace spg {
+
+template <typename VT>
+struct EscWarp {
+    uint32_t key[2][kEscTile];
+    VT val[2][kEscTile];
+    uint32_t cnt[1 << kEscRadixBits];
+    int32_t hstart[32];
+};
+
+template <typename VT>
+__host__ __device__ constexpr size_t esc_warp_bytes() {
+    return (sizeof(EscWarp<VT>) + 15) & ~size_t(15);
+}
+
+// Lane holding the owner of position q among 32 lanes with non-decreasing
+// exclusive offsets `excl` (the last lane whose offset is <= q).
+__device__ __forceinline__ int esc_owner(int excl, int q) {
+    int s = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int ex = __shfl_sync(0xffffffffu, excl, s + step);
+        if (ex <= q) s += step;
+    }
+    return s;
+}
+
+template <bool VALS, typename VT>
+__global__ void __launch_bounds__(kEscWarps * 32) k_esc(BinTask t, Operands o, const int64_t *base,
+                                                        int64_t *cnt_out, int32_t *Crow, VT *Cval, EscShape e) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_max, s_sum;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    EscWarp<VT> &S = *reinterpret_cast<EscWarp<VT> *>(smem + (size_t)warp * esc_warp_bytes<VT>());
+    if (threadIdx.x == 0) s_max = s_sum = 0;
+    __syncthreads();
+    const TOps<VT> ops = typed<VT>(o);
+    const uint64_t pol = keep_policy();
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t rowmask = e.rb >= 32 ? 0xffffffffu : ((1u << e.rb) - 1u);
+    const int64_t ntiles = ceil_div(t.count, (int64_t)e.ct);
+    unsigned long long my_max = 0, my_sum = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * kEscWarps + warp; tile < ntiles;
+         tile += (int64_t)gridDim.x * kEscWarps) {
+        const int64_t first = tile * e.ct;
+        const int nc = (int)(t.count - first < e.ct ? t.count - first : e.ct);
+        // ---- the tile's columns, one per lane: B entries and their offsets
+        int32_t j = 0;
+        int64_t p0 = 0, cb = 0, ccap = 0;
+        int nb = 0;
+        if (lane < nc) {
+            j = t.cols[first + lane];
+            p0 = ops.Bcp[j];
+            nb = (int)(ops.Bcp[j + 1] - p0);
+            cb = base[j];
+            ccap = base[j + 1] - cb;  // entries the column's place holds
+        }
+        int eincl = nb;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, eincl, d);
+            if (lane >= d) eincl += v;
+        }
+        const int eexcl = eincl - nb;
+        const int E = __shfl_sync(0xffffffffu, eincl, 31);
+        // ---- expand: 32 B entries per round, then their products
+        int n = 0;
+        bool over = false;
+        for (int e0 = 0; e0 < E; e0 += 32) {
+            const int en = e0 + lane;
+            const int c = esc_owner(eexcl, en < E ? en : E - 1);
+            const int64_t p0c = __shfl_sync(0xffffffffu, p0, c);
+            const int exc = __shfl_sync(0xffffffffu, eexcl, c);
+            int z = 0;
+            int64_t a0 = 0;
+            VT bv = VT(0);
+            if (en < E) {
+                const int64_t p = p0c + (en - exc);
+                const int32_t k = ops.Brow[p];
+                a0 = ops.Acp[k];
+                z = (int)(ops.Acp[k + 1] - a0);
+                if (VALS) bv = ops.Bval[p];
+            }
+            int zincl = z;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, zincl, d);
+                if (lane >= d) zincl += v;
+            }
+            const int zexcl = zincl - z;
+            const int total = __shfl_sync(0xffffffffu, zincl, 31);
+            if (n + total > kEscTile) {  // only if the pattern changed since planning
+                over = true;
+                break;
+            }
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int q = q0 + lane;
+                const int s = esc_owner(zexcl, q < total ? q : total - 1);
+                const int64_t a0s = __shfl_sync(0xffffffffu, a0, s);
+                const int exs = __shfl_sync(0xffffffffu, zexcl, s);
+                const int cs = __shfl_sync(0xffffffffu, c, s);
+                VT bs = VT(0);
+                if (VALS) bs = __shfl_sync(0xffffffffu, bv, s);
+                if (q < total) {
+                    const int64_t qa = a0s + (q - exs);
+                    const int32_t row = ld_keep(ops.Arow + qa, pol);
+                    S.key[0][n + q] = ((uint32_t)cs << e.rb) | ((uint32_t)row & rowmask);
+                    if (VALS) S.val[0][n + q] = ld_keep(ops.Aval + qa, pol) * bs;
+                }
+            }
+            n += total;
+        }
+        if (over) {
+            if (lane == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
+            continue;
+        }
+        __syncwarp();
+        // ---- sort: stable LSD radix over the key bits
+        int cur = 0;
+        for (int pass = 0; pass < e.passes; ++pass) {
+            const int sh = pass * kEscRadixBits;
+#pragma unroll
+            for (int b = lane; b < (1 << kEscRadixBits); b += 32) S.cnt[b] = 0u;
+            __syncwarp();
+            for (int i = lane; i < n; i += 32)
+                atomicAdd(&S.cnt[(S.key[cur][i] >> sh) & ((1u << kEscRadixBits) - 1u)], 1u);
+            __syncwarp();
+            {  // exclusive scan of the buckets: lane l owns the 8 buckets from 8 l
+                constexpr int PER = (1 << kEscRadixBits) / 32;
+                uint32_t v[PER];
+                uint32_t run = 0;
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    v[u] = S.cnt[lane * PER + u];
+                    const uint32_t x = v[u];
+                    v[u] = run;
+                    run += x;
+                }
+                uint32_t incl = run;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                const uint32_t off = incl - run;
+#pragma unroll
+                for (int u = 0; u < PER; ++u) S.cnt[lane * PER + u] = v[u] + off;
+            }
+            __syncwarp();
+            for (int i0 = 0; i0 < n; i0 += 32) {
+                const int i = i0 + lane;
+                const bool valid = i < n;
+                const uint32_t k = valid ? S.key[cur][i] : 0u;
+                VT v = VT(0);
+                if (VALS && valid) v = S.val[cur][i];
+                // lanes past n get digits of their own, so they never share a
+                // group with a key
+                const uint32_t dg = valid ? ((k >> sh) & ((1u << kEscRadixBits) - 1u)) : (0x10000u + lane);
+                const unsigned same = __match_any_sync(0xffffffffu, dg);
+                const int leader = __ffs(same) - 1;
+                uint32_t at = 0;
+                if (valid && lane == leader) {
+                    at = S.cnt[dg];
+                    S.cnt[dg] = at + (uint32_t)__popc(same);
+                }
+                at = __shfl_sync(0xffffffffu, at, leader) + (uint32_t)__popc(same & lt);
+                if (valid) {
+                    S.key[cur ^ 1][at] = k;
+                    if (VALS) S.val[cur ^ 1][at] = v;
+                }
+                __syncwarp();
+            }
+            cur ^= 1;
+        }
+        // ---- compress: the first key of each run writes the run's sum
+        if (lane < 32) S.hstart[lane] = 0x7fffffff;  // columns without runs stay unset
+        __syncwarp();
+        int hbase = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < n;
+            const uint32_t k = valid ? S.key[cur][i] : 0u;
+            const uint32_t kp = valid && i > 0 ? S.key[cur][i - 1] : 0u;
+            const bool head = valid && (i == 0 || kp != k);
+            const unsigned hm = __ballot_sync(0xffffffffu, head);
+            const int hr = hbase + __popc(hm & lt);
+            hbase += __popc(hm);
+            const int c = (int)(k >> e.rb);
+            if (head && (i == 0 || (int)(kp >> e.rb) != c)) S.hstart[c] = hr;
+            __syncwarp();
+            if (VALS) {
+                const int64_t cbase = __shfl_sync(0xffffffffu, cb, c & 31);
+                const int64_t cc = __shfl_sync(0xffffffffu, ccap, c & 31);
+                if (head) {
+                    VT sum = S.val[cur][i];
+                    for (int m2 = i + 1; m2 < n && S.key[cur][m2] == k; ++m2) sum += S.val[cur][m2];
+                    const int64_t r = hr - S.hstart[c];
+                    // a column with more runs than its place holds is reported
+                    // below and not written past its place
+                    if (r < cc) {
+                        Crow[cbase + r] = ops.crow((int32_t)(k & rowmask));
+                        Cval[cbase + r] = sum;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // ---- per-column run counts: written (symbolic, single pass) or checked.
+        // A column's runs end where the next column with runs starts.
+        const int st = lane < nc ? S.hstart[lane] : 0x7fffffff;
+        int nxt = st;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_down_sync(0xffffffffu, nxt, d);
+            if (lane + d < 32 && v < nxt) nxt = v;
+        }
+        nxt = __shfl_down_sync(0xffffffffu, nxt, 1);
+        if (lane == 31 || nxt > hbase) nxt = hbase;
+        if (lane < nc) {
+            const int64_t cnt = st == 0x7fffffff ? 0 : (int64_t)(nxt - st);
+            if (cnt_out) {
+                cnt_out[j + 1] = cnt;
+                if ((unsigned long long)cnt > my_max) my_max = (unsigned long long)cnt;
+                my_sum += (unsigned long long)cnt;
+            } else if (ccap != cnt) {
+                set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
+            }
+        }
+        __syncwarp();
+    }
+    if (cnt_out) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            my_sum += __shfl_xor_sync(0xffffffffu, my_sum, d);
+            const unsigned long long om = __shfl_xor_sync(0xffffffffu, my_max, d);
+            if (om > my_max) my_max = om;
+        }
+        if (lane == 0 && my_sum) {
+            atomicMax(&s_max, my_max);
+            atomicAdd(&s_sum, my_sum);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_max) {
+            atomicMax(&t.ctrl->maxnnz[t.bin], s_max);
+            atomicAdd(&t.ctrl->binnnz[t.bin], s_sum);
+        }
+    }
+}
+
+// ------------------------------------------------------------- launches
+template <typename K>
+static void esc_allow_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+bool esc_shape(int bin, int64_t m, EscShape &e) {
+    if (bin < BIN_WARP0 || bin >= BIN_CTA0) return false;
+    const int opmax = warp_bin_opmax(bin - BIN_WARP0);
+    e.ct = kEscTile / opmax;
+    if (e.ct > 32) e.ct = 32;
+    if (e.ct < 1) return false;
+    int cb = 0;
+    while ((1 << cb) < e.ct) ++cb;
+    int rb = 1;
+    while (rb < 32 && ((int64_t)1 << rb) < m) ++rb;
+    e.rb = rb;
+    const int bits = rb + cb;
+    if (bits > 32) return false;
+    e.passes = (bits + kEscRadixBits - 1) / kEscRadixBits;
+    return true;
+}
+
+template <bool VALS, typename VT>
+static cudaError_t launch_esc_t(const BinTask &t, const Operands &o, const int64_t *base, int64_t *cnt_out,
+                                int32_t *Crow, VT *Cval, const EscShape &e, int sms, cudaStream_t s) {
+    if (t.count <= 0) return cudaSuccess;
+    auto k = k_esc<VALS, VT>;
+    const size_t smem = (size_t)kEscWarps * esc_warp_bytes<VT>();
+    esc_allow_smem(k, smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kEscWarps * 32, smem) != cudaSuccess || occ < 1)
+        occ = 1;
+    const int64_t ntiles = ceil_div(t.count, (int64_t)e.ct);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntiles, kEscWarps), (int64_t)occ * sms));
+    k<<<(unsigned)grid, kEscWarps * 32, smem, s>>>(t, o, base, cnt_out, Crow, Cval, e);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_esc_bin(const BinTask &t, const Operands &o, const int64_t *base, int64_t *cnt_out,
+                           int32_t *Crow, void *Cval, bool values, int dtype, const EscShape &e, int sms,
+                           cudaStream_t s) {
+    if (!values)
+        return launch_esc_t<false, float>(t, o, base, cnt_out, nullptr, nullptr, e, sms, s);
+    return dtype == SPG_F64
+               ? launch_esc_t<true, double>(t, o, base, cnt_out, Crow, static_cast<double *>(Cval), e, sms, s)
+               : launch_esc_t<true, float>(t, o, base, cnt_out, Crow, static_cast<float *>(Cval), e, sms, s);
+}
+
+}  // namespace spg

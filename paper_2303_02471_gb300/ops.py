@@ -84,6 +84,7 @@ class Config:
     dense_cache_bytes: Optional[int] = None
     side_streams: Optional[bool] = None
     test_wait_timeout: Optional[bool] = None
+    small_accumulator: Optional[str] = None  # "hash" or "esc"
 
     def native(self) -> N.SpgConfig:
         c = N.SpgConfig()
@@ -97,6 +98,8 @@ class Config:
             v = getattr(self, f)
             if v is not None:
                 setattr(c, f, int(bool(v)))
+        if self.small_accumulator is not None:
+            c.small_accumulator = {"hash": N.SPG_ACC_HASH, "esc": N.SPG_ACC_ESC}[self.small_accumulator]
         return c
 
 

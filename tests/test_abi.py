@@ -44,9 +44,10 @@ def test_struct_layouts():
     from paper_2303_02471_gb300 import _native as N
     assert ctypes.sizeof(N.SpgCsc) == 56
     assert N.SpgCsc.values.offset == 40 and N.SpgCsc.dtype.offset == 48
-    assert ctypes.sizeof(N.SpgConfig) == 48
+    assert ctypes.sizeof(N.SpgConfig) == 56
     assert N.SpgConfig.dense_cache_bytes.offset == 32
     assert N.SpgConfig.side_streams.offset == 40 and N.SpgConfig.test_wait_timeout.offset == 44
+    assert N.SpgConfig.small_accumulator.offset == 48
 
 
 def test_status_strings_and_defaults(lib):

@@ -363,3 +363,57 @@ def test_serial_bins_match_forked_bins():
     ref = oracle.spgemm(A, A)
     assert_matches_oracle(C1, A, A, ref=ref)
     assert_matches_oracle(C2, A, A, ref=ref)
+
+
+# ------------------------------------------------------------------- ESC
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("seed", range(40))
+def test_esc_fuzz(seed, dtype):
+    A, B = synth.fuzz_pair(seed, dtype=dtype)
+    C, _ = _run(A, B, small_accumulator="esc")
+    assert_matches_oracle(C, A, B)
+
+
+@pytest.mark.parametrize("t", [None, 40, INF])
+def test_esc_rmat_every_bin(t):
+    # light columns by ESC beside CTA hash bins, the global table and the dense SPA
+    A = synth.rmat(13, seed=2, col_cap=600)
+    C, plan = _run(A, A, t=t, hash_cta_max=1024, small_accumulator="esc")
+    assert sum(plan.info()["bins"][1:7]) > 0
+    assert_matches_oracle(C, A, A, nthreads=NCPU)
+
+
+def test_esc_workload2_random_full():
+    """The random 2^20 product (every column Op_j <= 64) with the ESC accumulator."""
+    A, B = synth.workload(2)
+    C, plan = _run(A, B, small_accumulator="esc")
+    assert sum(plan.info()["bins"][1:7]) == B.ncols - plan.info()["bins"][0]
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
+def test_esc_tall_and_unsorted():
+    # 2^20 rows (20-bit rows in the keys) and columns whose rows come unsorted
+    rng = np.random.default_rng(7)
+    A = _tall(1 << 20, 4000, 1, 12, seed=25)
+    B = _tall(4000, 3000, 1, 9, seed=26)
+    perm = np.concatenate([rng.permutation(np.arange(A.colptr[j], A.colptr[j + 1])) for j in range(A.ncols)])
+    Au = synth.CSC(A.nrows, A.ncols, A.colptr, A.rowidx[perm], A.values[perm])
+    C, _ = _run(Au, B, small_accumulator="esc")
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
+def test_esc_sums_do_not_depend_on_timing():
+    # every column light (Op_j <= 225): the whole C comes from ESC, whose sums
+    # run in sorted order, so two calls agree bit for bit
+    from paper_2303_02471_gb300 import ops
+    A = synth.random_z(20000, 1, 15, seed=8)
+    B = synth.random_z(20000, 1, 15, seed=9)
+    dA, dB = upload(A), upload(B)
+    _, _, plan = ops.spgemm_symbolic(dA, dB, ops.Config(small_accumulator="esc"))
+    assert sum(plan.info()["bins"][7:]) == 0
+    C1 = ops.spgemm_numeric(plan, dA, dB)
+    v1 = C1.values.clone()
+    C2 = ops.spgemm_numeric(plan, dA, dB)
+    plan.check()
+    assert (C2.values == v1).all()
+    assert_matches_oracle(C2, A, B)
