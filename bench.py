@@ -463,6 +463,65 @@ def product_report(prod, res, serial, peak, peak_kind, args, w=8):
     return roof, per_bin
 
 
+def time_single_pass(A_h, B_h, dev, cfg, steps, warmup, flush):
+    """Steps of the single-pass form through the C ABI (spgemm_single_pass,
+    then spgemm_single_pass_copy into C), the workspace sized once
+    beforehand (sizing depends only on the patterns, as allocation does)."""
+    import torch
+    from paper_2303_02471_gb300 import _native as N
+    from paper_2303_02471_gb300 import ops
+    A = ops.CscMatrix.from_host(A_h, device=dev)
+    B = A if B_h is A_h else ops.CscMatrix.from_host(B_h, device=dev)
+    hd = ops.handle(dev)
+    lib = N.lib()
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    cA, cB = ops._csc(A), ops._csc(B)
+    ncfg = cfg.native()
+    need = ops.single_pass_workspace_size(A, B, cfg, hd)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=dev)
+
+    def run():
+        nnz, h = ctypes.c_int64(), ctypes.c_void_p()
+        N.check(lib.spgemm_single_pass(hd.ptr, ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(ncfg),
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       ctypes.c_void_p(colptr.data_ptr()), ctypes.byref(nnz), ctypes.byref(h), sp),
+                "spgemm_single_pass")
+        return h, nnz.value
+
+    h, nnz = run()
+    lib.spg_plan_destroy(h)
+    rows = torch.empty(nnz, dtype=torch.int32, device=dev)
+    vals = torch.empty(nnz, dtype=A.dtype, device=dev)
+
+    def copy(h):
+        N.check(lib.spgemm_single_pass_copy(h, ctypes.c_void_p(colptr.data_ptr()), ctypes.c_void_p(rows.data_ptr()),
+                                            ctypes.c_void_p(vals.data_ptr()), sp), "spgemm_single_pass_copy")
+
+    for _ in range(warmup):
+        h, _ = run()
+        copy(h)
+        lib.spg_plan_destroy(h)
+    torch.cuda.synchronize()
+    t_all, t_sp, t_cp = [], [], []
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        ev = _events(3)
+        ev[0].record(stream)
+        h, _ = run()
+        ev[1].record(stream)
+        copy(h)
+        ev[2].record(stream)
+        N.check(lib.spg_plan_check(h, sp), "spg_plan_check")
+        lib.spg_plan_destroy(h)
+        t_all.append(ev[0].elapsed_time(ev[2]))
+        t_sp.append(ev[0].elapsed_time(ev[1]))
+        t_cp.append(ev[1].elapsed_time(ev[2]))
+    return {"ms_per_step": round(float(np.median(t_all)), 4), "ms_single_pass": round(float(np.median(t_sp)), 4),
+            "ms_copy": round(float(np.median(t_cp)), 4), "workspace_bytes": int(need)}
+
+
 def measure_workload(k, args, dev, flush, steps, warmup, peak, peak_kind, cfg=None):
     """Steps, roofline and per-bin figures of workload k (a side entry)."""
     from paper_2303_02471_gb300 import ops
@@ -479,6 +538,10 @@ def measure_workload(k, args, dev, flush, steps, warmup, peak, peak_kind, cfg=No
            "phases_ms": {"symbolic": round(float(np.median(res["sym"])), 4),
                          "numeric": round(float(np.median(res["num"])), 4)},
            "roofline": roof, "numeric_bins": per_bin, "launches_per_step": prod.launches}
+    sp = time_single_pass(A_h, B_h, dev, cfg, steps, warmup, flush)
+    sp["value"] = round(2.0 * prod.products / (sp["ms_per_step"] * 1e-3) / 1e9, 3)
+    sp["unit"] = "GFLOP/s"
+    out["single_pass"] = sp
     del prod
     return out
 
@@ -506,6 +569,11 @@ def run_ours(args, rank, world):
     serial = serial_bin_times(A_h, B_h, dev, cfg, flush)
     roof, per_bin = product_report(prod, res, serial, peak, peak_kind, args, w)
 
+    sp_main = None
+    if not args.no_aux:
+        sp_main = time_single_pass(A_h, B_h, dev, cfg, max(3, min(args.steps, 10)), 3, flush)
+        sp_main["value"] = round(2.0 * products / (sp_main["ms_per_step"] * 1e-3) / 1e9, 3)
+        sp_main["unit"] = "GFLOP/s"
     # end to end through host buffers
     e2e = None
     if not args.no_e2e:
@@ -548,7 +616,8 @@ def run_ours(args, rank, world):
                            "parallelism": f"replicas x{world}"},
                 "phases_ms": {"symbolic": round(float(np.median(res["sym"])), 4),
                               "numeric": round(float(np.median(res["num"])), 4)},
-                "roofline": roof, "numeric_bins": per_bin, "cpu_baseline": base, "e2e": e2e, **aux,
+                "roofline": roof, "numeric_bins": per_bin, "single_pass": sp_main, "cpu_baseline": base, "e2e": e2e,
+                **aux,
                 "gpu_launches": prod.launches * args.steps,
                 "clocks": res["clocks"]}
     return line

@@ -266,6 +266,51 @@ spg_status spgemm_backward(spg_plan *plan, const spg_csc *A, const spg_csc *B,
                            const void *dC_values, void *dA_values,
                            void *dB_values, spg_stream stream);
 
+/*
+ * Single-pass form (no symbolic phase).  Section 3.2 sizes a column's hash
+ * table from Op_j alone; taken one step further, every column gets a slot of
+ * min(Op_j, m) entries (m = rows of the forward passes) in the workspace,
+ * which bounds nnz(C_j) without counting it first.  Each bin's accumulator
+ * (hash table, ESC or dense SPA, as in spgemm_numeric) writes its sorted
+ * column into its slot and its entry count into C_colptr[j + 1]; the counts
+ * are scanned into C_colptr.  spgemm_single_pass_copy then moves the columns
+ * from their slots into the caller's C.  The slots cost sum_j min(Op_j, m)
+ * entries of workspace and one copy of C, against the symbolic phase's walk
+ * of every product: it pays where Op_j and nnz(C_j) are close (very sparse
+ * columns).
+ *
+ * spgemm_single_pass_size: the workspace bytes spgemm_single_pass needs
+ *   (they depend on Op_j, hence on the patterns).  Runs the preparation (input
+ *   validation, row numbering, Op_j) in `workspace`, which must hold at least
+ *   spgemm_workspace_size(A, B, cfg) bytes computed with
+ *   cfg->dense_cache_bytes = 0 (the single pass keeps no flags); C_colptr
+ *   (device int64[B->ncols + 1]) is used as scratch.  Synchronises.
+ * spgemm_single_pass: A and B with values; workspace of at least the bytes
+ *   above, 256-byte aligned; writes C_colptr (device int64[B->ncols + 1]) and
+ *   nnzC (host), and returns a plan whose slots hold C.  The plan also serves
+ *   spgemm_numeric (which recomputes C from the A and B it is given, into the
+ *   caller's buffers), spgemm_backward and the plan queries.  Synchronises.
+ * spgemm_single_pass_copy: C's rows (device int32[nnzC]) and values (device,
+ *   plan dtype) from the plan's slots, in order; asynchronous.  The values are
+ *   those of the A and B given to spgemm_single_pass.
+ * Errors: as spgemm_symbolic; SPG_ERR_WORKSPACE when the workspace is smaller
+ * than spgemm_single_pass_size says; SPG_ERR_INVALID for a plan that is not
+ * a single-pass plan (copy).
+ */
+spg_status spgemm_single_pass_size(spg_handle *handle, const spg_csc *A,
+                                   const spg_csc *B, const spg_config *cfg,
+                                   void *workspace, size_t ws_bytes,
+                                   int64_t *C_colptr, size_t *bytes,
+                                   spg_stream stream);
+spg_status spgemm_single_pass(spg_handle *handle, const spg_csc *A,
+                              const spg_csc *B, const spg_config *cfg,
+                              void *workspace, size_t ws_bytes,
+                              int64_t *C_colptr, int64_t *nnzC,
+                              spg_plan **plan, spg_stream stream);
+spg_status spgemm_single_pass_copy(spg_plan *plan, const int64_t *C_colptr,
+                                   int32_t *C_rowidx, void *C_values,
+                                   spg_stream stream);
+
 /* Synchronise `stream` and report the first kernel-side error recorded in
  * the plan's workspace since spgemm_symbolic (SPG_OK if none). */
 spg_status spg_plan_check(spg_plan *plan, spg_stream stream);

@@ -51,6 +51,11 @@ SIGNATURES = {
     "spgemm_symbolic": (i32, [vp, vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(i64),
                               ctypes.POINTER(vp), vp]),
     "spgemm_numeric": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+    "spgemm_single_pass_size": (i32, [vp, vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_size_t),
+                                      vp]),
+    "spgemm_single_pass": (i32, [vp, vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(i64),
+                                 ctypes.POINTER(vp), vp]),
+    "spgemm_single_pass_copy": (i32, [vp, vp, vp, vp, vp]),
     "spgemm_backward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "spg_plan_check": (i32, [vp, vp]),
     "spg_plan_destroy": (i32, [vp]),

@@ -164,6 +164,11 @@ struct spg_plan {
     // lane-group bins worked by the ESC accumulator (and their tile shapes)
     bool esc[NBINS] = {};
     EscShape esc_shape_of[NBINS];
+    // single pass: the columns' slots (offsets, rows, values) after the
+    // regular layout, sum of the slot sizes
+    bool single = false;
+    size_t soff_at = 0, srow_at = 0, sval_at = 0, slots_total = 0;
+    int64_t capsum = 0;
 
     ~spg_plan() {
         for (int b = 0; b < NBINS; ++b) {
@@ -317,21 +322,33 @@ spg_status spg_destroy(spg_handle *handle) {
     return SPG_OK;
 }
 
-spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *B, const spg_config *cfg,
-                           void *workspace, size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC, spg_plan **plan_out,
-                           spg_stream stream) {
-    if (plan_out) *plan_out = nullptr;
-    if (!C_colptr || !nnzC || !plan_out) return SPG_ERR_INVALID;
-    spg_status st = check_pair(A, B, false);
-    if (st != SPG_OK) return st;
-    spg_config c = normalized(cfg);
-    if ((st = check_config(c)) != SPG_OK) return st;
+// Slots of the single pass after the regular layout: offsets int64[nB + 1],
+// rows int32[capsum], values[capsum].
+static void slot_layout(spg_plan *P) {
+    const size_t w = P->dtype == SPG_F64 ? 8 : 4;
+    size_t off = align256(P->L.total);
+    P->soff_at = off;
+    off = align256(off + (size_t)(P->nB + 1) * 8);
+    P->srow_at = off;
+    off = align256(off + (size_t)P->capsum * 4);
+    P->sval_at = off;
+    off = align256(off + (size_t)P->capsum * w);
+    P->slots_total = off;
+}
+
+// Everything before the accumulators, shared by the symbolic phase and the
+// single pass: a new plan over `workspace`, input validation, row
+// compaction, Op_j and bins (Sections 3.1-3.3) and, with `scatter`, the
+// per-bin column lists.  On success *out holds the plan; on error it is
+// deleted.
+static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B, const spg_config &c,
+                          void *workspace, size_t ws_bytes, int64_t *C_colptr, cudaStream_t s, bool scatter,
+                          spg_plan **out) {
+    *out = nullptr;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return SPG_ERR_WORKSPACE;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SPG_ERR_CUDA;
     if (handle && handle->device != dev) return SPG_ERR_INVALID;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-
     spg_plan *P = new (std::nothrow) spg_plan();
     if (!P) return SPG_ERR_INVALID;
     P->h = handle;
@@ -347,6 +364,7 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
     P->ws_bytes = ws_bytes;
     const int64_t hmax = c.hash_cta_max;
     Ctrl *ctrl = P->ctrl();
+    spg_status st;
 
 #define CK(expr)                                                      \
     do {                                                              \
@@ -382,14 +400,15 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
     // one read: the validation outcome (a malformed colptr would make the
     // walks read out of bounds: stop here) and the count of rows with entries
     CK(P->read(&P->host, ctrl, sizeof(Ctrl), try_compact ? &mC : nullptr,
-                try_compact ? P->rmark() + (P->mA - 1) : nullptr, try_compact ? sizeof(int64_t) : 0, s));
+               try_compact ? P->rmark() + (P->mA - 1) : nullptr, try_compact ? sizeof(int64_t) : 0, s));
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     P->compact = try_compact && mC > 0 && mC * 10 <= P->mA * 9;
     P->mC = P->compact ? mC : P->mA;
     P->t_eff = effective_t(c, P->mC);
     if (P->nB > 0) {
         const int g = (int)std::min<int64_t>(ceil_div(P->nB, 8), 16 * (int64_t)P->dev.sms);
-        k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->op(), C_colptr, ctrl);
+        k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->mC, P->op(),
+                                      C_colptr, ctrl);
         CK(cudaGetLastError());
     } else {
         CK(cudaMemsetAsync(C_colptr, 0, sizeof(int64_t), s));
@@ -399,18 +418,49 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
     // the walks index a column's products with 32-bit offsets
     for (int b = 0; b < NBINS; ++b)
         if (P->host.maxop[b] >= (1ULL << 31)) { delete P; return SPG_ERR_UNSUPPORTED; }
+    P->capsum = (int64_t)P->host.capsum;
     P->off.v[0] = 0;
     for (int b = 0; b < NBINS; ++b) {
         // empty columns are not listed
         const int64_t n = b == BIN_EMPTY ? 0 : (int64_t)P->host.hist[b];
         P->off.v[b + 1] = P->off.v[b] + n;
     }
-    if (P->nB > 0) {
+    if (scatter && P->nB > 0) {
         k_bin_scatter<<<(unsigned)ceil_div(P->nB, 256), 256, 0, s>>>(P->op(), P->nB, P->t_eff, hmax, P->off,
                                                                     P->cols(), ctrl);
         CK(cudaGetLastError());
     }
     CK(cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s));
+#undef CK
+    if (c.small_accumulator == SPG_ACC_ESC)
+        for (int b = BIN_WARP0; b < BIN_CTA0; ++b) P->esc[b] = esc_shape(b, P->mC, P->esc_shape_of[b]);
+    // validation, row compaction (mark, 3 scan kernels, map, remap), the two
+    // control reads, Op counting + scatter
+    P->sym_launches = (c.validate ? 2 : 0) + (try_compact ? 6 : 0) + 2 + (P->nB > 0 ? 1 + (scatter ? 1 : 0) : 0);
+    *out = P;
+    return SPG_OK;
+}
+
+spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *B, const spg_config *cfg,
+                           void *workspace, size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC, spg_plan **plan_out,
+                           spg_stream stream) {
+    if (plan_out) *plan_out = nullptr;
+    if (!C_colptr || !nnzC || !plan_out) return SPG_ERR_INVALID;
+    spg_status st = check_pair(A, B, false);
+    if (st != SPG_OK) return st;
+    spg_config c = normalized(cfg);
+    if ((st = check_config(c)) != SPG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    spg_plan *P = nullptr;
+    if ((st = prepare(handle, A, B, c, workspace, ws_bytes, C_colptr, s, true, &P)) != SPG_OK) return st;
+    Ctrl *ctrl = P->ctrl();
+
+#define CK(expr)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (expr);                                      \
+        if (e_ != cudaSuccess) { delete P; return SPG_ERR_CUDA; }     \
+    } while (0)
+
     Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, nullptr, B->colptr, B->rowidx, nullptr};
     // as in the numeric phase: beside a dense bin, the lane-group bins (shared
     // memory only) run on the side streams, launched after the dense kernel
@@ -421,8 +471,6 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
         if (!P->side_streams()) { delete P; return SPG_ERR_CUDA; }
         CK(cudaEventRecord(P->ss().fork, s));
     }
-    if (c.small_accumulator == SPG_ACC_ESC)
-        for (int b = BIN_WARP0; b < BIN_CTA0; ++b) P->esc[b] = esc_shape(b, P->mC, P->esc_shape_of[b]);
     auto sym_bin = [&](int b, cudaStream_t sb) {
         if (P->esc[b])
             return launch_esc_bin(P->task(b), o, C_colptr, C_colptr, nullptr, nullptr, false, P->dtype,
@@ -466,9 +514,8 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
                                          P->L.scratch_ctas);
     }
     P->num_geo_ready = true;
-    // validation, row compaction (mark, 3 scan kernels, map, remap), the
-    // three control reads, Op counting + scatter + 3 scan kernels, the bins
-    P->sym_launches = (c.validate ? 2 : 0) + (try_compact ? 6 : 0) + 3 + (P->nB > 0 ? 5 : 0) + P->nonempty_bins();
+    // the preparation, 3 scan kernels, the control read, the bins
+    P->sym_launches += 4 + P->nonempty_bins();
     *nnzC = P->nnzC;
     *plan_out = P;
     return SPG_OK;
@@ -484,36 +531,27 @@ static spg_status check_plan_operands(const spg_plan *P, const spg_csc *A, const
     return SPG_OK;
 }
 
-spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const int64_t *C_colptr,
-                          int32_t *C_rowidx, void *C_values, spg_stream stream) {
-    spg_status st = check_plan_operands(P, A, B);
-    if (st != SPG_OK) return st;
-    if (!C_colptr || (P->nnzC > 0 && (!C_rowidx || !C_values))) return SPG_ERR_INVALID;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    Ctrl *ctrl = P->ctrl();
-    if (cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s) != cudaSuccess) return SPG_ERR_CUDA;
-    if (P->compact && P->nnzA > 0) {
-        // A's rows renumbered again from the A given here: an entry in a row
-        // that held none at planning time is reported, not walked
-        const int ga = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A->nnz, 256), 8 * P->dev.sms));
-        k_row_remap<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->rmap(), P->mA, P->arow(), ctrl);
-        if (cudaGetLastError() != cudaSuccess) return SPG_ERR_CUDA;
-    }
-    Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, A->values, B->colptr, B->rowidx, B->values,
-               P->compact ? P->rinv() : nullptr};
+// The accumulators of every bin on `s` (side streams forked and joined as
+// the plan says): C's rows and values at base[j] + rank, the counts checked
+// against base (two-pass) or written to cnt_out[j + 1] (single pass).
+static spg_status run_numeric(spg_plan *P, const Operands &o, const int64_t *base, int64_t *cnt_out,
+                              int32_t *rows, void *vals, cudaStream_t s) {
     auto on_side = [&](int b) { return P->side_rule(b); };
     const bool fork = P->numeric_fork();
     if (fork && !P->side_streams()) return SPG_ERR_CUDA;
     auto launch = [&](int b, cudaStream_t sb) -> spg_status {
         if (P->timing && cudaEventRecord(P->ev0[b], sb) != cudaSuccess) return SPG_ERR_CUDA;
-        cudaError_t e = P->esc[b] ? launch_esc_bin(P->task(b), o, C_colptr, nullptr, C_rowidx, C_values, true,
-                                                   P->dtype, P->esc_shape_of[b], P->dev.sms, sb)
-                                  : launch_numeric_bin(P->task(b), o, C_colptr, C_rowidx, C_values, P->dtype,
-                                                       P->num_geo[b], sb);
+        BinTask t = P->task(b);
+        t.cnt_out = cnt_out;
+        if (cnt_out) t.cache_cols = 0;  // no symbolic phase kept flags
+        cudaError_t e = P->esc[b] ? launch_esc_bin(t, o, base, cnt_out, rows, vals, true, P->dtype,
+                                                   P->esc_shape_of[b], P->dev.sms, sb)
+                                  : launch_numeric_bin(t, o, base, rows, vals, P->dtype, P->num_geo[b], sb);
         if (e != cudaSuccess) return SPG_ERR_CUDA;
         if (P->timing && cudaEventRecord(P->ev1[b], sb) != cudaSuccess) return SPG_ERR_CUDA;
         return SPG_OK;
     };
+    spg_status st;
     if (fork) {
         if (cudaEventRecord(P->ss().fork, s) != cudaSuccess) return SPG_ERR_CUDA;
         // from here on the side streams are joined back to `stream` whatever
@@ -541,6 +579,112 @@ spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const
     }
     P->timed = P->timing;
     return SPG_OK;
+}
+
+spg_status spgemm_numeric(spg_plan *P, const spg_csc *A, const spg_csc *B, const int64_t *C_colptr,
+                          int32_t *C_rowidx, void *C_values, spg_stream stream) {
+    spg_status st = check_plan_operands(P, A, B);
+    if (st != SPG_OK) return st;
+    if (!C_colptr || (P->nnzC > 0 && (!C_rowidx || !C_values))) return SPG_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Ctrl *ctrl = P->ctrl();
+    if (cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s) != cudaSuccess) return SPG_ERR_CUDA;
+    if (P->compact && P->nnzA > 0) {
+        // A's rows renumbered again from the A given here: an entry in a row
+        // that held none at planning time is reported, not walked
+        const int ga = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A->nnz, 256), 8 * P->dev.sms));
+        k_row_remap<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->rmap(), P->mA, P->arow(), ctrl);
+        if (cudaGetLastError() != cudaSuccess) return SPG_ERR_CUDA;
+    }
+    Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, A->values, B->colptr, B->rowidx, B->values,
+               P->compact ? P->rinv() : nullptr};
+    return run_numeric(P, o, C_colptr, nullptr, C_rowidx, C_values, s);
+}
+
+spg_status spgemm_single_pass_size(spg_handle *handle, const spg_csc *A, const spg_csc *B, const spg_config *cfg,
+                                   void *workspace, size_t ws_bytes, int64_t *C_colptr, size_t *bytes,
+                                   spg_stream stream) {
+    if (!bytes || !C_colptr) return SPG_ERR_INVALID;
+    spg_status st = check_pair(A, B, false);
+    if (st != SPG_OK) return st;
+    spg_config c = normalized(cfg);
+    if ((st = check_config(c)) != SPG_OK) return st;
+    c.dense_cache_bytes = 0;  // nothing is kept between phases
+    spg_plan *P = nullptr;
+    if ((st = prepare(handle, A, B, c, workspace, ws_bytes, C_colptr, reinterpret_cast<cudaStream_t>(stream), false,
+                      &P)) != SPG_OK)
+        return st;
+    slot_layout(P);
+    *bytes = P->slots_total;
+    delete P;
+    return SPG_OK;
+}
+
+spg_status spgemm_single_pass(spg_handle *handle, const spg_csc *A, const spg_csc *B, const spg_config *cfg,
+                              void *workspace, size_t ws_bytes, int64_t *C_colptr, int64_t *nnzC,
+                              spg_plan **plan_out, spg_stream stream) {
+    if (plan_out) *plan_out = nullptr;
+    if (!C_colptr || !nnzC || !plan_out) return SPG_ERR_INVALID;
+    spg_status st = check_pair(A, B, true);
+    if (st != SPG_OK) return st;
+    spg_config c = normalized(cfg);
+    if ((st = check_config(c)) != SPG_OK) return st;
+    c.dense_cache_bytes = 0;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    spg_plan *P = nullptr;
+    if ((st = prepare(handle, A, B, c, workspace, ws_bytes, C_colptr, s, true, &P)) != SPG_OK) return st;
+    slot_layout(P);
+    if (ws_bytes < P->slots_total) { delete P; return SPG_ERR_WORKSPACE; }
+    P->single = true;
+    Ctrl *ctrl = P->ctrl();
+    int64_t *soff = reinterpret_cast<int64_t *>(P->ws + P->soff_at);
+
+#define CK(expr)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (expr);                                      \
+        if (e_ != cudaSuccess) { delete P; return SPG_ERR_CUDA; }     \
+    } while (0)
+
+    // slot offsets: an exclusive scan of min(Op_j, rows)
+    CK(cudaMemsetAsync(soff, 0, sizeof(int64_t), s));
+    if (P->nB > 0) {
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(P->nB, 256), 16 * (int64_t)P->dev.sms));
+        k_slot_caps<<<g, 256, 0, s>>>(P->op(), P->nB, P->mC, soff + 1);
+        CK(cudaGetLastError());
+        CK(launch_inclusive_scan(soff + 1, P->nB, P->tiles(), s));
+    }
+    // the tables and shared-memory shapes follow the slot sizes (no nnz(C_j) yet)
+    for (int b = 1; b < NBINS; ++b) {
+        if (!P->host.hist[b]) continue;
+        const int64_t bound = std::min<int64_t>((int64_t)P->host.maxop[b], P->mC);
+        P->num_geo[b] = numeric_geometry(b, (int64_t)P->host.hist[b], P->mC, c.cta_threads, P->dev.sms,
+                                         P->dev.smem_optin, bound, P->dtype, c.table_shrink, P->L.scratch_ctas);
+    }
+    P->num_geo_ready = true;
+    Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, A->values, B->colptr, B->rowidx, B->values,
+               P->compact ? P->rinv() : nullptr};
+    st = run_numeric(P, o, soff, C_colptr, reinterpret_cast<int32_t *>(P->ws + P->srow_at), P->ws + P->sval_at, s);
+    if (st != SPG_OK) { delete P; return st; }
+    CK(launch_inclusive_scan(C_colptr + 1, P->nB, P->tiles(), s));
+    CK(P->read(&P->nnzC, C_colptr + P->nB, sizeof(int64_t), &P->host, ctrl, sizeof(Ctrl), s));
+#undef CK
+    if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
+    // the preparation, slot caps and 3 scan kernels, the bins, 3 scan
+    // kernels and the control read
+    P->sym_launches += (P->nB > 0 ? 4 : 0) + P->nonempty_bins() + 4;
+    *nnzC = P->nnzC;
+    *plan_out = P;
+    return SPG_OK;
+}
+
+spg_status spgemm_single_pass_copy(spg_plan *P, const int64_t *C_colptr, int32_t *C_rowidx, void *C_values,
+                                   spg_stream stream) {
+    if (!P || !P->single || !C_colptr || (P->nnzC > 0 && (!C_rowidx || !C_values))) return SPG_ERR_INVALID;
+    const int w = P->dtype == SPG_F64 ? 8 : 4;
+    return cuda_status(launch_slot_copy(P->nB, C_colptr, reinterpret_cast<const int64_t *>(P->ws + P->soff_at),
+                                        reinterpret_cast<const int32_t *>(P->ws + P->srow_at),
+                                        P->ws + P->sval_at, C_rowidx, C_values, w, P->dev.sms,
+                                        reinterpret_cast<cudaStream_t>(stream)));
 }
 
 spg_status spgemm_backward(spg_plan *P, const spg_csc *A, const spg_csc *B, const int64_t *C_colptr,

@@ -137,11 +137,12 @@ __device__ __forceinline__ int64_t sym_dense_column(const TOps<float> &o, int32_
 // ================================================================= numeric
 // Column j by a group: hash accumulation (Section 3.2) in a table of H <= 2 G R
 // slots, compaction, register bitonic sort, write at c0.  Returns false if
-// the table overflowed or the count differs from nn.
+// the count differs from nn (with cnt_out: exceeds nn, the slot size; the
+// count is then written to cnt_out[j + 1]).
 template <int G, int R, typename VT>
 __device__ __forceinline__ bool num_group_column(unsigned mask, const TOps<VT> &o, int32_t j, int64_t c0,
                                                  int64_t nn, int32_t *keys, VT *vals, uint32_t H, int32_t *Crow,
-                                                 VT *Cval, bool &ovf) {
+                                                 VT *Cval, bool &ovf, int64_t *cnt_out = nullptr) {
     const int gl = threadIdx.x & (G - 1);
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) {
@@ -196,7 +197,12 @@ __device__ __forceinline__ bool num_group_column(unsigned mask, const TOps<VT> &
         }
     }
     group_bitonic_sort<G, R, VT>(mask, key, val);
-    if (nn != n || n > G * R) return false;
+    if (cnt_out) {
+        if (n > nn || n > G * R) return false;
+        if (gl == 0) cnt_out[j + 1] = n;
+    } else if (nn != n || n > G * R) {
+        return false;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int e = r * G + gl;
@@ -216,7 +222,8 @@ template <typename VT>
 __device__ __forceinline__ bool num_cta_column(const TOps<VT> &o, int32_t j, int64_t c0, int64_t nn,
                                                int32_t *keys, VT *vals, int32_t *wlist, uint32_t H, uint32_t *L0,
                                                uint32_t *L1, int64_t W, const WalkSmem<VT> &w, unsigned *s_occ,
-                                               int64_t *s_warp, int32_t *Crow, VT *Cval, bool &ovf) {
+                                               int64_t *s_warp, int32_t *Crow, VT *Cval, bool &ovf,
+                                               int64_t *cnt_out = nullptr) {
     for (uint32_t s = threadIdx.x; s < H; s += blockDim.x) {
         keys[s] = kEmptyKey;
         vals[s] = VT(0);
@@ -242,7 +249,10 @@ __device__ __forceinline__ bool num_cta_column(const TOps<VT> &o, int32_t j, int
     for (int d = 16; d > 0; d >>= 1) occ += __shfl_xor_sync(0xffffffffu, occ, d);
     if ((threadIdx.x & 31) == 0 && occ) atomicAdd(s_occ, occ);
     __syncthreads();
-    const bool ok = (int64_t)*s_occ == nn;
+    const int64_t found = (int64_t)*s_occ;
+    // single pass: nn is the slot size, the count is written
+    const bool ok = cnt_out ? found <= nn : found == nn;
+    if (cnt_out && ok && threadIdx.x == 0) cnt_out[j + 1] = found;
     const int64_t K = cta_list_words(L1, (W + 31) / 32, wlist, s_warp);
     cta_expand_words(L0, wlist, K, s_warp, [&](int32_t row, int64_t rank) {
         const int32_t slot = hash_find(keys, H, row);
@@ -267,7 +277,8 @@ template <typename VT, typename AP>
 __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, int64_t c0, int64_t nn, uint2 *bm,
                                                  int64_t W, const uint32_t *keep, VT *s_acc, int64_t cap,
                                                  const WalkSmem<VT> &w, int64_t *s_warp, unsigned *s_next,
-                                                 int32_t *Crow, VT *Cval, AP &&after_prefix) {
+                                                 int32_t *Crow, VT *Cval, AP &&after_prefix,
+                                                 int64_t *cnt_out = nullptr) {
     // the previous user of *s_next finished before the caller's last barrier
     if (threadIdx.x == 0) *s_next = (blockDim.x >> 5) * kVisitGroup;
     // flags kept from the symbolic phase are read straight into the prefix
@@ -277,12 +288,17 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                             [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
     const int64_t total = cta_bitmap_prefix(bm, W, keep, s_warp);
     after_prefix();
-    if (total != nn) {
+    // single pass: nn is the slot size, the count is written
+    if (cnt_out ? total > nn : total != nn) {
         // the pattern changed since the symbolic phase: the caller reports
         // it and the column is left unwritten
         for (int i = threadIdx.x; i < (int)W; i += blockDim.x) bm[i].x = 0u;
         __syncthreads();
         return false;
+    }
+    if (cnt_out) {
+        if (threadIdx.x == 0) cnt_out[j + 1] = total;
+        nn = total;
     }
     // nn <= m < 2^31: positions are 32-bit
     const int32_t n32 = (int32_t)nn;

@@ -32,18 +32,32 @@
 
 namespace spg {
 
-template <typename VT>
+// Shared memory of one warp.  The sort moves (key, index) pairs; the values
+// stay where the expansion put them and are read through the index.
+template <bool VALS, typename VT>
 struct EscWarp {
     uint32_t key[2][kEscTile];
-    VT val[2][kEscTile];
     uint32_t cnt[1 << kEscRadixBits];
     int32_t hstart[32];
 };
-
 template <typename VT>
+struct EscWarp<true, VT> {
+    uint32_t key[2][kEscTile];
+    VT val[kEscTile];
+    uint32_t cnt[1 << kEscRadixBits];
+    int32_t hstart[32];
+    uint8_t idx[2][kEscTile];
+};
+
+template <bool VALS, typename VT>
 __host__ __device__ constexpr size_t esc_warp_bytes() {
-    return (sizeof(EscWarp<VT>) + 15) & ~size_t(15);
+    return (sizeof(EscWarp<VALS, VT>) + 15) & ~size_t(15);
 }
+
+// CTAs per SM the kernels are built for (registers): the value-carrying
+// form holds more shared memory per warp.
+template <bool VALS>
+constexpr int esc_min_blocks() { return VALS ? 5 : 6; }
 
 // Lane holding the owner of position q among 32 lanes with non-decreasing
 // exclusive offsets `excl` (the last lane whose offset is <= q).
@@ -58,12 +72,12 @@ __device__ __forceinline__ int esc_owner(int excl, int q) {
 }
 
 template <bool VALS, typename VT>
-__global__ void __launch_bounds__(kEscWarps * 32) k_esc(BinTask t, Operands o, const int64_t *base,
-                                                        int64_t *cnt_out, int32_t *Crow, VT *Cval, EscShape e) {
+__global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
+    k_esc(BinTask t, Operands o, const int64_t *base, int64_t *cnt_out, int32_t *Crow, VT *Cval, EscShape e) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_max, s_sum;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    EscWarp<VT> &S = *reinterpret_cast<EscWarp<VT> *>(smem + (size_t)warp * esc_warp_bytes<VT>());
+    EscWarp<VALS, VT> &S = *reinterpret_cast<EscWarp<VALS, VT> *>(smem + (size_t)warp * esc_warp_bytes<VALS, VT>());
     if (threadIdx.x == 0) s_max = s_sum = 0;
     __syncthreads();
     const TOps<VT> ops = typed<VT>(o);
@@ -72,21 +86,34 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_esc(BinTask t, Operands o, c
     const uint32_t rowmask = e.rb >= 32 ? 0xffffffffu : ((1u << e.rb) - 1u);
     const int64_t ntiles = ceil_div(t.count, (int64_t)e.ct);
     unsigned long long my_max = 0, my_sum = 0;
-    for (int64_t tile = (int64_t)blockIdx.x * kEscWarps + warp; tile < ntiles;
-         tile += (int64_t)gridDim.x * kEscWarps) {
+    const int64_t tstride = (int64_t)gridDim.x * kEscWarps;
+    int64_t tile = (int64_t)blockIdx.x * kEscWarps + warp;
+    // the next tile's column ids and B column pointers are loaded while the
+    // current tile is sorted
+    int32_t nj = 0;
+    int64_t np0 = 0, np1 = 0;
+    auto fetch = [&](int64_t tl) {
+        const int64_t f = tl * e.ct;
+        if (tl < ntiles && lane < e.ct && f + lane < t.count) {
+            nj = t.cols[f + lane];
+            np0 = ops.Bcp[nj];
+            np1 = ops.Bcp[nj + 1];
+        }
+    };
+    fetch(tile);
+    for (; tile < ntiles; tile += tstride) {
         const int64_t first = tile * e.ct;
         const int nc = (int)(t.count - first < e.ct ? t.count - first : e.ct);
         // ---- the tile's columns, one per lane: B entries and their offsets
-        int32_t j = 0;
-        int64_t p0 = 0, cb = 0, ccap = 0;
-        int nb = 0;
+        const int32_t j = lane < nc ? nj : 0;
+        const int64_t p0 = lane < nc ? np0 : 0;
+        const int nb = lane < nc ? (int)(np1 - np0) : 0;
+        int64_t cb = 0, ccap = 0;
         if (lane < nc) {
-            j = t.cols[first + lane];
-            p0 = ops.Bcp[j];
-            nb = (int)(ops.Bcp[j + 1] - p0);
             cb = base[j];
             ccap = base[j + 1] - cb;  // entries the column's place holds
         }
+        fetch(tile + tstride);
         int eincl = nb;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -137,7 +164,10 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_esc(BinTask t, Operands o, c
                     const int64_t qa = a0s + (q - exs);
                     const int32_t row = ld_keep(ops.Arow + qa, pol);
                     S.key[0][n + q] = ((uint32_t)cs << e.rb) | ((uint32_t)row & rowmask);
-                    if (VALS) S.val[0][n + q] = ld_keep(ops.Aval + qa, pol) * bs;
+                    if constexpr (VALS) {
+                        S.val[n + q] = ld_keep(ops.Aval + qa, pol) * bs;
+                        S.idx[0][n + q] = (uint8_t)(n + q);
+                    }
                 }
             }
             n += total;
@@ -183,8 +213,8 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_esc(BinTask t, Operands o, c
                 const int i = i0 + lane;
                 const bool valid = i < n;
                 const uint32_t k = valid ? S.key[cur][i] : 0u;
-                VT v = VT(0);
-                if (VALS && valid) v = S.val[cur][i];
+                uint8_t ix = 0;
+                if constexpr (VALS) ix = valid ? S.idx[cur][i] : (uint8_t)0;
                 // lanes past n get digits of their own, so they never share a
                 // group with a key
                 const uint32_t dg = valid ? ((k >> sh) & ((1u << kEscRadixBits) - 1u)) : (0x10000u + lane);
@@ -198,7 +228,7 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_esc(BinTask t, Operands o, c
                 at = __shfl_sync(0xffffffffu, at, leader) + (uint32_t)__popc(same & lt);
                 if (valid) {
                     S.key[cur ^ 1][at] = k;
-                    if (VALS) S.val[cur ^ 1][at] = v;
+                    if constexpr (VALS) S.idx[cur ^ 1][at] = ix;
                 }
                 __syncwarp();
             }
@@ -220,12 +250,12 @@ __global__ void __launch_bounds__(kEscWarps * 32) k_esc(BinTask t, Operands o, c
             const int c = (int)(k >> e.rb);
             if (head && (i == 0 || (int)(kp >> e.rb) != c)) S.hstart[c] = hr;
             __syncwarp();
-            if (VALS) {
+            if constexpr (VALS) {
                 const int64_t cbase = __shfl_sync(0xffffffffu, cb, c & 31);
                 const int64_t cc = __shfl_sync(0xffffffffu, ccap, c & 31);
                 if (head) {
-                    VT sum = S.val[cur][i];
-                    for (int m2 = i + 1; m2 < n && S.key[cur][m2] == k; ++m2) sum += S.val[cur][m2];
+                    VT sum = S.val[S.idx[cur][i]];
+                    for (int m2 = i + 1; m2 < n && S.key[cur][m2] == k; ++m2) sum += S.val[S.idx[cur][m2]];
                     const int64_t r = hr - S.hstart[c];
                     // a column with more runs than its place holds is reported
                     // below and not written past its place
@@ -307,7 +337,7 @@ static cudaError_t launch_esc_t(const BinTask &t, const Operands &o, const int64
                                 int32_t *Crow, VT *Cval, const EscShape &e, int sms, cudaStream_t s) {
     if (t.count <= 0) return cudaSuccess;
     auto k = k_esc<VALS, VT>;
-    const size_t smem = (size_t)kEscWarps * esc_warp_bytes<VT>();
+    const size_t smem = (size_t)kEscWarps * esc_warp_bytes<VALS, VT>();
     esc_allow_smem(k, smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kEscWarps * 32, smem) != cudaSuccess || occ < 1)

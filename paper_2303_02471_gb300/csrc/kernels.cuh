@@ -756,7 +756,10 @@ int64_t scan_tile_count(int64_t n);
 __global__ void k_validate(const int64_t *cp, const int32_t *row, int64_t nrows, int64_t ncols,
                            int64_t nnz, int which, Ctrl *ctrl);
 __global__ void k_count_bin(const int64_t *Bcp, const int32_t *Brow, const int64_t *Acp, int64_t nB,
-                            int64_t t, int64_t hmax, int64_t *op, int64_t *Ccp, Ctrl *ctrl);
+                            int64_t t, int64_t hmax, int64_t mrows, int64_t *op, int64_t *Ccp, Ctrl *ctrl);
+__global__ void k_slot_caps(const int64_t *op, int64_t nB, int64_t mrows, int64_t *caps);
+cudaError_t launch_slot_copy(int64_t nB, const int64_t *Ccp, const int64_t *soff, const int32_t *srow,
+                             const void *sval, int32_t *Crow, void *Cval, int w, int sms, cudaStream_t s);
 __global__ void k_bin_scatter(const int64_t *op, int64_t nB, int64_t t, int64_t hmax,
                               BinOffsets off, int32_t *bin_cols, Ctrl *ctrl);
 
@@ -786,6 +789,11 @@ struct BinTask {
     uint32_t *flag_cache;    // dense bin: W words per listed column, for the
     int64_t cache_cols;      //   first cache_cols columns of the bin's list
     long long wait_cycles;   // dense bin: limit of a wait for kept flags (<= 0: give up at once)
+    // single pass: the numeric kernels write each column at its slot (the
+    // column pointers passed in are the slot offsets, slot capacity
+    // min(Op_j, m)) and its entry count to cnt_out[j + 1]; null otherwise
+    // (the count is checked against the symbolic phase's)
+    int64_t *cnt_out = nullptr;
 };
 
 struct Operands {

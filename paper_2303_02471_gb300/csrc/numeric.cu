@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kGroupThreads, 4) k_num_group(BinTask t, Opera
     const int64_t c0 = Ccp[j];
     bool ovf = false;
     const bool ok = num_group_column<G, R, VT>(group_mask(G), typed<VT>(o), j, c0, Ccp[j + 1] - c0, keys, vals,
-                                               Hj, Crow, Cval, ovf);
+                                               Hj, Crow, Cval, ovf, t.cnt_out);
     if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
     if (!ok) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
 }
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_cta(BinTask t, Operands o, cons
         if (H < 1) H = 1;
         bool ovf = false;
         const bool ok = num_cta_column<VT>(ops, j, c0, nn, keys, vals, wlist, H, L0, L1, t.W, w, &s_occ, s_warp,
-                                           Crow, Cval, ovf);
+                                           Crow, Cval, ovf, t.cnt_out);
         if (ovf) set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
     }
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_dense(BinTask t, Operands o, co
             }
         };
         const bool ok = num_dense_column<VT>(ops, j, c0, nn, bm, t.W, keep, s_acc, cap, w, s_warp, &s_chunk, Crow,
-                                             Cval, next);
+                                             Cval, next, t.cnt_out);
         if (!ok && threadIdx.x == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
     }
     // a copy is in flight only after a time-out: wait for it (bounded, at

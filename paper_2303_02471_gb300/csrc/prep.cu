@@ -28,26 +28,26 @@ __global__ void k_validate(const int64_t *__restrict__ cp, const int32_t *__rest
 // Op_j = sum over stored B_kj of Z^A_k (Section 3.1), its bin, the bin
 // histogram and the total product count.  Empty columns get nnz 0 here.
 __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__restrict__ Brow,
-                            const int64_t *__restrict__ Acp, int64_t nB, int64_t t, int64_t hmax,
+                            const int64_t *__restrict__ Acp, int64_t nB, int64_t t, int64_t hmax, int64_t mrows,
                             int64_t *__restrict__ op, int64_t *__restrict__ Ccp, Ctrl *ctrl) {
     __shared__ unsigned long long s_hist[NBINS];
     __shared__ unsigned long long s_max[NBINS];
     __shared__ unsigned long long s_binprod[NBINS];
     __shared__ unsigned long long s_binb[NBINS];
-    __shared__ unsigned long long s_prod;
+    __shared__ unsigned long long s_prod, s_cap;
     if (threadIdx.x < NBINS) {
         s_hist[threadIdx.x] = 0;
         s_max[threadIdx.x] = 0;
         s_binprod[threadIdx.x] = 0;
         s_binb[threadIdx.x] = 0;
     }
-    if (threadIdx.x == 0) s_prod = 0;
+    if (threadIdx.x == 0) s_prod = s_cap = 0;
     __syncthreads();
     // one warp per column: its B entries are read coalesced and the Z^A_k
     // loads are independent, so long columns take no serial chain
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long mine = 0;
+    unsigned long long mine = 0, cap = 0;
     for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nB; j += nwarps) {
         const int64_t p0 = Bcp[j], p1 = Bcp[j + 1];
         int64_t s = 0;
@@ -60,6 +60,7 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
         if (lane == 0) {
             op[j] = s;
             mine += (unsigned long long)s;
+            cap += (unsigned long long)(s < mrows ? s : mrows);
             const int b = bin_of(s, t, hmax);
             atomicAdd(&s_hist[b], 1ULL);
             atomicMax(&s_max[b], (unsigned long long)s);
@@ -69,8 +70,14 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) Ccp[0] = 0;
-    for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, d);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&s_prod, mine);
+    for (int d = 16; d > 0; d >>= 1) {
+        mine += __shfl_xor_sync(0xffffffffu, mine, d);
+        cap += __shfl_xor_sync(0xffffffffu, cap, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_prod, mine);
+        atomicAdd(&s_cap, cap);
+    }
     __syncthreads();
     if (threadIdx.x < NBINS && s_hist[threadIdx.x]) {
         atomicAdd(&ctrl->hist[threadIdx.x], s_hist[threadIdx.x]);
@@ -78,7 +85,51 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
         atomicAdd(&ctrl->binprod[threadIdx.x], s_binprod[threadIdx.x]);
         atomicAdd(&ctrl->binnnzb[threadIdx.x], s_binb[threadIdx.x]);
     }
-    if (threadIdx.x == 0) atomicAdd(&ctrl->products, s_prod);
+    if (threadIdx.x == 0) {
+        atomicAdd(&ctrl->products, s_prod);
+        atomicAdd(&ctrl->capsum, s_cap);
+    }
+}
+
+// Single pass: slot capacity min(Op_j, rows) of every column, written to
+// caps[j] (caps = the slot offsets + 1, scanned afterwards).
+__global__ void k_slot_caps(const int64_t *__restrict__ op, int64_t nB, int64_t mrows, int64_t *__restrict__ caps) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nB; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = op[j];
+        caps[j] = v < mrows ? v : mrows;
+    }
+}
+
+// Single pass: every column's entries from its slot (soff[j]) to its place
+// in C (Ccp[j]); a warp per column, W-byte values.
+template <typename W>
+__global__ void k_slot_copy(int64_t nB, const int64_t *__restrict__ Ccp, const int64_t *__restrict__ soff,
+                            const int32_t *__restrict__ srow, const W *__restrict__ sval, int32_t *__restrict__ Crow,
+                            W *__restrict__ Cval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nB; j += nw) {
+        const int64_t c0 = Ccp[j], s0 = soff[j], cap = soff[j + 1] - s0;
+        int64_t n = Ccp[j + 1] - c0;
+        if (n > cap) n = cap;  // a count never exceeds its slot; reads stay inside the slots
+        for (int64_t i = lane; i < n; i += 32) {
+            Crow[c0 + i] = srow[s0 + i];
+            Cval[c0 + i] = sval[s0 + i];
+        }
+    }
+}
+
+cudaError_t launch_slot_copy(int64_t nB, const int64_t *Ccp, const int64_t *soff, const int32_t *srow,
+                             const void *sval, int32_t *Crow, void *Cval, int w, int sms, cudaStream_t s) {
+    if (nB <= 0) return cudaSuccess;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nB, 8), 16 * (int64_t)sms));
+    if (w == 8)
+        k_slot_copy<uint64_t><<<g, 256, 0, s>>>(nB, Ccp, soff, srow, static_cast<const uint64_t *>(sval), Crow,
+                                                  static_cast<uint64_t *>(Cval));
+    else
+        k_slot_copy<uint32_t><<<g, 256, 0, s>>>(nB, Ccp, soff, srow, static_cast<const uint32_t *>(sval), Crow,
+                                                  static_cast<uint32_t *>(Cval));
+    return cudaGetLastError();
 }
 
 // Column ids into per-bin lists at off[bin] (each block reserves its slots

@@ -63,7 +63,8 @@ struct Ctrl {
     unsigned long long binnnz[NBINS];   // sum of nnz(C_j) per bin
     unsigned long long binnnzb[NBINS];  // sum of nnz(B_j) per bin
     unsigned long long products;        // sum_j Op_j
-    unsigned long long pad[3];
+    unsigned long long capsum;          // sum_j min(Op_j, rows): the single pass's slots
+    unsigned long long pad[2];
 };
 
 // Code for a column whose numeric count disagrees with the symbolic one

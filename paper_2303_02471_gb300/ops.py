@@ -301,6 +301,47 @@ def spgemm(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None):
     return C, plan
 
 
+def single_pass_workspace_size(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None,
+                               lib_handle: Optional[Handle] = None) -> int:
+    """Workspace bytes of spgemm_single_pass for these patterns (synchronises)."""
+    config = replace(config or Config(), dense_cache_bytes=0)
+    hd = lib_handle if lib_handle is not None else handle(A.device)
+    cA, cB = _csc(A), _csc(B, A.dtype)
+    base = workspace_size(A, B, config)
+    ws = torch.empty(max(base, 256), dtype=torch.uint8, device=A.device)
+    colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=A.device)
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().spgemm_single_pass_size(hd.ptr, ctypes.byref(cA), ctypes.byref(cB),
+                                            ctypes.byref(config.native()), _ptr(ws), ws.numel(), _ptr(colptr),
+                                            ctypes.byref(nbytes), _stream()), "spgemm_single_pass_size")
+    return nbytes.value
+
+
+def spgemm_single_pass(A: CscMatrix, B: CscMatrix, config: Optional[Config] = None,
+                       workspace: Optional[torch.Tensor] = None, lib_handle: Optional[Handle] = None):
+    """C = A B without a symbolic phase: every column written to a slot of
+    min(Op_j, m) entries, the counts scanned into C's column pointers, then
+    the columns copied into C.  Returns (C, plan)."""
+    config = config or Config()
+    hd = lib_handle if lib_handle is not None else handle(A.device)
+    cA, cB = _csc(A), _csc(B, A.dtype)
+    need = single_pass_workspace_size(A, B, config, hd)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
+    colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=A.device)
+    nnz = ctypes.c_int64()
+    h = ctypes.c_void_p()
+    N.check(N.lib().spgemm_single_pass(hd.ptr, ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(config.native()),
+                                       _ptr(workspace), workspace.numel(), _ptr(colptr), ctypes.byref(nnz),
+                                       ctypes.byref(h), _stream()), "spgemm_single_pass")
+    plan = Plan(h, workspace, A, B, colptr, nnz.value, config, hd)
+    rowidx = torch.empty(nnz.value, dtype=torch.int32, device=A.device)
+    values = torch.empty(nnz.value, dtype=A.dtype, device=A.device)
+    N.check(N.lib().spgemm_single_pass_copy(plan.handle, _ptr(colptr), _ptr(rowidx), _ptr(values), _stream()),
+            "spgemm_single_pass_copy")
+    return CscMatrix(A.nrows, B.ncols, colptr, rowidx, values), plan
+
+
 def spgemm_backward(plan: Plan, A: CscMatrix, B: CscMatrix, C: CscMatrix, dC: torch.Tensor,
                     need_dA: bool = True, need_dB: bool = True):
     """(dA, dB) on the stored entries of A and B for dC on pattern(C)."""

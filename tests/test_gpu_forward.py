@@ -417,3 +417,89 @@ def test_esc_sums_do_not_depend_on_timing():
     plan.check()
     assert (C2.values == v1).all()
     assert_matches_oracle(C2, A, B)
+
+
+# ----------------------------------------------------------- single pass
+def _single(A, B, dtype=None, **cfg):
+    from paper_2303_02471_gb300 import ops
+    dA, dB = upload(A, dtype), upload(B, dtype)
+    C, plan = ops.spgemm_single_pass(dA, dB, ops.Config(**cfg) if cfg else None)
+    plan.check()
+    return C, plan
+
+
+@pytest.mark.parametrize("acc", ["hash", "esc"])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("seed", range(20))
+def test_single_pass_fuzz(seed, dtype, acc):
+    A, B = synth.fuzz_pair(seed, dtype=dtype)
+    C, _ = _single(A, B, small_accumulator=acc)
+    assert_matches_oracle(C, A, B)
+
+
+@pytest.mark.parametrize("acc", ["hash", "esc"])
+@pytest.mark.parametrize("t", [0, 40, None, INF])
+def test_single_pass_rmat_every_bin(t, acc):
+    # every accumulator writing to Op_j-sized slots: lane groups or ESC, CTA
+    # tables, the global table and the dense SPA (flags set by a first walk)
+    A = synth.rmat(13, seed=2, col_cap=600)
+    C, plan = _single(A, A, t=t, hash_cta_max=1024, small_accumulator=acc)
+    assert_matches_oracle(C, A, A, nthreads=NCPU)
+
+
+@pytest.mark.parametrize("acc", ["hash", "esc"])
+def test_single_pass_workload2_random_full(acc):
+    A, B = synth.workload(2)
+    C, _ = _single(A, B, small_accumulator=acc)
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
+def test_single_pass_workload1_and_tall():
+    A, B = synth.workload(1)
+    C, _ = _single(A, B, t=12)
+    assert_matches_oracle(C, A, B)
+    assert C.nnz == 12676
+    A = _tall(1 << 20, 3000, 900, 1100, seed=21)
+    B = _tall(3000, 600, 1, 12, seed=22)
+    for t in (0, INF):
+        C, _ = _single(A, B, t=t)
+        assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
+def test_single_pass_plan_serves_numeric_and_backward():
+    import torch
+    from paper_2303_02471_gb300 import ops
+    A = synth.rmat(12, seed=9, col_cap=400)
+    dA = upload(A)
+    C1, plan = ops.spgemm_single_pass(dA, dA, ops.Config(t=64))
+    C2 = ops.spgemm_numeric(plan, dA, dA)
+    plan.check()
+    assert (C1.rowidx == C2.rowidx).all()
+    ref = oracle.spgemm(A, A)
+    assert_matches_oracle(C2, A, A, ref=ref)
+    dc = torch.ones(C1.nnz, dtype=torch.float64, device="cuda")
+    gA, gB = ops.spgemm_backward(plan, dA, dA, C1, dc)
+    plan.check()
+    rA, rB = oracle.backward(A, A, C1.to_host(), np.ones(C1.nnz))
+    Aa = A.with_values(np.abs(A.values))
+    sA, sB = oracle.backward(Aa, Aa, C1.to_host(), np.ones(C1.nnz))
+    assert np.all(np.abs(gA.cpu().numpy() - rA) <= 1e-12 * sA)
+    assert np.all(np.abs(gB.cpu().numpy() - rB) <= 1e-12 * sB)
+
+
+def test_single_pass_workspace_too_small():
+    import ctypes
+    import torch
+    from paper_2303_02471_gb300 import _native as N
+    from paper_2303_02471_gb300 import ops
+    A = upload(synth.random_z(800, 1, 6, seed=4))
+    need = ops.single_pass_workspace_size(A, A)
+    assert need > ops.workspace_size(A, A, ops.Config(dense_cache_bytes=0))
+    ws = torch.empty(need - 4096, dtype=torch.uint8, device="cuda")
+    cp = torch.empty(A.ncols + 1, dtype=torch.int64, device="cuda")
+    nnz, h = ctypes.c_int64(), ctypes.c_void_p()
+    cA = ops._csc(A)
+    rc = N.lib().spgemm_single_pass(ops.handle().ptr, ctypes.byref(cA), ctypes.byref(cA), None,
+                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(cp.data_ptr()),
+                                    ctypes.byref(nnz), ctypes.byref(h), ops._stream())
+    assert N.STATUS[rc] == "SPG_ERR_WORKSPACE" and h.value is None
