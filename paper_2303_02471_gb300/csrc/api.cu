@@ -389,13 +389,9 @@ static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B
     if (try_compact) {
         CK(cudaMemsetAsync(P->rmark(), 0, (size_t)P->mA * 8, s));
         const int ga = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A->nnz, 256), 8 * P->dev.sms));
-        const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(P->mA, 256), 8 * P->dev.sms));
         k_row_mark<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->mA, P->rmark());
         CK(cudaGetLastError());
         CK(launch_inclusive_scan(P->rmark(), P->mA, reinterpret_cast<int64_t *>(P->ws + P->L.rtiles), s));
-        k_row_map<<<gm, 256, 0, s>>>(P->rmark(), P->mA, P->rmap(), P->rinv());
-        k_row_remap<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->rmap(), P->mA, P->arow(), ctrl);
-        CK(cudaGetLastError());
     }
     // one read: the validation outcome (a malformed colptr would make the
     // walks read out of bounds: stop here) and the count of rows with entries
@@ -404,9 +400,19 @@ static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B
     if (P->host.err) { st = (spg_status)P->host.err; delete P; return st; }
     P->compact = try_compact && mC > 0 && mC * 10 <= P->mA * 9;
     P->mC = P->compact ? mC : P->mA;
+    if (P->compact) {
+        // the map to compact rows and back, and A's rows renumbered (rows
+        // out of range were rejected by the validation, or are reported here)
+        const int ga = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(A->nnz, 256), 8 * P->dev.sms));
+        const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(P->mA, 256), 8 * P->dev.sms));
+        k_row_map<<<gm, 256, 0, s>>>(P->rmark(), P->mA, P->rmap(), P->rinv());
+        k_row_remap<<<ga, 256, 0, s>>>(A->rowidx, A->nnz, P->rmap(), P->mA, P->arow(), ctrl);
+        CK(cudaGetLastError());
+    }
     P->t_eff = effective_t(c, P->mC);
     if (P->nB > 0) {
-        const int g = (int)std::min<int64_t>(ceil_div(P->nB, 8), 16 * (int64_t)P->dev.sms);
+        // a warp per 32 columns, 8 warps per CTA
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(P->nB, 256), 16 * (int64_t)P->dev.sms));
         k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->mC, P->op(),
                                       C_colptr, ctrl);
         CK(cudaGetLastError());
@@ -434,9 +440,10 @@ static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B
 #undef CK
     if (c.small_accumulator == SPG_ACC_ESC)
         for (int b = BIN_WARP0; b < BIN_CTA0; ++b) P->esc[b] = esc_shape(b, P->mC, P->esc_shape_of[b]);
-    // validation, row compaction (mark, 3 scan kernels, map, remap), the two
-    // control reads, Op counting + scatter
-    P->sym_launches = (c.validate ? 2 : 0) + (try_compact ? 6 : 0) + 2 + (P->nB > 0 ? 1 + (scatter ? 1 : 0) : 0);
+    // validation, row marks (mark, 3 scan kernels) and, when compacting,
+    // map and remap, the two control reads, Op counting + scatter
+    P->sym_launches = (c.validate ? 2 : 0) + (try_compact ? 4 : 0) + (P->compact ? 2 : 0) + 2 +
+                      (P->nB > 0 ? 1 + (scatter ? 1 : 0) : 0);
     *out = P;
     return SPG_OK;
 }

@@ -27,6 +27,13 @@ __global__ void k_validate(const int64_t *__restrict__ cp, const int32_t *__rest
 
 // Op_j = sum over stored B_kj of Z^A_k (Section 3.1), its bin, the bin
 // histogram and the total product count.  Empty columns get nnz 0 here.
+//
+// A warp takes 32 consecutive columns, one per lane, and walks their B
+// entries 32 at a time as one flattened sequence (the owner of an entry is
+// found by a search over the lanes' entry offsets), so short columns keep
+// every lane busy and long ones are split over the warp; the Z^A_k of an
+// entry's lanes are summed by a segmented warp scan.  Per-bin statistics are
+// summed over the warp before one shared atomic per bin present.
 __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__restrict__ Brow,
                             const int64_t *__restrict__ Acp, int64_t nB, int64_t t, int64_t hmax, int64_t mrows,
                             int64_t *__restrict__ op, int64_t *__restrict__ Ccp, Ctrl *ctrl) {
@@ -35,6 +42,7 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
     __shared__ unsigned long long s_binprod[NBINS];
     __shared__ unsigned long long s_binb[NBINS];
     __shared__ unsigned long long s_prod, s_cap;
+    __shared__ int64_t s_op[32 * 32];  // per warp: the Op of its 32 columns (blockDim <= 1024)
     if (threadIdx.x < NBINS) {
         s_hist[threadIdx.x] = 0;
         s_max[threadIdx.x] = 0;
@@ -43,31 +51,89 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
     }
     if (threadIdx.x == 0) s_prod = s_cap = 0;
     __syncthreads();
-    // one warp per column: its B entries are read coalesced and the Z^A_k
-    // loads are independent, so long columns take no serial chain
     const int lane = threadIdx.x & 31;
+    int64_t *wop = s_op + (threadIdx.x & ~31);
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long mine = 0, cap = 0;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nB; j += nwarps) {
-        const int64_t p0 = Bcp[j], p1 = Bcp[j + 1];
-        int64_t s = 0;
-        for (int64_t p = p0 + lane; p < p1; p += 32) {
-            const int32_t k = Brow[p];
-            s += Acp[k + 1] - Acp[k];
+    for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < nB; j0 += nwarps * 32) {
+        const int64_t j = j0 + lane;
+        const bool on = j < nB;
+        int64_t p0 = 0, nb = 0;
+        if (on) {
+            p0 = Bcp[j];
+            nb = Bcp[j + 1] - p0;
         }
+        wop[lane] = 0;
+        int64_t eincl = nb;
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-        if (lane == 0) {
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t v = __shfl_up_sync(0xffffffffu, eincl, d);
+            if (lane >= d) eincl += v;
+        }
+        const int64_t eexcl = eincl - nb;
+        const int64_t E = __shfl_sync(0xffffffffu, eincl, 31);
+        __syncwarp();
+        for (int64_t e0 = 0; e0 < E; e0 += 32) {
+            const int64_t e = e0 + lane;
+            const int64_t q = e < E ? e : E - 1;
+            int c = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int64_t ex = __shfl_sync(0xffffffffu, eexcl, c + step);
+                if (ex <= q) c += step;
+            }
+            const int64_t pc = __shfl_sync(0xffffffffu, p0, c);
+            const int64_t xc = __shfl_sync(0xffffffffu, eexcl, c);
+            int64_t z = 0;
+            if (e < E) {
+                const int32_t k = Brow[pc + (e - xc)];
+                z = Acp[k + 1] - Acp[k];
+            }
+            // owners are non-decreasing over the lanes: segmented inclusive sum
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t v = __shfl_up_sync(0xffffffffu, z, d);
+                const int oc = __shfl_up_sync(0xffffffffu, c, d);
+                if (lane >= d && oc == c) z += v;
+            }
+            const int cn = __shfl_down_sync(0xffffffffu, c, 1);
+            if (e < E && (lane == 31 || e + 1 >= E || cn != c)) wop[c] += z;
+            __syncwarp();
+        }
+        const int64_t s = wop[lane];
+        int b = -1;
+        if (on) {
             op[j] = s;
             mine += (unsigned long long)s;
             cap += (unsigned long long)(s < mrows ? s : mrows);
-            const int b = bin_of(s, t, hmax);
-            atomicAdd(&s_hist[b], 1ULL);
-            atomicMax(&s_max[b], (unsigned long long)s);
-            if (s) atomicAdd(&s_binprod[b], (unsigned long long)s);
-            if (p1 > p0) atomicAdd(&s_binb[b], (unsigned long long)(p1 - p0));
+            b = bin_of(s, t, hmax);
             if (b == BIN_EMPTY) Ccp[j + 1] = 0;
         }
+        // per-bin statistics, one group of lanes per bin present
+        unsigned pending = __ballot_sync(0xffffffffu, on);
+        while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const int bb = __shfl_sync(0xffffffffu, b, leader);
+            const unsigned m = __ballot_sync(0xffffffffu, on && b == bb);
+            unsigned long long sm = (m >> lane) & 1u ? (unsigned long long)s : 0ull;
+            unsigned long long mx = sm;
+            unsigned long long nbs = (m >> lane) & 1u ? (unsigned long long)nb : 0ull;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                sm += __shfl_xor_sync(0xffffffffu, sm, d);
+                nbs += __shfl_xor_sync(0xffffffffu, nbs, d);
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, d);
+                if (o > mx) mx = o;
+            }
+            if (lane == leader) {
+                atomicAdd(&s_hist[bb], (unsigned long long)__popc(m));
+                atomicMax(&s_max[bb], mx);
+                if (sm) atomicAdd(&s_binprod[bb], sm);
+                if (nbs) atomicAdd(&s_binb[bb], nbs);
+            }
+            pending &= ~m;
+        }
+        __syncwarp();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) Ccp[0] = 0;
     for (int d = 16; d > 0; d >>= 1) {
@@ -112,9 +178,26 @@ __global__ void k_slot_copy(int64_t nB, const int64_t *__restrict__ Ccp, const i
         const int64_t c0 = Ccp[j], s0 = soff[j], cap = soff[j + 1] - s0;
         int64_t n = Ccp[j + 1] - c0;
         if (n > cap) n = cap;  // a count never exceeds its slot; reads stay inside the slots
-        for (int64_t i = lane; i < n; i += 32) {
-            Crow[c0 + i] = srow[s0 + i];
-            Cval[c0 + i] = sval[s0 + i];
+        // four loads in flight per lane before the stores
+        for (int64_t i = lane; i < n; i += 128) {
+            int32_t r[4];
+            W v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t x = i + 32 * u;
+                if (x < n) {
+                    r[u] = srow[s0 + x];
+                    v[u] = sval[s0 + x];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t x = i + 32 * u;
+                if (x < n) {
+                    Crow[c0 + x] = r[u];
+                    Cval[c0 + x] = v[u];
+                }
+            }
         }
     }
 }
