@@ -90,7 +90,9 @@ __device__ __forceinline__ void esc_segment_sort(uint32_t (&k)[kEscTile / 32]) {
                 for (int r = 0; r < kEscTile / 32; ++r) {
                     if ((r & jr) == 0) {
                         const int e = r * 32 + lane;
-                        const bool up = (e & kk) == 0;
+                        // direction from the slot's place in its segment: every
+                        // segment ends ascending (the last stage has kk = S)
+                        const bool up = ((e & (S - 1)) & kk) == 0;
                         const uint32_t a = k[r], b = k[r | jr];
                         const bool swap = up ? a > b : a < b;
                         k[r] = swap ? b : a;
@@ -102,7 +104,7 @@ __device__ __forceinline__ void esc_segment_sort(uint32_t (&k)[kEscTile / 32]) {
                 for (int r = 0; r < kEscTile / 32; ++r) {
                     const int e = r * 32 + lane;
                     const uint32_t o = __shfl_xor_sync(0xffffffffu, k[r], j);
-                    const bool up = (e & kk) == 0;
+                    const bool up = ((e & (S - 1)) & kk) == 0;
                     const bool lower = (e & j) == 0;
                     // the lower slot keeps the minimum when ascending
                     const bool take = lower ? (up ? o < k[r] : o > k[r]) : (up ? o > k[r] : o < k[r]);
