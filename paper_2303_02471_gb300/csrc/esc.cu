@@ -1,28 +1,21 @@
 // ESC accumulator (Expand, Sort, Compress; Section 4) for the light columns
 // of C = A x B: the lane-group bins, Op_j <= 256.
 //
-// A warp works a tile of kEscTile = 256 product slots: the columns of a bin
-// list are cut into tiles of 256 / S columns, S = the bin's largest Op_j (a
-// power of two, 8 .. 256), and column c of the tile owns the aligned slots
-// [c S, (c + 1) S).  Per tile:
-//   Expand    every product A_ik * B_kj of the tile's columns is gathered:
-//             its value into the warp's shared memory at its slot, its key
-//             (i << 8) | slot into the slot's key (unused slots hold a key
-//             above every row);
-//   Sort      the 256 keys sit in eight registers per lane (slot e in
-//             register e / 32 of lane e % 32) and a bitonic network over the
-//             slots, cut off at S, sorts every column's segment by row: the
-//             stages exchange partners by shuffles (distance < 32) or within
-//             a lane's registers, and the eight registers are independent;
-//   Compress  equal rows are neighbours: the first of each run sums the run
-//             in sorted order (values looked up through the slot in the key)
-//             and writes one entry of C at its column's pointer plus its rank
-//             among the column's runs.
-// The sums do not depend on timing (no atomics on values).  The paper's ESC
-// sorts with a radix sort tuned to its vector unit; a warp-level radix sort
-// (8-bit digits, ranks from __match_any_sync) was measured here first and
-// spent its time in chains of dependent shared-memory steps, which the
-// register network does not have.
+// A warp works a tile of kEscTile products: the columns of a bin list are cut
+// into tiles of kEscTile / opmax columns (opmax = the bin's largest Op_j, so
+// every tile fits), one column per lane.  Per tile:
+//   Expand    every product A_ik * B_kj of the tile's columns is gathered
+//             into the warp's shared memory as the key (c << rb) | i (c the
+//             column's place in the tile, i the row, rb the row bits) and
+//             its value;
+//   Sort      a stable LSD radix sort of the keys (digits of kEscRadixBits
+//             bits; a lane's place among the lanes with the same digit comes
+//             from __match_any_sync), which orders the products by column
+//             and, inside a column, by row;
+//   Compress  equal keys are neighbours: the first of each run sums the run
+//             in sorted order and writes one entry of C at its column's
+//             pointer plus its rank among the column's runs.
+// The sums do not depend on timing (no atomics on values).
 //
 // Modes: with values and no count output it is the numeric phase (C's
 // column pointers come from the symbolic phase; a column whose run count
@@ -31,27 +24,29 @@
 // writes each column at base[j] and its count into cnt_out[j + 1] (the
 // single-pass form, where base holds slots sized by Op_j).
 //
-// Keys are 32-bit: the forward passes' rows must be below 2^24 - 1; the host
-// keeps hash tables otherwise.
+// Keys are 32-bit: the forward passes' rows and the tile's column places must
+// fit (rb + log2(columns per tile) <= 32); the host keeps hash tables
+// otherwise.
 #include "columns.cuh"
 #include "esc.cuh"
 
 namespace spg {
 
-constexpr uint32_t kEscPad = 0xffffffffu;
-
-// Shared memory of one warp: the slots' keys (expansion, then the sorted
-// keys), the run count of each of the tile's columns, and the values.
+// Shared memory of one warp.  The sort moves (key, index) pairs; the values
+// stay where the expansion put them and are read through the index.
 template <bool VALS, typename VT>
 struct EscWarp {
-    uint32_t key[kEscTile];
-    int32_t cnt[32];
+    uint32_t key[2][kEscTile];
+    uint32_t cnt[1 << kEscRadixBits];
+    int32_t hstart[32];
 };
 template <typename VT>
 struct EscWarp<true, VT> {
-    uint32_t key[kEscTile];
-    int32_t cnt[32];
+    uint32_t key[2][kEscTile];
     VT val[kEscTile];
+    uint32_t cnt[1 << kEscRadixBits];
+    int32_t hstart[32];
+    uint8_t idx[2][kEscTile];
 };
 
 template <bool VALS, typename VT>
@@ -59,9 +54,10 @@ __host__ __device__ constexpr size_t esc_warp_bytes() {
     return (sizeof(EscWarp<VALS, VT>) + 15) & ~size_t(15);
 }
 
-// CTAs per SM the kernels are built for (registers).
+// CTAs per SM the kernels are built for (registers): the value-carrying
+// form holds more shared memory per warp.
 template <bool VALS>
-constexpr int esc_min_blocks() { return VALS ? 4 : 4; }
+constexpr int esc_min_blocks() { return VALS ? 5 : 6; }
 
 // Lane holding the owner of position q among 32 lanes with non-decreasing
 // exclusive offsets `excl` (the last lane whose offset is <= q).
@@ -75,91 +71,45 @@ __device__ __forceinline__ int esc_owner(int excl, int q) {
     return s;
 }
 
-// Bitonic network over the 256 slots (slot e = r * 32 + lane in register r),
-// stages kk = 2 .. S: every aligned segment of S slots ends up ascending.
-template <int S>
-__device__ __forceinline__ void esc_segment_sort(uint32_t (&k)[kEscTile / 32]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int kk = 2; kk <= S; kk <<= 1) {
-#pragma unroll
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int jr = j / 32;
-#pragma unroll
-                for (int r = 0; r < kEscTile / 32; ++r) {
-                    if ((r & jr) == 0) {
-                        const int e = r * 32 + lane;
-                        // direction from the slot's place in its segment: every
-                        // segment ends ascending (the last stage has kk = S)
-                        const bool up = ((e & (S - 1)) & kk) == 0;
-                        const uint32_t a = k[r], b = k[r | jr];
-                        const bool swap = up ? a > b : a < b;
-                        k[r] = swap ? b : a;
-                        k[r | jr] = swap ? a : b;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < kEscTile / 32; ++r) {
-                    const int e = r * 32 + lane;
-                    const uint32_t o = __shfl_xor_sync(0xffffffffu, k[r], j);
-                    const bool up = ((e & (S - 1)) & kk) == 0;
-                    const bool lower = (e & j) == 0;
-                    // the lower slot keeps the minimum when ascending
-                    const bool take = lower ? (up ? o < k[r] : o > k[r]) : (up ? o > k[r] : o < k[r]);
-                    if (take) k[r] = o;
-                }
-            }
-        }
-    }
-}
-
-template <bool VALS, typename VT, int S>
+template <bool VALS, typename VT>
 __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
-    k_esc(BinTask t, Operands o, const int64_t *base, int64_t *cnt_out, int32_t *Crow, VT *Cval) {
-    constexpr int CT = kEscTile / S;   // columns per tile (<= 32)
-    constexpr int NR = kEscTile / 32;  // key registers per lane
+    k_esc(BinTask t, Operands o, const int64_t *base, int64_t *cnt_out, int32_t *Crow, VT *Cval, EscShape e) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_max, s_sum;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    EscWarp<VALS, VT> &W = *reinterpret_cast<EscWarp<VALS, VT> *>(smem + (size_t)warp * esc_warp_bytes<VALS, VT>());
+    EscWarp<VALS, VT> &S = *reinterpret_cast<EscWarp<VALS, VT> *>(smem + (size_t)warp * esc_warp_bytes<VALS, VT>());
     if (threadIdx.x == 0) s_max = s_sum = 0;
     __syncthreads();
     const TOps<VT> ops = typed<VT>(o);
     const uint64_t pol = keep_policy();
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t ntiles = ceil_div(t.count, (int64_t)CT);
+    const uint32_t rowmask = e.rb >= 32 ? 0xffffffffu : ((1u << e.rb) - 1u);
+    const int64_t ntiles = ceil_div(t.count, (int64_t)e.ct);
     unsigned long long my_max = 0, my_sum = 0;
     const int64_t tstride = (int64_t)gridDim.x * kEscWarps;
     int64_t tile = (int64_t)blockIdx.x * kEscWarps + warp;
-    // the next tile's column ids, B column pointers and Op_j are loaded
-    // while the current tile is sorted
+    // the next tile's column ids and B column pointers are loaded while the
+    // current tile is sorted
     int32_t nj = 0;
-    int64_t np0 = 0, np1 = 0, nop = 0;
+    int64_t np0 = 0, np1 = 0;
     auto fetch = [&](int64_t tl) {
-        const int64_t f = tl * CT;
-        if (tl < ntiles && lane < CT && f + lane < t.count) {
+        const int64_t f = tl * e.ct;
+        if (tl < ntiles && lane < e.ct && f + lane < t.count) {
             nj = t.cols[f + lane];
             np0 = ops.Bcp[nj];
             np1 = ops.Bcp[nj + 1];
-            nop = t.op[nj];
         }
     };
     fetch(tile);
     for (; tile < ntiles; tile += tstride) {
-        const int64_t first = tile * CT;
-        const int nc = (int)(t.count - first < CT ? t.count - first : CT);
+        const int64_t first = tile * e.ct;
+        const int nc = (int)(t.count - first < e.ct ? t.count - first : e.ct);
         // ---- the tile's columns, one per lane: B entries and their offsets
-        const bool col = lane < nc;
-        const int32_t j = col ? nj : 0;
-        const int64_t p0 = col ? np0 : 0;
-        const int nb = col ? (int)(np1 - np0) : 0;
-        // products of the column (Op_j of the plan; products beyond it mean
-        // the pattern changed: reported, never written past the segment)
-        const int opc = col ? (int)nop : 0;
+        const int32_t j = lane < nc ? nj : 0;
+        const int64_t p0 = lane < nc ? np0 : 0;
+        const int nb = lane < nc ? (int)(np1 - np0) : 0;
         int64_t cb = 0, ccap = 0;
-        if (col) {
+        if (lane < nc) {
             cb = base[j];
             ccap = base[j + 1] - cb;  // entries the column's place holds
         }
@@ -172,20 +122,9 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
         }
         const int eexcl = eincl - nb;
         const int E = __shfl_sync(0xffffffffu, eincl, 31);
-        // first flat product of each column (the expansion runs column by column)
-        int pincl = opc;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, pincl, d);
-            if (lane >= d) pincl += v;
-        }
-        const int pexcl = pincl - opc;
-        // ---- expand: every slot starts as padding, products take their slots
-#pragma unroll
-        for (int r = 0; r < NR; ++r) W.key[r * 32 + lane] = kEscPad;
-        __syncwarp();
-        int n = 0;  // flat products so far
-        bool bad = false;
+        // ---- expand: 32 B entries per round, then their products
+        int n = 0;
+        bool over = false;
         for (int e0 = 0; e0 < E; e0 += 32) {
             const int en = e0 + lane;
             const int c = esc_owner(eexcl, en < E ? en : E - 1);
@@ -209,91 +148,138 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
             }
             const int zexcl = zincl - z;
             const int total = __shfl_sync(0xffffffffu, zincl, 31);
+            if (n + total > kEscTile) {  // only if the pattern changed since planning
+                over = true;
+                break;
+            }
             for (int q0 = 0; q0 < total; q0 += 32) {
                 const int q = q0 + lane;
                 const int s = esc_owner(zexcl, q < total ? q : total - 1);
                 const int64_t a0s = __shfl_sync(0xffffffffu, a0, s);
                 const int exs = __shfl_sync(0xffffffffu, zexcl, s);
                 const int cs = __shfl_sync(0xffffffffu, c, s);
-                const int ps = __shfl_sync(0xffffffffu, pexcl, cs);
-                const int os = __shfl_sync(0xffffffffu, opc, cs);
                 VT bs = VT(0);
                 if (VALS) bs = __shfl_sync(0xffffffffu, bv, s);
                 if (q < total) {
-                    const int within = n + q - ps;  // the product's place in its column
-                    if (within >= 0 && within < os && within < S) {
-                        const int slot = cs * S + within;
-                        const int64_t qa = a0s + (q - exs);
-                        const int32_t row = ld_keep(ops.Arow + qa, pol);
-                        W.key[slot] = ((uint32_t)row << 8) | (uint32_t)slot;
-                        if constexpr (VALS) W.val[slot] = ld_keep(ops.Aval + qa, pol) * bs;
-                    } else {
-                        bad = true;  // Op_j differs from the plan's
+                    const int64_t qa = a0s + (q - exs);
+                    const int32_t row = ld_keep(ops.Arow + qa, pol);
+                    S.key[0][n + q] = ((uint32_t)cs << e.rb) | ((uint32_t)row & rowmask);
+                    if constexpr (VALS) {
+                        S.val[n + q] = ld_keep(ops.Aval + qa, pol) * bs;
+                        S.idx[0][n + q] = (uint8_t)(n + q);
                     }
                 }
             }
             n += total;
         }
-        if (__any_sync(0xffffffffu, bad)) {
+        if (over) {
             if (lane == 0) set_error(t.ctrl, SPG_ERR_INVALID, kDetailCountMismatch + t.bin, j);
             continue;
         }
         __syncwarp();
-        // ---- sort every column's segment by row
-        uint32_t k[NR];
+        // ---- sort: stable LSD radix over the key bits
+        int cur = 0;
+        for (int pass = 0; pass < e.passes; ++pass) {
+            const int sh = pass * kEscRadixBits;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) k[r] = W.key[r * 32 + lane];
-        esc_segment_sort<S>(k);
-        __syncwarp();
+            for (int b = lane; b < (1 << kEscRadixBits); b += 32) S.cnt[b] = 0u;
+            __syncwarp();
+            for (int i = lane; i < n; i += 32)
+                atomicAdd(&S.cnt[(S.key[cur][i] >> sh) & ((1u << kEscRadixBits) - 1u)], 1u);
+            __syncwarp();
+            {  // exclusive scan of the buckets: lane l owns the 8 buckets from 8 l
+                constexpr int PER = (1 << kEscRadixBits) / 32;
+                uint32_t v[PER];
+                uint32_t run = 0;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) W.key[r * 32 + lane] = k[r];
-        __syncwarp();
-        // ---- compress: the first slot of each run of equal rows writes the
-        // run's sum; heads are ranked inside their column's segment
-        int runs = 0;  // S >= 32: heads of the current column in earlier registers
+                for (int u = 0; u < PER; ++u) {
+                    v[u] = S.cnt[lane * PER + u];
+                    const uint32_t x = v[u];
+                    v[u] = run;
+                    run += x;
+                }
+                uint32_t incl = run;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const int e = r * 32 + lane;
-            const int c = e / S;  // column of the slot (< CT <= 32)
-            const int q = e % S;  // place in the column's sorted segment
-            const int oc = __shfl_sync(0xffffffffu, opc, c);
-            const bool valid = q < oc;
-            const uint32_t kv = k[r];
-            const uint32_t row = kv >> 8;
-            const bool head = valid && (q == 0 || (W.key[e - 1] >> 8) != row);
-            const unsigned hm = __ballot_sync(0xffffffffu, head);
-            int rank;
-            if constexpr (S >= 32) {
-                // every lane of the register is in the same column
-                if ((r * 32) % S == 0) runs = 0;
-                rank = runs + __popc(hm & lt);
-                runs += __popc(hm);
-                if ((r * 32) % S == S - 32 && lane == 0) W.cnt[c] = runs;
-            } else {
-                const unsigned seg = ((1u << S) - 1u) << (lane & ~(S - 1));
-                rank = __popc(hm & seg & lt);
-                if (q == 0) W.cnt[c] = __popc(hm & seg);
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                const uint32_t off = incl - run;
+#pragma unroll
+                for (int u = 0; u < PER; ++u) S.cnt[lane * PER + u] = v[u] + off;
             }
+            __syncwarp();
+            for (int i0 = 0; i0 < n; i0 += 32) {
+                const int i = i0 + lane;
+                const bool valid = i < n;
+                const uint32_t k = valid ? S.key[cur][i] : 0u;
+                uint8_t ix = 0;
+                if constexpr (VALS) ix = valid ? S.idx[cur][i] : (uint8_t)0;
+                // lanes past n get digits of their own, so they never share a
+                // group with a key
+                const uint32_t dg = valid ? ((k >> sh) & ((1u << kEscRadixBits) - 1u)) : (0x10000u + lane);
+                const unsigned same = __match_any_sync(0xffffffffu, dg);
+                const int leader = __ffs(same) - 1;
+                uint32_t at = 0;
+                if (valid && lane == leader) {
+                    at = S.cnt[dg];
+                    S.cnt[dg] = at + (uint32_t)__popc(same);
+                }
+                at = __shfl_sync(0xffffffffu, at, leader) + (uint32_t)__popc(same & lt);
+                if (valid) {
+                    S.key[cur ^ 1][at] = k;
+                    if constexpr (VALS) S.idx[cur ^ 1][at] = ix;
+                }
+                __syncwarp();
+            }
+            cur ^= 1;
+        }
+        // ---- compress: the first key of each run writes the run's sum
+        if (lane < 32) S.hstart[lane] = 0x7fffffff;  // columns without runs stay unset
+        __syncwarp();
+        int hbase = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < n;
+            const uint32_t k = valid ? S.key[cur][i] : 0u;
+            const uint32_t kp = valid && i > 0 ? S.key[cur][i - 1] : 0u;
+            const bool head = valid && (i == 0 || kp != k);
+            const unsigned hm = __ballot_sync(0xffffffffu, head);
+            const int hr = hbase + __popc(hm & lt);
+            hbase += __popc(hm);
+            const int c = (int)(k >> e.rb);
+            if (head && (i == 0 || (int)(kp >> e.rb) != c)) S.hstart[c] = hr;
+            __syncwarp();
             if constexpr (VALS) {
-                const int64_t cbase = __shfl_sync(0xffffffffu, cb, c);
-                const int64_t cc = __shfl_sync(0xffffffffu, ccap, c);
+                const int64_t cbase = __shfl_sync(0xffffffffu, cb, c & 31);
+                const int64_t cc = __shfl_sync(0xffffffffu, ccap, c & 31);
                 if (head) {
-                    VT sum = W.val[kv & 0xffu];
-                    for (int m2 = e + 1; (m2 % S) != 0 && (m2 % S) < oc && (W.key[m2] >> 8) == row; ++m2)
-                        sum += W.val[W.key[m2] & 0xffu];
+                    VT sum = S.val[S.idx[cur][i]];
+                    for (int m2 = i + 1; m2 < n && S.key[cur][m2] == k; ++m2) sum += S.val[S.idx[cur][m2]];
+                    const int64_t r = hr - S.hstart[c];
                     // a column with more runs than its place holds is reported
                     // below and not written past its place
-                    if (rank < cc) {
-                        Crow[cbase + rank] = ops.crow((int32_t)row);
-                        Cval[cbase + rank] = sum;
+                    if (r < cc) {
+                        Crow[cbase + r] = ops.crow((int32_t)(k & rowmask));
+                        Cval[cbase + r] = sum;
                     }
                 }
             }
         }
         __syncwarp();
-        // ---- per-column run counts: written (symbolic, single pass) or checked
-        if (col) {
-            const int64_t cnt = W.cnt[lane];
+        // ---- per-column run counts: written (symbolic, single pass) or checked.
+        // A column's runs end where the next column with runs starts.
+        const int st = lane < nc ? S.hstart[lane] : 0x7fffffff;
+        int nxt = st;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_down_sync(0xffffffffu, nxt, d);
+            if (lane + d < 32 && v < nxt) nxt = v;
+        }
+        nxt = __shfl_down_sync(0xffffffffu, nxt, 1);
+        if (lane == 31 || nxt > hbase) nxt = hbase;
+        if (lane < nc) {
+            const int64_t cnt = st == 0x7fffffff ? 0 : (int64_t)(nxt - st);
             if (cnt_out) {
                 cnt_out[j + 1] = cnt;
                 if ((unsigned long long)cnt > my_max) my_max = (unsigned long long)cnt;
@@ -333,43 +319,33 @@ bool esc_shape(int bin, int64_t m, EscShape &e) {
     if (bin < BIN_WARP0 || bin >= BIN_CTA0) return false;
     const int opmax = warp_bin_opmax(bin - BIN_WARP0);
     e.ct = kEscTile / opmax;
-    if (e.ct < 1 || e.ct > 32) return false;
-    // keys (row << 8) | slot stay below the padding key
-    if (m >= ((int64_t)1 << 24) - 1) return false;
+    if (e.ct > 32) e.ct = 32;
+    if (e.ct < 1) return false;
+    int cb = 0;
+    while ((1 << cb) < e.ct) ++cb;
     int rb = 1;
     while (rb < 32 && ((int64_t)1 << rb) < m) ++rb;
     e.rb = rb;
+    const int bits = rb + cb;
+    if (bits > 32) return false;
+    e.passes = (bits + kEscRadixBits - 1) / kEscRadixBits;
     return true;
-}
-
-template <bool VALS, typename VT, int S>
-static cudaError_t launch_esc_s(const BinTask &t, const Operands &o, const int64_t *base, int64_t *cnt_out,
-                                int32_t *Crow, VT *Cval, int sms, cudaStream_t s) {
-    auto k = k_esc<VALS, VT, S>;
-    const size_t smem = (size_t)kEscWarps * esc_warp_bytes<VALS, VT>();
-    esc_allow_smem(k, smem);
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kEscWarps * 32, smem) != cudaSuccess || occ < 1)
-        occ = 1;
-    const int64_t ntiles = ceil_div(t.count, (int64_t)(kEscTile / S));
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntiles, kEscWarps), (int64_t)occ * sms));
-    k<<<(unsigned)grid, kEscWarps * 32, smem, s>>>(t, o, base, cnt_out, Crow, Cval);
-    return cudaGetLastError();
 }
 
 template <bool VALS, typename VT>
 static cudaError_t launch_esc_t(const BinTask &t, const Operands &o, const int64_t *base, int64_t *cnt_out,
                                 int32_t *Crow, VT *Cval, const EscShape &e, int sms, cudaStream_t s) {
     if (t.count <= 0) return cudaSuccess;
-    switch (kEscTile / e.ct) {
-        case 8: return launch_esc_s<VALS, VT, 8>(t, o, base, cnt_out, Crow, Cval, sms, s);
-        case 16: return launch_esc_s<VALS, VT, 16>(t, o, base, cnt_out, Crow, Cval, sms, s);
-        case 32: return launch_esc_s<VALS, VT, 32>(t, o, base, cnt_out, Crow, Cval, sms, s);
-        case 64: return launch_esc_s<VALS, VT, 64>(t, o, base, cnt_out, Crow, Cval, sms, s);
-        case 128: return launch_esc_s<VALS, VT, 128>(t, o, base, cnt_out, Crow, Cval, sms, s);
-        case 256: return launch_esc_s<VALS, VT, 256>(t, o, base, cnt_out, Crow, Cval, sms, s);
-    }
-    return cudaErrorInvalidValue;
+    auto k = k_esc<VALS, VT>;
+    const size_t smem = (size_t)kEscWarps * esc_warp_bytes<VALS, VT>();
+    esc_allow_smem(k, smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kEscWarps * 32, smem) != cudaSuccess || occ < 1)
+        occ = 1;
+    const int64_t ntiles = ceil_div(t.count, (int64_t)e.ct);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(ntiles, kEscWarps), (int64_t)occ * sms));
+    k<<<(unsigned)grid, kEscWarps * 32, smem, s>>>(t, o, base, cnt_out, Crow, Cval, e);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_esc_bin(const BinTask &t, const Operands &o, const int64_t *base, int64_t *cnt_out,

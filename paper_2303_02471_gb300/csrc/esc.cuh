@@ -6,16 +6,19 @@
 namespace spg {
 
 constexpr int kEscWarps = 8;       // warps per CTA, each working its own tiles
-constexpr int kEscTile = 256;      // product slots of one warp tile
+constexpr int kEscTile = 256;      // products one warp tile holds
+constexpr int kEscRadixBits = 8;   // digit width of the radix sort
 
-// Tile shape of one lane-group bin: columns per tile and row bits of the keys.
+// Tile shape of one lane-group bin: columns per tile, row bits of the keys
+// and radix passes over the key bits.
 struct EscShape {
     int ct = 0;
     int rb = 0;
+    int passes = 0;
 };
 
 // Shape of bin `bin` for a product whose forward passes number m rows; false
-// when the bin is no lane-group bin or the rows do not fit the keys' 24 bits.
+// when the bin is no lane-group bin or the keys do not fit 32 bits.
 bool esc_shape(int bin, int64_t m, EscShape &e);
 
 // values = false: run counts into cnt_out[j + 1] (symbolic).  values = true:

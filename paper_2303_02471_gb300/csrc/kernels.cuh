@@ -272,52 +272,32 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                     if (w.key[mid] <= win0) li = mid; else hi = mid - 1;
                 }
                 if constexpr (UB == 1) {
-                    // one flattened sequence of windows over the entries: a
-                    // cursor loads two windows ahead, across entry
-                    // boundaries, so gathers stay in flight where an A column
-                    // ends after a window or two
-                    int pl = li, pw = win0;
-                    int pk = w.key[pl], pz = w.z[pl];
-                    int64_t pa = w.a0[pl];
-                    VT pb = VALS ? w.bv[pl] : VT(0);
-                    int pnext = pl + 1 < nl ? w.key[pl + 1] : 0x7fffffff;
-                    auto load = [&](int32_t &row, VT &av, VT &bb) {
-                        row = -1;
-                        av = VT(0);
-                        bb = pb;
-                        if (pw < e1) {
-                            while (pw >= pnext) {
-                                ++pl;
-                                pk = pnext;
-                                pz = w.z[pl];
-                                pa = w.a0[pl];
-                                if (VALS) pb = w.bv[pl];
-                                pnext = pl + 1 < nl ? w.key[pl + 1] : 0x7fffffff;
-                            }
-                            bb = pb;
-                            const int idx = ((pw - pk) << 5) + lane;
-                            if (idx < pz) {
-                                row = ld_keep(Arow + pa + idx, pol);
-                                if (VALS) av = ld_keep(Aval + pa + idx, pol);
-                            }
+                    // entry by entry: the entry's windows in [win, e_end)
+                    // are one warp-uniform loop over idx = window * 32 + lane
+                    // of its A column
+                    for (int win = win0; win < e1; ++li) {
+                        const int e_key = w.key[li], e_z = w.z[li];
+                        const int nk = li + 1 < nl ? w.key[li + 1] : 0x7fffffff;
+                        const int e_end = nk < e1 ? nk : e1;
+                        const int64_t a0 = w.a0[li];
+                        const int32_t *rp = Arow + a0;
+                        const VT *vp = VALS ? Aval + a0 : nullptr;
+                        const VT b = VALS ? w.bv[li] : VT(0);
+                        const int i1 = (e_end - e_key) << 5;
+                        // one window ahead: the next window's gathers are in
+                        // flight while this one is consumed
+                        int idx = ((win - e_key) << 5) + lane;
+                        int32_t row = idx < e_z ? ld_keep(rp + idx, pol) : -1;
+                        VT av = VALS && idx < e_z ? ld_keep(vp + idx, pol) : VT(0);
+                        for (; idx < i1; idx += 32) {
+                            const int nx = idx + 32;
+                            const int32_t row_n = nx < i1 && nx < e_z ? ld_keep(rp + nx, pol) : -1;
+                            const VT av_n = VALS && nx < i1 && nx < e_z ? ld_keep(vp + nx, pol) : VT(0);
+                            if (row >= 0) f(row, VALS ? av * b : VT(0));
+                            row = row_n;
+                            av = av_n;
                         }
-                        ++pw;
-                    };
-                    int32_t r0, r1;
-                    VT v0, v1, b0, b1;
-                    load(r0, v0, b0);
-                    load(r1, v1, b1);
-                    for (int win = win0; win < e1; ++win) {
-                        int32_t r2;
-                        VT v2, b2;
-                        load(r2, v2, b2);
-                        if (r0 >= 0) f(r0, VALS ? v0 * b0 : VT(0));
-                        r0 = r1;
-                        v0 = v1;
-                        b0 = b1;
-                        r1 = r2;
-                        v1 = v2;
-                        b1 = b2;
+                        win = e_end;
                     }
                 } else {
                     // the owner is the same for every lane of a window: keep its
@@ -661,22 +641,14 @@ __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W64, bool cl
         const int cnt = __popc(v.x);
         const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
         if (maxc <= kVisitLight) {
-            // the word's rows first, then their writes: the writes' look-ups
-            // (C's row of a compact row) are in flight together
             const int32_t row0 = wd << 5;
             uint32_t bits = v.x;
-            int32_t rr[kVisitLight];
-#pragma unroll
-            for (int u = 0; u < kVisitLight; ++u) {
-                rr[u] = -1;
-                if (bits) {
-                    rr[u] = row0 + __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                }
+            int32_t rank = (int32_t)v.y;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                f(row0 + b, rank++);
             }
-#pragma unroll
-            for (int u = 0; u < kVisitLight; ++u)
-                if (rr[u] >= 0) f(rr[u], (int32_t)v.y + u);
         } else {
             // lane 0's word always exists; words past W never hold rank o < S
             const uint32_t y0 = __shfl_sync(0xffffffffu, v.y, 0);

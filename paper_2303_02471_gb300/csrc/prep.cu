@@ -28,12 +28,14 @@ __global__ void k_validate(const int64_t *__restrict__ cp, const int32_t *__rest
 // Op_j = sum over stored B_kj of Z^A_k (Section 3.1), its bin, the bin
 // histogram and the total product count.  Empty columns get nnz 0 here.
 //
-// A warp takes 32 consecutive columns, one per lane, and walks their B
-// entries 32 at a time as one flattened sequence (the owner of an entry is
-// found by a search over the lanes' entry offsets), so short columns keep
-// every lane busy and long ones are split over the warp; the Z^A_k of an
-// entry's lanes are summed by a segmented warp scan.  Per-bin statistics are
-// summed over the warp before one shared atomic per bin present.
+// A warp takes 32 columns, one per lane, strided by the number of warps (so
+// the heavy columns of a skewed matrix, which sit together, spread over the
+// warps), and walks their B entries 32 at a time as one flattened sequence
+// (the owner of an entry is found by a search over the lanes' entry
+// offsets), so short columns keep every lane busy and long ones are split
+// over the warp; the Z^A_k of an entry's lanes are summed by a segmented
+// warp scan.  Per-bin statistics are summed over the warp before one shared
+// atomic per bin present.
 __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__restrict__ Brow,
                             const int64_t *__restrict__ Acp, int64_t nB, int64_t t, int64_t hmax, int64_t mrows,
                             int64_t *__restrict__ op, int64_t *__restrict__ Ccp, Ctrl *ctrl) {
@@ -55,8 +57,8 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
     int64_t *wop = s_op + (threadIdx.x & ~31);
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long mine = 0, cap = 0;
-    for (int64_t j0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < nB; j0 += nwarps * 32) {
-        const int64_t j = j0 + lane;
+    for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j0 < nB; j0 += nwarps * 32) {
+        const int64_t j = j0 + (int64_t)lane * nwarps;
         const bool on = j < nB;
         int64_t p0 = 0, nb = 0;
         if (on) {
