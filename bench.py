@@ -591,16 +591,15 @@ def run_ours(args, rank, world):
             for k in (2, 3):
                 if k != args.workload:
                     others[str(k)] = measure_workload(k, args, dev, flush, max(3, min(args.steps, 10)), 3, *peak_w)
-            # the light columns by the ESC accumulator (Section 4) instead of hash tables
+            # the light columns with hash tables in both phases (Section 3.2)
+            # and with ESC in both phases (Section 4), beside the default
+            # (hash-table counts, ESC values)
             ksteps = max(3, min(args.steps, 10))
             for k in (2, 3):
-                entry = others.get(str(k))
-                esc = measure_workload(k, args, dev, flush, ksteps, 3, *peak_w,
-                                       cfg=ops.Config(small_accumulator="esc"))
-                if entry is None:
-                    others[str(k)] = {"esc": esc}
-                else:
-                    entry["esc"] = esc
+                entry = others.setdefault(str(k), {})
+                for acc in ("hash", "esc"):
+                    entry[acc] = measure_workload(k, args, dev, flush, ksteps, 3, *peak_w,
+                                                  cfg=ops.Config(small_accumulator=acc))
             aux = {"workloads": others, "batched": run_batched(args, dev, *peak_w),
                    "backward": run_backward(args, dev, *peak_w)}
             if not args.no_sweep:

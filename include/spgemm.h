@@ -118,16 +118,20 @@ typedef struct {
      * runs without any fault. */
     int32_t test_wait_timeout;
     /* Accumulator of the lane-group bins (columns with Op_j <= 256):
-     * SPG_ACC_HASH, the hash tables of Section 3.2; SPG_ACC_ESC, the ESC
-     * algorithm of Section 4 (the products of a tile of columns are expanded
-     * into shared memory, radix-sorted by (column, row) and compressed); a
-     * bin whose (column, row) keys do not fit 32 bits keeps hash tables.
-     * Both give the same C (the ESC sums do not depend on timing).  Only the
-     * single products use it; the batched calls keep hash tables. */
+     * SPG_ACC_HASH, the hash tables of Section 3.2, in both phases;
+     * SPG_ACC_ESC, the ESC algorithm of Section 4 (the products of a tile of
+     * columns are expanded into shared memory, radix-sorted by (column, row)
+     * and compressed), in both phases; SPG_ACC_AUTO (default), hash tables
+     * for the symbolic phase's counts and ESC for the numeric phase (the
+     * cheaper of the two in each phase, measured on GB300).  A bin whose
+     * (column, row) keys do not fit 32 bits keeps hash tables.  All give the
+     * same C (the ESC sums do not depend on timing).  The single pass uses
+     * ESC unless SPG_ACC_HASH.  Only the single products use it; the batched
+     * calls keep hash tables. */
     int32_t small_accumulator;
 } spg_config;
 
-enum { SPG_ACC_HASH = 0, SPG_ACC_ESC = 1 };
+enum { SPG_ACC_HASH = 0, SPG_ACC_ESC = 1, SPG_ACC_AUTO = 2 };
 
 typedef struct spg_plan spg_plan;
 

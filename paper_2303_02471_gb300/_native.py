@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libspgemm.so")
 i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
 
 SPG_F64, SPG_F32 = 0, 1
-SPG_ACC_HASH, SPG_ACC_ESC = 0, 1
+SPG_ACC_HASH, SPG_ACC_ESC, SPG_ACC_AUTO = 0, 1, 2
 STATUS = {
     0: "SPG_OK", 1: "SPG_ERR_INVALID", 2: "SPG_ERR_WORKSPACE", 3: "SPG_ERR_TABLE_OVERFLOW",
     4: "SPG_ERR_TIMEOUT", 5: "SPG_ERR_CUDA", 6: "SPG_ERR_UNSUPPORTED", 7: "SPG_ERR_INDEX_OVERFLOW",

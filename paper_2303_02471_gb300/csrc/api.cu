@@ -252,7 +252,7 @@ spg_status spg_config_default(spg_config *cfg) {
     cfg->dense_cache_bytes = (int64_t)2 << 30;
     cfg->side_streams = 1;
     cfg->test_wait_timeout = 0;
-    cfg->small_accumulator = SPG_ACC_HASH;
+    cfg->small_accumulator = SPG_ACC_AUTO;
     return SPG_OK;
 }
 
@@ -284,7 +284,9 @@ static spg_status check_config(const spg_config &c) {
     if (c.cta_threads < 128 || c.cta_threads > 1024 || c.cta_threads % 32) return SPG_ERR_INVALID;
     if (c.table_shrink < 0 || c.table_shrink > 30) return SPG_ERR_INVALID;
     if (c.dense_cache_bytes < 0 || c.scratch_cap_bytes < 0) return SPG_ERR_INVALID;
-    if (c.small_accumulator != SPG_ACC_HASH && c.small_accumulator != SPG_ACC_ESC) return SPG_ERR_INVALID;
+    if (c.small_accumulator != SPG_ACC_HASH && c.small_accumulator != SPG_ACC_ESC &&
+        c.small_accumulator != SPG_ACC_AUTO)
+        return SPG_ERR_INVALID;
     return SPG_OK;
 }
 
@@ -413,8 +415,8 @@ static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B
     if (P->nB > 0) {
         // a warp per 32 columns, 8 warps per CTA
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(P->nB, 256), 16 * (int64_t)P->dev.sms));
-        k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->mC, P->op(),
-                                      C_colptr, ctrl);
+        k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->mC,
+                                      column_deal_mult(P->nB), P->op(), C_colptr, ctrl);
         CK(cudaGetLastError());
     } else {
         CK(cudaMemsetAsync(C_colptr, 0, sizeof(int64_t), s));
@@ -438,7 +440,9 @@ static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B
     }
     CK(cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s));
 #undef CK
-    if (c.small_accumulator == SPG_ACC_ESC)
+    // the numeric phase (and the single pass) take ESC unless hash tables
+    // were asked for; the symbolic phase counts with ESC only when asked
+    if (c.small_accumulator != SPG_ACC_HASH)
         for (int b = BIN_WARP0; b < BIN_CTA0; ++b) P->esc[b] = esc_shape(b, P->mC, P->esc_shape_of[b]);
     // validation, row marks (mark, 3 scan kernels) and, when compacting,
     // map and remap, the two control reads, Op counting + scatter
@@ -479,7 +483,7 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
         CK(cudaEventRecord(P->ss().fork, s));
     }
     auto sym_bin = [&](int b, cudaStream_t sb) {
-        if (P->esc[b])
+        if (P->esc[b] && c.small_accumulator == SPG_ACC_ESC)
             return launch_esc_bin(P->task(b), o, C_colptr, C_colptr, nullptr, nullptr, false, P->dtype,
                                   P->esc_shape_of[b], P->dev.sms, sb);
         // the symbolic CTA kernels carry no values: CTAs of up to 256 threads,

@@ -756,7 +756,11 @@ int64_t scan_tile_count(int64_t n);
 __global__ void k_validate(const int64_t *cp, const int32_t *row, int64_t nrows, int64_t ncols,
                            int64_t nnz, int which, Ctrl *ctrl);
 __global__ void k_count_bin(const int64_t *Bcp, const int32_t *Brow, const int64_t *Acp, int64_t nB,
-                            int64_t t, int64_t hmax, int64_t mrows, int64_t *op, int64_t *Ccp, Ctrl *ctrl);
+                            int64_t t, int64_t hmax, int64_t mrows, int64_t mult, int64_t *op, int64_t *Ccp,
+                            Ctrl *ctrl);
+// Multiplier coprime to n (n >= 1) near n times the golden ratio's fraction,
+// dealing the columns of k_count_bin over the warps.
+int64_t column_deal_mult(int64_t n);
 __global__ void k_slot_caps(const int64_t *op, int64_t nB, int64_t mrows, int64_t *caps);
 cudaError_t launch_slot_copy(int64_t nB, const int64_t *Ccp, const int64_t *soff, const int32_t *srow,
                              const void *sval, int32_t *Crow, void *Cval, int w, int sms, cudaStream_t s);

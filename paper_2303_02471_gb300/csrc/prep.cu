@@ -28,17 +28,21 @@ __global__ void k_validate(const int64_t *__restrict__ cp, const int32_t *__rest
 // Op_j = sum over stored B_kj of Z^A_k (Section 3.1), its bin, the bin
 // histogram and the total product count.  Empty columns get nnz 0 here.
 //
-// A warp takes 32 columns, one per lane, strided by the number of warps (so
-// the heavy columns of a skewed matrix, which sit together, spread over the
-// warps), and walks their B entries 32 at a time as one flattened sequence
-// (the owner of an entry is found by a search over the lanes' entry
-// offsets), so short columns keep every lane busy and long ones are split
-// over the warp; the Z^A_k of an entry's lanes are summed by a segmented
-// warp scan.  Per-bin statistics are summed over the warp before one shared
-// atomic per bin present.
+// A warp takes 32 columns, one per lane.  The columns are dealt through a
+// permutation (index times `mult` modulo nB, mult coprime to nB) so that the
+// heavy columns of a skewed matrix, which sit together (or, in R-MAT, at
+// indices with few one bits), spread over the warps.  Columns with more than
+// 32 B entries are walked by the whole warp one after another, its loads
+// strided over the lanes; the others' entries are walked 32 at a time as one
+// flattened sequence (the owner of an entry is found by a search over the
+// lanes' entry offsets) and the Z^A_k of an owner's lanes are summed by a
+// segmented warp scan.  Per-bin statistics are summed over the warp before
+// one shared atomic per bin present.
+constexpr int kCountLong = 32;
+
 __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__restrict__ Brow,
                             const int64_t *__restrict__ Acp, int64_t nB, int64_t t, int64_t hmax, int64_t mrows,
-                            int64_t *__restrict__ op, int64_t *__restrict__ Ccp, Ctrl *ctrl) {
+                            int64_t mult, int64_t *__restrict__ op, int64_t *__restrict__ Ccp, Ctrl *ctrl) {
     __shared__ unsigned long long s_hist[NBINS];
     __shared__ unsigned long long s_max[NBINS];
     __shared__ unsigned long long s_binprod[NBINS];
@@ -57,22 +61,43 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
     int64_t *wop = s_op + (threadIdx.x & ~31);
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long mine = 0, cap = 0;
-    for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j0 < nB; j0 += nwarps * 32) {
-        const int64_t j = j0 + (int64_t)lane * nwarps;
-        const bool on = j < nB;
+    for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; g0 < nB; g0 += nwarps * 32) {
+        const int64_t g = g0 + lane;
+        const bool on = g < nB;
+        // mult < nB < 2^31 and g < nB: the product fits 63 bits
+        const int64_t j = on ? (int64_t)(((unsigned long long)g * (unsigned long long)mult) % (unsigned long long)nB)
+                             : 0;
         int64_t p0 = 0, nb = 0;
         if (on) {
             p0 = Bcp[j];
             nb = Bcp[j + 1] - p0;
         }
         wop[lane] = 0;
-        int64_t eincl = nb;
+        // long columns: the whole warp, one column at a time
+        unsigned longs = __ballot_sync(0xffffffffu, nb > kCountLong);
+        while (longs) {
+            const int c = __ffs(longs) - 1;
+            longs &= longs - 1u;
+            const int64_t pc = __shfl_sync(0xffffffffu, p0, c);
+            const int64_t nc = __shfl_sync(0xffffffffu, nb, c);
+            int64_t sz = 0;
+            for (int64_t p = pc + lane; p < pc + nc; p += 32) {
+                const int32_t k = Brow[p];
+                sz += Acp[k + 1] - Acp[k];
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) sz += __shfl_xor_sync(0xffffffffu, sz, d);
+            if (lane == c) wop[c] = sz;
+        }
+        // short columns: their entries as one flattened sequence
+        const int64_t ns = nb > kCountLong ? 0 : nb;
+        int64_t eincl = ns;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int64_t v = __shfl_up_sync(0xffffffffu, eincl, d);
             if (lane >= d) eincl += v;
         }
-        const int64_t eexcl = eincl - nb;
+        const int64_t eexcl = eincl - ns;
         const int64_t E = __shfl_sync(0xffffffffu, eincl, 31);
         __syncwarp();
         for (int64_t e0 = 0; e0 < E; e0 += 32) {
@@ -102,8 +127,9 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
             if (e < E && (lane == 31 || e + 1 >= E || cn != c)) wop[c] += z;
             __syncwarp();
         }
+        __syncwarp();
         const int64_t s = wop[lane];
-        int b = -1;
+    int b = -1;
         if (on) {
             op[j] = s;
             mine += (unsigned long long)s;
@@ -157,6 +183,22 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
         atomicAdd(&ctrl->products, s_prod);
         atomicAdd(&ctrl->capsum, s_cap);
     }
+}
+
+int64_t column_deal_mult(int64_t n) {
+    if (n <= 2) return 1;
+    auto gcd = [](int64_t a, int64_t b) {
+        while (b) {
+            const int64_t r = a % b;
+            a = b;
+            b = r;
+        }
+        return a;
+    };
+    int64_t m = (int64_t)((double)n * 0.6180339887498949);
+    if (m < 1) m = 1;
+    while (gcd(m, n) != 1) ++m;
+    return m % n == 0 ? 1 : m;
 }
 
 // Single pass: slot capacity min(Op_j, rows) of every column, written to

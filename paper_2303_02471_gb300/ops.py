@@ -84,7 +84,7 @@ class Config:
     dense_cache_bytes: Optional[int] = None
     side_streams: Optional[bool] = None
     test_wait_timeout: Optional[bool] = None
-    small_accumulator: Optional[str] = None  # "hash" or "esc"
+    small_accumulator: Optional[str] = None  # "hash", "esc" or "auto"
 
     def native(self) -> N.SpgConfig:
         c = N.SpgConfig()
@@ -99,7 +99,8 @@ class Config:
             if v is not None:
                 setattr(c, f, int(bool(v)))
         if self.small_accumulator is not None:
-            c.small_accumulator = {"hash": N.SPG_ACC_HASH, "esc": N.SPG_ACC_ESC}[self.small_accumulator]
+            c.small_accumulator = {"hash": N.SPG_ACC_HASH, "esc": N.SPG_ACC_ESC,
+                                   "auto": N.SPG_ACC_AUTO}[self.small_accumulator]
         return c
 
 

@@ -57,7 +57,7 @@ def test_status_strings_and_defaults(lib):
     c = N.SpgConfig()
     assert lib.spg_config_default(ctypes.byref(c)) == 0
     assert c.t == -1 and c.validate == 1 and c.hash_cta_max == 8192
-    assert c.side_streams == 1 and c.test_wait_timeout == 0
+    assert c.side_streams == 1 and c.test_wait_timeout == 0 and c.small_accumulator == N.SPG_ACC_AUTO
     assert lib.spg_config_default(None) == 1
 
 

@@ -503,3 +503,26 @@ def test_single_pass_workspace_too_small():
                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(cp.data_ptr()),
                                     ctypes.byref(nnz), ctypes.byref(h), ops._stream())
     assert N.STATUS[rc] == "SPG_ERR_WORKSPACE" and h.value is None
+
+
+# ------------------------------------------------ hash tables in both phases
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("seed", range(30))
+def test_hash_fuzz(seed, dtype):
+    A, B = synth.fuzz_pair(seed, dtype=dtype)
+    C, _ = _run(A, B, small_accumulator="hash")
+    assert_matches_oracle(C, A, B)
+
+
+@pytest.mark.parametrize("t", [None, 40, INF])
+def test_hash_rmat_every_bin(t):
+    A = synth.rmat(13, seed=2, col_cap=600)
+    C, plan = _run(A, A, t=t, hash_cta_max=1024, small_accumulator="hash")
+    assert sum(plan.info()["bins"][1:7]) > 0
+    assert_matches_oracle(C, A, A, nthreads=NCPU)
+
+
+def test_hash_workload2_random_full():
+    A, B = synth.workload(2)
+    C, _ = _run(A, B, small_accumulator="hash")
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
