@@ -315,6 +315,46 @@ spg_status spgemm_single_pass_copy(spg_plan *plan, const int64_t *C_colptr,
                                    int32_t *C_rowidx, void *C_values,
                                    spg_stream stream);
 
+/*
+ * Row-wise (CSR) form.  Section 2.1 notes that the method applies to rows of
+ * CSR matrices as well as to columns of CSC ones.  A CSR matrix's arrays
+ * (row pointers, column indices, values) are the CSC arrays of its
+ * transpose, and C^T = B^T A^T, so these calls run the column-wise product
+ * on (B^T, A^T): Op_j, bins and accumulators work on the rows of B and the
+ * output's row pointers, column indices (ascending in each row) and values
+ * are C in CSR.  Same conventions, ownership and errors as the CSC calls,
+ * with rows for columns:
+ *   A (m x k) and B (k x n) in CSR, device arrays; C_rowptr int64[m + 1];
+ *   spgemm_csr_backward gives dA on pattern(A) and dB on pattern(B).
+ * The plan belongs to the CSR calls (it holds the roles swapped).
+ */
+typedef struct {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    const int64_t *rowptr; /* device, nrows + 1 */
+    const int32_t *colidx; /* device, nnz */
+    const void *values;    /* device, nnz elements of `dtype` */
+    int32_t dtype;         /* spg_dtype */
+} spg_csr;
+
+spg_status spgemm_csr_workspace_size(const spg_csr *A, const spg_csr *B,
+                                     const spg_config *cfg, size_t *bytes);
+spg_status spgemm_csr_symbolic(spg_handle *handle, const spg_csr *A,
+                               const spg_csr *B, const spg_config *cfg,
+                               void *workspace, size_t ws_bytes,
+                               int64_t *C_rowptr, int64_t *nnzC,
+                               spg_plan **plan, spg_stream stream);
+spg_status spgemm_csr_numeric(spg_plan *plan, const spg_csr *A,
+                              const spg_csr *B, const int64_t *C_rowptr,
+                              int32_t *C_colidx, void *C_values,
+                              spg_stream stream);
+spg_status spgemm_csr_backward(spg_plan *plan, const spg_csr *A,
+                               const spg_csr *B, const int64_t *C_rowptr,
+                               const int32_t *C_colidx,
+                               const void *dC_values, void *dA_values,
+                               void *dB_values, spg_stream stream);
+
 /* Synchronise `stream` and report the first kernel-side error recorded in
  * the plan's workspace since spgemm_symbolic (SPG_OK if none). */
 spg_status spg_plan_check(spg_plan *plan, spg_stream stream);

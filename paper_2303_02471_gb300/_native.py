@@ -28,6 +28,11 @@ class SpgCsc(ctypes.Structure):
                 ("values", vp), ("dtype", i32)]
 
 
+class SpgCsr(ctypes.Structure):
+    _fields_ = [("nrows", i64), ("ncols", i64), ("nnz", i64), ("rowptr", vp), ("colidx", vp),
+                ("values", vp), ("dtype", i32)]
+
+
 class SpgConfig(ctypes.Structure):
     _fields_ = [("t", i64), ("hash_cta_max", i32), ("cta_threads", i32), ("validate", i32),
                 ("table_shrink", i32), ("scratch_cap_bytes", i64), ("dense_cache_bytes", i64),
@@ -57,6 +62,11 @@ SIGNATURES = {
                                  ctypes.POINTER(vp), vp]),
     "spgemm_single_pass_copy": (i32, [vp, vp, vp, vp, vp]),
     "spgemm_backward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "spgemm_csr_workspace_size": (i32, [vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "spgemm_csr_symbolic": (i32, [vp, vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.POINTER(i64),
+                                  ctypes.POINTER(vp), vp]),
+    "spgemm_csr_numeric": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+    "spgemm_csr_backward": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "spg_plan_check": (i32, [vp, vp]),
     "spg_plan_destroy": (i32, [vp]),
     "spg_plan_info": (i32, [vp, ctypes.POINTER(i32), vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),

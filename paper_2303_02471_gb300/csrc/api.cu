@@ -732,6 +732,43 @@ spg_status spgemm_backward(spg_plan *P, const spg_csc *A, const spg_csc *B, cons
     return SPG_OK;
 }
 
+// ------------------------------------------------------------ row-wise form
+// The CSC view of M^T for a CSR matrix M: the same arrays.
+static spg_csc csc_of_transpose(const spg_csr *M) {
+    return spg_csc{M->ncols, M->nrows, M->nnz, M->rowptr, M->colidx, M->values, M->dtype};
+}
+
+spg_status spgemm_csr_workspace_size(const spg_csr *A, const spg_csr *B, const spg_config *cfg, size_t *bytes) {
+    if (!A || !B) return SPG_ERR_INVALID;
+    const spg_csc Bt = csc_of_transpose(B), At = csc_of_transpose(A);
+    return spgemm_workspace_size(&Bt, &At, cfg, bytes);
+}
+
+spg_status spgemm_csr_symbolic(spg_handle *handle, const spg_csr *A, const spg_csr *B, const spg_config *cfg,
+                               void *workspace, size_t ws_bytes, int64_t *C_rowptr, int64_t *nnzC,
+                               spg_plan **plan, spg_stream stream) {
+    if (plan) *plan = nullptr;
+    if (!A || !B) return SPG_ERR_INVALID;
+    const spg_csc Bt = csc_of_transpose(B), At = csc_of_transpose(A);
+    return spgemm_symbolic(handle, &Bt, &At, cfg, workspace, ws_bytes, C_rowptr, nnzC, plan, stream);
+}
+
+spg_status spgemm_csr_numeric(spg_plan *plan, const spg_csr *A, const spg_csr *B, const int64_t *C_rowptr,
+                              int32_t *C_colidx, void *C_values, spg_stream stream) {
+    if (!A || !B) return SPG_ERR_INVALID;
+    const spg_csc Bt = csc_of_transpose(B), At = csc_of_transpose(A);
+    return spgemm_numeric(plan, &Bt, &At, C_rowptr, C_colidx, C_values, stream);
+}
+
+spg_status spgemm_csr_backward(spg_plan *plan, const spg_csr *A, const spg_csr *B, const int64_t *C_rowptr,
+                               const int32_t *C_colidx, const void *dC_values, void *dA_values, void *dB_values,
+                               spg_stream stream) {
+    if (!A || !B) return SPG_ERR_INVALID;
+    const spg_csc Bt = csc_of_transpose(B), At = csc_of_transpose(A);
+    // the product runs as B^T A^T: its first operand's gradient is dB
+    return spgemm_backward(plan, &Bt, &At, C_rowptr, C_colidx, dC_values, dB_values, dA_values, stream);
+}
+
 spg_status spg_plan_check(spg_plan *P, spg_stream stream) {
     if (!P) return SPG_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -72,6 +72,35 @@ class CscMatrix:
 
 
 @dataclass
+class CsrMatrix:
+    """A CSR matrix in device memory (the row-wise form of Section 2.1)."""
+
+    nrows: int
+    ncols: int
+    rowptr: torch.Tensor            # int64 [nrows + 1]
+    colidx: torch.Tensor            # int32 [nnz]
+    values: Optional[torch.Tensor]  # float64 / float32 [nnz] or None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.shape[0])
+
+    @property
+    def dtype(self):
+        return self.values.dtype if self.values is not None else torch.float64
+
+    @property
+    def device(self):
+        return self.rowptr.device
+
+    @staticmethod
+    def from_host(nrows, ncols, rowptr, colidx, values, device="cuda") -> "CsrMatrix":
+        return CsrMatrix(int(nrows), int(ncols), torch.as_tensor(rowptr, dtype=torch.int64).to(device),
+                         torch.as_tensor(colidx, dtype=torch.int32).to(device),
+                         torch.as_tensor(values).to(device))
+
+
+@dataclass
 class Config:
     """Mirror of spg_config; None fields keep the library defaults."""
 
@@ -341,6 +370,50 @@ def spgemm_single_pass(A: CscMatrix, B: CscMatrix, config: Optional[Config] = No
     N.check(N.lib().spgemm_single_pass_copy(plan.handle, _ptr(colptr), _ptr(rowidx), _ptr(values), _stream()),
             "spgemm_single_pass_copy")
     return CscMatrix(A.nrows, B.ncols, colptr, rowidx, values), plan
+
+
+def _csr(M: CsrMatrix, dtype=None) -> N.SpgCsr:
+    dt = dtype if dtype is not None else M.dtype
+    for t, want in ((M.rowptr, torch.int64), (M.colidx, torch.int32)):
+        if t.dtype != want or not t.is_contiguous() or not t.is_cuda:
+            raise TypeError("CSR index arrays must be contiguous CUDA int64 rowptr / int32 colidx")
+    return N.SpgCsr(M.nrows, M.ncols, M.nnz, M.rowptr.data_ptr(), _ptr(M.colidx), _ptr(M.values), _DT[dt])
+
+
+def spgemm_csr(A: CsrMatrix, B: CsrMatrix, config: Optional[Config] = None,
+               lib_handle: Optional[Handle] = None):
+    """C = A B with A, B and C in CSR (row-wise form).  Returns (C, plan)."""
+    config = config or Config()
+    hd = lib_handle if lib_handle is not None else handle(A.device)
+    cfg = config.native()
+    cA, cB = _csr(A), _csr(B, A.dtype)
+    nbytes = ctypes.c_size_t()
+    N.check(N.lib().spgemm_csr_workspace_size(ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(cfg),
+                                              ctypes.byref(nbytes)), "spgemm_csr_workspace_size")
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=A.device)
+    rowptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=A.device)
+    nnz = ctypes.c_int64()
+    h = ctypes.c_void_p()
+    N.check(N.lib().spgemm_csr_symbolic(hd.ptr, ctypes.byref(cA), ctypes.byref(cB), ctypes.byref(cfg), _ptr(ws),
+                                        ws.numel(), _ptr(rowptr), ctypes.byref(nnz), ctypes.byref(h), _stream()),
+            "spgemm_csr_symbolic")
+    plan = Plan(h, ws, A, B, rowptr, nnz.value, config, hd)
+    colidx = torch.empty(nnz.value, dtype=torch.int32, device=A.device)
+    values = torch.empty(nnz.value, dtype=A.dtype, device=A.device)
+    N.check(N.lib().spgemm_csr_numeric(plan.handle, ctypes.byref(cA), ctypes.byref(cB), _ptr(rowptr),
+                                       _ptr(colidx), _ptr(values), _stream()), "spgemm_csr_numeric")
+    return CsrMatrix(A.nrows, B.ncols, rowptr, colidx, values), plan
+
+
+def spgemm_csr_backward(plan: Plan, A: CsrMatrix, B: CsrMatrix, C: CsrMatrix, dC: torch.Tensor):
+    """(dA, dB) on the stored entries of CSR A and B for dC on pattern(C)."""
+    dA = torch.empty(A.nnz, dtype=A.dtype, device=A.device)
+    dB = torch.empty(B.nnz, dtype=A.dtype, device=A.device)
+    dC = dC.contiguous()
+    N.check(N.lib().spgemm_csr_backward(plan.handle, ctypes.byref(_csr(A)), ctypes.byref(_csr(B)), _ptr(C.rowptr),
+                                        _ptr(C.colidx), _ptr(dC), _ptr(dA), _ptr(dB), _stream()),
+            "spgemm_csr_backward")
+    return dA, dB
 
 
 def spgemm_backward(plan: Plan, A: CscMatrix, B: CscMatrix, C: CscMatrix, dC: torch.Tensor,

@@ -42,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_struct_layouts():
     from paper_2303_02471_gb300 import _native as N
-    assert ctypes.sizeof(N.SpgCsc) == 56
+    assert ctypes.sizeof(N.SpgCsc) == 56 and ctypes.sizeof(N.SpgCsr) == 56
     assert N.SpgCsc.values.offset == 40 and N.SpgCsc.dtype.offset == 48
     assert ctypes.sizeof(N.SpgConfig) == 56
     assert N.SpgConfig.dense_cache_bytes.offset == 32
