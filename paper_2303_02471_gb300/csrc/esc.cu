@@ -37,14 +37,14 @@ namespace spg {
 template <bool VALS, typename VT>
 struct EscWarp {
     uint32_t key[2][kEscTile];
-    uint32_t cnt[1 << kEscRadixBits];
+    uint32_t cnt[2][1 << kEscRadixBits];
     int32_t hstart[32];
 };
 template <typename VT>
 struct EscWarp<true, VT> {
     uint32_t key[2][kEscTile];
     VT val[kEscTile];
-    uint32_t cnt[1 << kEscRadixBits];
+    uint32_t cnt[2][1 << kEscRadixBits];
     int32_t hstart[32];
     uint8_t idx[2][kEscTile];
 };
@@ -57,7 +57,7 @@ __host__ __device__ constexpr size_t esc_warp_bytes() {
 // CTAs per SM the kernels are built for (registers): the value-carrying
 // form holds more shared memory per warp.
 template <bool VALS>
-constexpr int esc_min_blocks() { return VALS ? 5 : 6; }
+constexpr int esc_min_blocks() { return VALS ? 4 : 4; }
 
 // Lane holding the owner of position q among 32 lanes with non-decreasing
 // exclusive offsets `excl` (the last lane whose offset is <= q).
@@ -122,7 +122,12 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
         }
         const int eexcl = eincl - nb;
         const int E = __shfl_sync(0xffffffffu, eincl, 31);
-        // ---- expand: 32 B entries per round, then their products
+        // ---- expand: 32 B entries per round, then their products; the
+        // first pass's digits are counted as the keys are written
+        constexpr uint32_t DM = (1u << kEscRadixBits) - 1u;
+#pragma unroll
+        for (int b = lane; b < (1 << kEscRadixBits); b += 32) S.cnt[0][b] = 0u;
+        __syncwarp();
         int n = 0;
         bool over = false;
         for (int e0 = 0; e0 < E; e0 += 32) {
@@ -163,7 +168,9 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 if (q < total) {
                     const int64_t qa = a0s + (q - exs);
                     const int32_t row = ld_keep(ops.Arow + qa, pol);
-                    S.key[0][n + q] = ((uint32_t)cs << e.rb) | ((uint32_t)row & rowmask);
+                    const uint32_t key = ((uint32_t)cs << e.rb) | ((uint32_t)row & rowmask);
+                    S.key[0][n + q] = key;
+                    atomicAdd(&S.cnt[0][key & DM], 1u);
                     if constexpr (VALS) {
                         S.val[n + q] = ld_keep(ops.Aval + qa, pol) * bs;
                         S.idx[0][n + q] = (uint8_t)(n + q);
@@ -177,23 +184,22 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
             continue;
         }
         __syncwarp();
-        // ---- sort: stable LSD radix over the key bits
+        // ---- sort: stable LSD radix over the key bits.  The counts of pass
+        // p + 1's digits are taken while pass p scatters the keys.
         int cur = 0;
+        const unsigned vm_all = 0xffffffffu;
         for (int pass = 0; pass < e.passes; ++pass) {
             const int sh = pass * kEscRadixBits;
-#pragma unroll
-            for (int b = lane; b < (1 << kEscRadixBits); b += 32) S.cnt[b] = 0u;
-            __syncwarp();
-            for (int i = lane; i < n; i += 32)
-                atomicAdd(&S.cnt[(S.key[cur][i] >> sh) & ((1u << kEscRadixBits) - 1u)], 1u);
-            __syncwarp();
+            uint32_t *cnt = S.cnt[pass & 1];
+            uint32_t *ncnt = S.cnt[(pass + 1) & 1];
+            const bool more = pass + 1 < e.passes;
             {  // exclusive scan of the buckets: lane l owns the 8 buckets from 8 l
                 constexpr int PER = (1 << kEscRadixBits) / 32;
                 uint32_t v[PER];
                 uint32_t run = 0;
 #pragma unroll
                 for (int u = 0; u < PER; ++u) {
-                    v[u] = S.cnt[lane * PER + u];
+                    v[u] = cnt[lane * PER + u];
                     const uint32_t x = v[u];
                     v[u] = run;
                     run += x;
@@ -206,7 +212,10 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 }
                 const uint32_t off = incl - run;
 #pragma unroll
-                for (int u = 0; u < PER; ++u) S.cnt[lane * PER + u] = v[u] + off;
+                for (int u = 0; u < PER; ++u) cnt[lane * PER + u] = v[u] + off;
+                if (more)
+#pragma unroll
+                    for (int u = 0; u < PER; ++u) ncnt[lane * PER + u] = 0u;
             }
             __syncwarp();
             for (int i0 = 0; i0 < n; i0 += 32) {
@@ -215,20 +224,26 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 const uint32_t k = valid ? S.key[cur][i] : 0u;
                 uint8_t ix = 0;
                 if constexpr (VALS) ix = valid ? S.idx[cur][i] : (uint8_t)0;
-                // lanes past n get digits of their own, so they never share a
-                // group with a key
-                const uint32_t dg = valid ? ((k >> sh) & ((1u << kEscRadixBits) - 1u)) : (0x10000u + lane);
-                const unsigned same = __match_any_sync(0xffffffffu, dg);
-                const int leader = __ffs(same) - 1;
+                const uint32_t dg = (k >> sh) & DM;
+                // the lanes holding the same digit: one ballot per digit bit
+                unsigned same = __ballot_sync(vm_all, valid);
+#pragma unroll
+                for (int b = 0; b < kEscRadixBits; ++b) {
+                    const bool bit = (dg >> b) & 1u;
+                    const unsigned bb = __ballot_sync(vm_all, bit);
+                    same &= bit ? bb : ~bb;
+                }
+                const int leader = __ffs(same | (1u << lane)) - 1;
                 uint32_t at = 0;
                 if (valid && lane == leader) {
-                    at = S.cnt[dg];
-                    S.cnt[dg] = at + (uint32_t)__popc(same);
+                    at = cnt[dg];
+                    cnt[dg] = at + (uint32_t)__popc(same);
                 }
                 at = __shfl_sync(0xffffffffu, at, leader) + (uint32_t)__popc(same & lt);
                 if (valid) {
                     S.key[cur ^ 1][at] = k;
                     if constexpr (VALS) S.idx[cur ^ 1][at] = ix;
+                    if (more) atomicAdd(&ncnt[(k >> (sh + kEscRadixBits)) & DM], 1u);
                 }
                 __syncwarp();
             }
