@@ -575,15 +575,15 @@ def run_ours(args, rank, world):
     serial = serial_bin_times(A_h, B_h, dev, cfg, flush)
     roof, per_bin = product_report(prod, res, serial, peak, peak_kind, args, w)
 
+    # end to end through host buffers, right after the device-timed steps
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, A_h, B_h, products, prod, dev, world)
     sp_main = None
     if not args.no_aux:
         sp_main = time_single_pass(A_h, B_h, dev, cfg, max(3, min(args.steps, 10)), 3, flush)
         sp_main["value"] = round(2.0 * products / (sp_main["ms_per_step"] * 1e-3) / 1e9, 3)
         sp_main["unit"] = "GFLOP/s"
-    # end to end through host buffers
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(args, A_h, B_h, products, prod, dev, world)
 
     line = None
     if rank == 0:
