@@ -829,8 +829,20 @@ def run_t_sweep(args, dev, flush):
             key = "inf" if t == INF else ("default(%d)" % prod.t if t is None else str(t))
             row[key] = round(2.0 * prod.products / (ms * 1e-3) / 1e9, 3)
             del prod
+        # the product autotuner's pick (t, table limit, CTA size, light-column accumulator)
+        dA = ops.CscMatrix.from_host(A_h, device=dev)
+        dB = dA if B_h is A_h else ops.CscMatrix.from_host(B_h, device=dev)
+        tuned, _ = autotune.tune_product(dA, dB, repeats=1)
+        del dA, dB
+        prod = Product(A_h, B_h, dev, tuned)
+        res = time_steps(prod, 3, 1, flush, bin_timing=False)
+        row["autotuned"] = round(2.0 * prod.products / (float(np.median(res["step"])) * 1e-3) / 1e9, 3)
+        del prod
         base = row["0"]
-        out[str(k)] = {"GFLOPs": row, "speedup_vs_t0": {k2: round(v / base, 3) for k2, v in row.items()}}
+        out[str(k)] = {"GFLOPs": row, "speedup_vs_t0": {k2: round(v / base, 3) for k2, v in row.items()},
+                       "autotuned_config": {"t": tuned.t, "hash_cta_max": tuned.hash_cta_max,
+                                            "cta_threads": tuned.cta_threads,
+                                            "small_accumulator": tuned.small_accumulator}}
     pairs = synth.batch_pairs(512, seed=0)
     As = [ops.CscMatrix.from_host(A, device=dev) for A, _ in pairs]
     Bs = [ops.CscMatrix.from_host(B, device=dev) for _, B in pairs]

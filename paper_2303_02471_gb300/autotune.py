@@ -1,6 +1,8 @@
-"""Autotuner of the batched form: picks the H-HASH threshold t, the largest
-shared-memory hash table (hash_cta_max) and the threads per CTA of the
-persistent kernels by timing candidate configurations on the batch itself.
+"""Autotuners: for a batch (the H-HASH threshold t, the largest shared-memory
+hash table hash_cta_max and the threads per CTA of the persistent kernels)
+and for a single product (t, hash_cta_max, the threads per CTA of the CTA
+bins and the accumulator of the light columns), each by timing candidate
+configurations on the products themselves.
 
 The paper fixes t = 40 for its vector unit and studies t, b_min and b_max by
 hand (Section 5.4); here the choice is measured on the GPU and cached per GPU
@@ -94,6 +96,88 @@ def tune(As, Bs, grid: Optional[dict] = None, repeats: int = 2, cache: Optional[
         else:
             err = None
         results.append({"config": {"t": t, "hash_cta_max": hmax, "cta_threads": thr}, "ms": ms, "error": err})
+    ok = [r for r in results if np.isfinite(r["ms"])]
+    if not ok:
+        raise RuntimeError("no candidate configuration ran")
+    best = min(ok, key=lambda r: r["ms"])
+    entry = {"config": best["config"], "ms": best["ms"], "candidates": results}
+    table[key] = entry
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return Config(**best["config"]), entry
+
+
+PRODUCT_GRID = {
+    "t": [65, 129, 257, 513, 1025, None],
+    "hash_cta_max": [2048, 8192],
+    "cta_threads": [512, 1024],
+    "small_accumulator": ["hash", "esc", "auto"],
+}
+
+
+def product_signature(A, B) -> str:
+    """GPU model, shapes, nnz, dtype and log2 histograms of the column lengths
+    of A and B (the quantities Op_j and the bins follow from)."""
+    dev = torch.cuda.get_device_name(A.device)
+
+    def hist(M):
+        z = torch.diff(M.colptr).clamp(min=1).double().log2().floor().long().cpu().numpy()
+        return np.bincount(z, minlength=32).tolist()
+    key = json.dumps([dev, "product", A.nrows, A.ncols, B.ncols, A.nnz, B.nnz, str(A.dtype), hist(A), hist(B)])
+    return hashlib.sha1(key.encode()).hexdigest()
+
+
+def _time_product(A, B, cfg: Config, repeats: int) -> float:
+    C, plan = ops.spgemm(A, B, cfg)
+    plan.check()
+    plan.destroy()
+    stream = torch.cuda.current_stream()
+    best = float("inf")
+    for _ in range(repeats):
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        _, _, p = ops.spgemm_symbolic(A, B, cfg)
+        ops.spgemm_numeric(p, A, B, C.rowidx, C.values)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+        p.destroy()
+    return best
+
+
+def tune_product(A, B, grid: Optional[dict] = None, repeats: int = 2, cache: Optional[str] = None,
+                 refresh: bool = False):
+    """Best Config for one product C = A B, timed as a whole step (symbolic
+    and numeric phases) per candidate; cached per GPU model and pattern
+    signature.  Returns (config, report)."""
+    path = _cache_path(cache)
+    key = product_signature(A, B)
+    table = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if key in table and not refresh:
+        return Config(**table[key]["config"]), table[key]
+    grid = grid or PRODUCT_GRID
+    names = sorted(grid)
+    results = []
+    for values in itertools.product(*(grid[n] for n in names)):
+        conf = dict(zip(names, values))
+        try:
+            ms = _time_product(A, B, Config(**conf), repeats)
+            err = None
+        except RuntimeError as e:  # a configuration the product does not support
+            ms, err = float("inf"), str(e)
+        results.append({"config": conf, "ms": ms, "error": err})
     ok = [r for r in results if np.isfinite(r["ms"])]
     if not ok:
         raise RuntimeError("no candidate configuration ran")

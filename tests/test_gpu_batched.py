@@ -210,3 +210,20 @@ def test_autotune_chooses_and_caches(tmp_path):
     Cs, plan = ops.spgemm_batched(As, Bs, cfg)
     for (A, B), C in zip(pairs, Cs):
         assert_matches_oracle(C, A, B)
+
+
+def test_product_autotune_chooses_and_caches(tmp_path):
+    """The single-product autotuner times its grid on the product, caches the
+    pick per pattern signature, and its configuration gives the oracle's C."""
+    from paper_2303_02471_gb300 import autotune, ops
+    A = synth.rmat(12, seed=3, col_cap=400)
+    dA = upload(A)
+    path = str(tmp_path / "tune.json")
+    grid = {"t": [65, None], "hash_cta_max": [2048], "cta_threads": [512], "small_accumulator": ["hash", "esc"]}
+    cfg, rep = autotune.tune_product(dA, dA, grid=grid, repeats=1, cache=path)
+    assert len(rep["candidates"]) == 4 and all(r["error"] is None for r in rep["candidates"])
+    cfg2, rep2 = autotune.tune_product(dA, dA, grid=grid, repeats=1, cache=path)
+    assert rep2["config"] == rep["config"]
+    C, plan = ops.spgemm(dA, dA, cfg)
+    plan.check()
+    assert_matches_oracle(C, A, A)
