@@ -305,13 +305,17 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
     const int32_t ns = (int32_t)(nn < cap ? nn : cap);
     VT *gacc = Cval + c0;
     int32_t *crow = Crow + c0;
+    // the extraction stages rows in the walk's scratch, free once cta_walk
+    // has returned (it ends with a barrier): 20 bytes per thread
+    static_assert(kVisitStage * 4 <= 32 * (16 + sizeof(float)), "visit staging exceeds the walk scratch");
+    int32_t *stage = reinterpret_cast<int32_t *>(w.a0);
     for (int32_t i = threadIdx.x; i < ns; i += blockDim.x) s_acc[i] = VT(0);
     for (int32_t i = ns + threadIdx.x; i < n32; i += blockDim.x) gacc[i] = VT(0);
     __syncthreads();
     if (ns == 0) {  // every sum in C (uniform over the CTA)
         cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                            [&](int32_t row, VT prod) { atomicAdd(&gacc[bitmap_rank(bm, row)], prod); });
-        cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) { crow[rank] = o.crow(row); });
+        cta_bitmap_visit(bm, W, true, s_next, stage, [&](int32_t row, int32_t rank) { crow[rank] = o.crow(row); });
     } else {
         cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                            [&](int32_t row, VT prod) {
@@ -319,7 +323,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                if (r < ns) atomicAdd(&s_acc[r], prod);
                                else atomicAdd(&gacc[r], prod);
                            });
-        cta_bitmap_visit(bm, W, true, s_next, [&](int32_t row, int32_t rank) {
+        cta_bitmap_visit(bm, W, true, s_next, stage, [&](int32_t row, int32_t rank) {
             crow[rank] = o.crow(row);
             if (rank < ns) gacc[rank] = s_acc[rank];
         });

@@ -614,60 +614,66 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W64, con
 // take groups of kVisitGroup chunks of 32 words, the first group by warp
 // index and the next ones from the shared counter *s_next, which must hold
 // kVisitGroup * (number of warps) before a barrier that precedes the call
-// (one shared atomic per 4096 rows).  In a chunk whose words hold at most
-// kVisitLight bits each, every lane visits its own word; otherwise the warp
-// expands the chunk's S bits 32 ranks at a time: lane l takes rank
-// y0 + o (o = round * 32 + l), finds the word holding it by a search over
-// the words' prefix counts and the bit by select_bit.  So a dense stretch of
-// rows (the hub rows of a power-law matrix) costs no lane serial steps and
-// its stores are coalesced.  Clears the bits when `clear`.  No barrier
-// inside.
+// (one shared atomic per 4096 rows).  Every lane holds one word of a chunk.
+// In a chunk whose words hold at most kVisitLight bits each, every lane
+// visits its own bits.  Otherwise the lanes write their rows, in rank order,
+// into the warp's kVisitStage-entry slice of `stage` (rank minus the chunk's
+// first rank is the slot), and the warp then calls f on consecutive slots,
+// one per lane, so that a fuller chunk costs each lane one step per bit and
+// its stores are coalesced; a chunk of more than kVisitStage bits goes
+// through the slice in pieces.  stage: kVisitStage ints per warp of shared
+// memory that nothing else uses during the call.  Clears the bits when
+// `clear`.  No barrier inside.
 constexpr int kVisitLight = 3;
 // Chunks of 32 words a warp takes per grab in cta_bitmap_visit.
 constexpr int kVisitGroup = 4;
+// Rows a warp stages per piece of a chunk in cta_bitmap_visit.
+constexpr int kVisitStage = 160;
 
 template <typename F>
-__device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W64, bool clear, unsigned *s_next, F &&f) {
+__device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W64, bool clear, unsigned *s_next,
+                                                 int32_t *stage, F &&f) {
     // m < 2^31, so words, chunks and ranks all fit 32-bit indices
     const int W = (int)W64;
     const int lane = threadIdx.x & 31;
     const int nchunks = (W + 31) >> 5;
+    int32_t *slots = stage + (threadIdx.x >> 5) * kVisitStage;
     for (int g = (threadIdx.x >> 5) * kVisitGroup; g < nchunks;) {
         const int gend = g + kVisitGroup < nchunks ? g + kVisitGroup : nchunks;
         for (int c = g; c < gend; ++c) {
-        const int wd = (c << 5) + lane;
-        const uint2 v = wd < W ? bm[wd] : make_uint2(0u, 0u);
-        if (clear && v.x) bm[wd].x = 0u;
-        const int cnt = __popc(v.x);
-        const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
-        if (maxc <= kVisitLight) {
+            const int wd = (c << 5) + lane;
+            const uint2 v = wd < W ? bm[wd] : make_uint2(0u, 0u);
+            if (clear && v.x) bm[wd].x = 0u;
+            const int cnt = __popc(v.x);
+            const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
             const int32_t row0 = wd << 5;
             uint32_t bits = v.x;
-            int32_t rank = (int32_t)v.y;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1u;
-                f(row0 + b, rank++);
-            }
-        } else {
-            // lane 0's word always exists; words past W never hold rank o < S
-            const uint32_t y0 = __shfl_sync(0xffffffffu, v.y, 0);
-            const int excl = wd < W ? (int)(v.y - y0) : 0x3fffffff;
-            const int S = (int)__reduce_max_sync(0xffffffffu, wd < W ? (unsigned)(excl + cnt) : 0u);
-            const int32_t crow = c << 10;
-            for (int o0 = 0; o0 < S; o0 += 32) {
-                const int o = o0 + lane;
-                int sl = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int ex = __shfl_sync(0xffffffffu, excl, sl + step);
-                    if (ex <= o) sl += step;
+            if (maxc <= kVisitLight) {
+                int32_t rank = (int32_t)v.y;
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    f(row0 + b, rank++);
                 }
-                const uint32_t bw = __shfl_sync(0xffffffffu, v.x, sl);
-                const int k = o - __shfl_sync(0xffffffffu, excl, sl);
-                if (o < S) f(crow + (sl << 5) + select_bit(bw, k), (int32_t)y0 + o);
+                continue;
             }
-        }
+            // lane 0's word always exists; lanes past W hold no bits
+            const uint32_t y0 = __shfl_sync(0xffffffffu, v.y, 0);
+            int pos = wd < W ? (int)(v.y - y0) : 0;
+            const int S = (int)__reduce_max_sync(0xffffffffu, (unsigned)(pos + cnt));
+            for (int base = 0; base < S; base += kVisitStage) {
+                const int lim = base + kVisitStage;
+                while (bits && pos < lim) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    slots[pos - base] = row0 + b;
+                    ++pos;
+                }
+                __syncwarp();
+                const int end = S < lim ? S : lim;
+                for (int o = base + lane; o < end; o += 32) f(slots[o - base], (int32_t)y0 + o);
+                __syncwarp();
+            }
         }
         unsigned nc = 0;
         if (lane == 0) nc = atomicAdd(s_next, (unsigned)kVisitGroup);
