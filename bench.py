@@ -92,8 +92,8 @@ def peaks():
 # algorithmic bytes.  Valid only for the kernel sources it was taken with:
 # the hash below covers the files that define that kernel, and any change
 # there reports null.
-MEASURED_TRAFFIC = {"bin": 13, "scale": 17, "bytes": 421188608 + 1972065000, "algorithmic_bytes": 5313831440,
-                    "sources_sha256_16": "66c2d6fec46d4fdb",
+MEASURED_TRAFFIC = {"bin": 13, "scale": 17, "bytes": 421671680 + 1980509696, "algorithmic_bytes": 5313831440,
+                    "sources_sha256_16": "771875f20125ae99",
                     "sources": ("spgemm_internal.cuh", "kernels.cuh", "columns.cuh", "numeric.cu")}
 
 

@@ -302,7 +302,9 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
     }
     // nn <= m < 2^31: positions are 32-bit
     const int32_t n32 = (int32_t)nn;
-    const int32_t ns = (int32_t)(nn < cap ? nn : cap);
+    // double sums always go to C in place (cap is 0 for them): a compile-time
+    // 0 drops the shared-memory path and its registers from that kernel
+    const int32_t ns = sizeof(VT) == 8 ? 0 : (int32_t)(nn < cap ? nn : cap);
     VT *gacc = Cval + c0;
     int32_t *crow = Crow + c0;
     // the extraction stages rows in the walk's scratch, free once cta_walk
@@ -313,11 +315,11 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
     for (int32_t i = ns + threadIdx.x; i < n32; i += blockDim.x) gacc[i] = VT(0);
     __syncthreads();
     if (ns == 0) {  // every sum in C (uniform over the CTA)
-        cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
+        cta_walk<true, VT, kWalkAhead>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                            [&](int32_t row, VT prod) { atomicAdd(&gacc[bitmap_rank(bm, row)], prod); });
         cta_bitmap_visit(bm, W, true, s_next, stage, [&](int32_t row, int32_t rank) { crow[rank] = o.crow(row); });
     } else {
-        cta_walk<true, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
+        cta_walk<true, VT, kWalkAhead>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                            [&](int32_t row, VT prod) {
                                const int32_t r = bitmap_rank(bm, row);
                                if (r < ns) atomicAdd(&s_acc[r], prod);

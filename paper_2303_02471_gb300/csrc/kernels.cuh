@@ -118,6 +118,11 @@ constexpr int kWalkBatch = 4;
 // Entries whose A column has at least this many entries are walked one
 // 32-product window at a time with a single owner per window.
 constexpr int kLongEntry = 32;
+// Windows of a long entry whose gathers are in flight while one is consumed
+// in the value walk of the dense bin (cta_walk's AHEAD; other callers keep
+// one): four 256-thread CTAs per SM leave 64 registers a thread, which hold
+// three without spilling.
+constexpr int kWalkAhead = 3;
 
 // Inclusive block scan of four int32 counters packed as two int64 lanes
 // (each half < 2^31); totals returned.  Two barriers.
@@ -213,14 +218,14 @@ __device__ __forceinline__ WalkSmem<VT> carve_walk(unsigned char *p) {
 // over products, not B entries); kWalkBatch windows are gathered before any
 // product is consumed.  f(row, product) per product.  Contains barriers:
 // every thread of the CTA must call it.
-template <bool VALS, typename VT, typename F>
+template <bool VALS, typename VT, int AHEAD = 1, typename F>
 __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const int32_t *__restrict__ Arow,
                                          const VT *__restrict__ Aval, const int32_t *__restrict__ Brow,
                                          const VT *__restrict__ Bval, int64_t p0, int64_t p1,
                                          const WalkSmem<VT> &w, F &&f) {
-    // windows gathered per lane before any is consumed: with values, one at
-    // a time measured fastest (the warps of two CTAs per SM give the memory
-    // parallelism, and the loop stays small enough not to spill)
+    // windows gathered per lane before any is consumed: with values, short
+    // entries take one at a time (the loop stays small enough not to spill)
+    // and long ones keep a queue of AHEAD windows in flight
     constexpr int UB = VALS ? 1 : kWalkBatch;
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
@@ -284,18 +289,31 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                         const VT *vp = VALS ? Aval + a0 : nullptr;
                         const VT b = VALS ? w.bv[li] : VT(0);
                         const int i1 = (e_end - e_key) << 5;
-                        // one window ahead: the next window's gathers are in
-                        // flight while this one is consumed
+                        // a register queue of AHEAD windows: while one is
+                        // consumed, the gathers of the next AHEAD are in flight
                         int idx = ((win - e_key) << 5) + lane;
-                        int32_t row = idx < e_z ? ld_keep(rp + idx, pol) : -1;
-                        VT av = VALS && idx < e_z ? ld_keep(vp + idx, pol) : VT(0);
+                        int32_t rq[AHEAD];
+                        VT vq[AHEAD];
+#pragma unroll
+                        for (int d = 0; d < AHEAD; ++d) {
+                            const int q = idx + 32 * d;
+                            const bool in = q < i1 && q < e_z;
+                            rq[d] = in ? ld_keep(rp + q, pol) : -1;
+                            vq[d] = VALS && in ? ld_keep(vp + q, pol) : VT(0);
+                        }
                         for (; idx < i1; idx += 32) {
-                            const int nx = idx + 32;
-                            const int32_t row_n = nx < i1 && nx < e_z ? ld_keep(rp + nx, pol) : -1;
-                            const VT av_n = VALS && nx < i1 && nx < e_z ? ld_keep(vp + nx, pol) : VT(0);
-                            if (row >= 0) f(row, VALS ? av * b : VT(0));
-                            row = row_n;
-                            av = av_n;
+                            const int nx = idx + 32 * AHEAD;
+                            const bool in = nx < i1 && nx < e_z;
+                            const int32_t rn = in ? ld_keep(rp + nx, pol) : -1;
+                            const VT vn = VALS && in ? ld_keep(vp + nx, pol) : VT(0);
+                            if (rq[0] >= 0) f(rq[0], VALS ? vq[0] * b : VT(0));
+#pragma unroll
+                            for (int d = 0; d + 1 < AHEAD; ++d) {
+                                rq[d] = rq[d + 1];
+                                vq[d] = vq[d + 1];
+                            }
+                            rq[AHEAD - 1] = rn;
+                            vq[AHEAD - 1] = vn;
                         }
                         win = e_end;
                     }
