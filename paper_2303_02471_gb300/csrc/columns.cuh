@@ -317,7 +317,8 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
     if (ns == 0) {  // every sum in C (uniform over the CTA)
         cta_walk<true, VT, kWalkAhead>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                            [&](int32_t row, VT prod) { atomicAdd(&gacc[bitmap_rank(bm, row)], prod); });
-        cta_bitmap_visit(bm, W, true, s_next, stage, [&](int32_t row, int32_t rank) { crow[rank] = o.crow(row); });
+        cta_bitmap_visit(bm, W, true, s_next, stage, [&](int32_t row) { return o.crow(row); },
+                         [&](int32_t rank, int32_t r) { crow[rank] = r; });
     } else {
         cta_walk<true, VT, kWalkAhead>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                            [&](int32_t row, VT prod) {
@@ -325,10 +326,11 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
                                if (r < ns) atomicAdd(&s_acc[r], prod);
                                else atomicAdd(&gacc[r], prod);
                            });
-        cta_bitmap_visit(bm, W, true, s_next, stage, [&](int32_t row, int32_t rank) {
-            crow[rank] = o.crow(row);
-            if (rank < ns) gacc[rank] = s_acc[rank];
-        });
+        cta_bitmap_visit(bm, W, true, s_next, stage, [&](int32_t row) { return o.crow(row); },
+                         [&](int32_t rank, int32_t r) {
+                             crow[rank] = r;
+                             if (rank < ns) gacc[rank] = s_acc[rank];
+                         });
     }
     __syncthreads();
     return true;

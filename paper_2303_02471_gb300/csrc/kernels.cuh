@@ -118,11 +118,10 @@ constexpr int kWalkBatch = 4;
 // Entries whose A column has at least this many entries are walked one
 // 32-product window at a time with a single owner per window.
 constexpr int kLongEntry = 32;
-// Windows of a long entry whose gathers are in flight while one is consumed
-// in the value walk of the dense bin (cta_walk's AHEAD; other callers keep
-// one): four 256-thread CTAs per SM leave 64 registers a thread, which hold
-// three without spilling.
-constexpr int kWalkAhead = 3;
+// Windows of a long entry in the register ring of the dense bin's value
+// walk (cta_walk's AHEAD; other callers keep one): four 256-thread CTAs per
+// SM leave 64 registers a thread, which hold five without spilling.
+constexpr int kWalkAhead = 5;
 
 // Inclusive block scan of four int32 counters packed as two int64 lanes
 // (each half < 2^31); totals returned.  Two barriers.
@@ -225,7 +224,7 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                                          const WalkSmem<VT> &w, F &&f) {
     // windows gathered per lane before any is consumed: with values, short
     // entries take one at a time (the loop stays small enough not to spill)
-    // and long ones keep a queue of AHEAD windows in flight
+    // and long ones keep a ring of AHEAD windows in flight
     constexpr int UB = VALS ? 1 : kWalkBatch;
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
@@ -289,8 +288,11 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                         const VT *vp = VALS ? Aval + a0 : nullptr;
                         const VT b = VALS ? w.bv[li] : VT(0);
                         const int i1 = (e_end - e_key) << 5;
-                        // a register queue of AHEAD windows: while one is
-                        // consumed, the gathers of the next AHEAD are in flight
+                        // a ring of AHEAD windows in registers: slot d is
+                        // consumed and refilled with the window AHEAD
+                        // further on, so the gathers of the other slots stay
+                        // in flight (the loop is unrolled by AHEAD, so the
+                        // slots never move between registers)
                         int idx = ((win - e_key) << 5) + lane;
                         int32_t rq[AHEAD];
                         VT vq[AHEAD];
@@ -301,19 +303,15 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                             rq[d] = in ? ld_keep(rp + q, pol) : -1;
                             vq[d] = VALS && in ? ld_keep(vp + q, pol) : VT(0);
                         }
-                        for (; idx < i1; idx += 32) {
-                            const int nx = idx + 32 * AHEAD;
-                            const bool in = nx < i1 && nx < e_z;
-                            const int32_t rn = in ? ld_keep(rp + nx, pol) : -1;
-                            const VT vn = VALS && in ? ld_keep(vp + nx, pol) : VT(0);
-                            if (rq[0] >= 0) f(rq[0], VALS ? vq[0] * b : VT(0));
+                        for (; idx < i1; idx += 32 * AHEAD) {
 #pragma unroll
-                            for (int d = 0; d + 1 < AHEAD; ++d) {
-                                rq[d] = rq[d + 1];
-                                vq[d] = vq[d + 1];
+                            for (int d = 0; d < AHEAD; ++d) {
+                                if (rq[d] >= 0) f(rq[d], VALS ? vq[d] * b : VT(0));
+                                const int q = idx + 32 * (AHEAD + d);
+                                const bool in = q < i1 && q < e_z;
+                                rq[d] = in ? ld_keep(rp + q, pol) : -1;
+                                vq[d] = VALS && in ? ld_keep(vp + q, pol) : VT(0);
                             }
-                            rq[AHEAD - 1] = rn;
-                            vq[AHEAD - 1] = vn;
                         }
                         win = e_end;
                     }
@@ -627,72 +625,87 @@ __device__ __forceinline__ int64_t cta_bitmap_prefix(uint2 *bm, int64_t W64, con
     return carry;
 }
 
-// Visits the set bits of bm[0..W) with f(row, rank), rank = position of the
-// row in the sorted column (bm[..].y must hold the prefix counts).  Warps
-// take groups of kVisitGroup chunks of 32 words, the first group by warp
-// index and the next ones from the shared counter *s_next, which must hold
-// kVisitGroup * (number of warps) before a barrier that precedes the call
-// (one shared atomic per 4096 rows).  Every lane holds one word of a chunk.
-// In a chunk whose words hold at most kVisitLight bits each, every lane
-// visits its own bits.  Otherwise the lanes write their rows, in rank order,
-// into the warp's kVisitStage-entry slice of `stage` (rank minus the chunk's
-// first rank is the slot), and the warp then calls f on consecutive slots,
-// one per lane, so that a fuller chunk costs each lane one step per bit and
-// its stores are coalesced; a chunk of more than kVisitStage bits goes
-// through the slice in pieces.  stage: kVisitStage ints per warp of shared
-// memory that nothing else uses during the call.  Clears the bits when
-// `clear`.  No barrier inside.
-constexpr int kVisitLight = 3;
+// Writes out the set bits of bm[0..W) in ascending row order: the row at
+// sorted position `rank` of the column is stored by put(rank, map(row))
+// (bm[..].y must hold the prefix counts).  Warps take groups of kVisitGroup
+// chunks of 32 words, the first group by warp index and the next ones from
+// the shared counter *s_next, which must hold kVisitGroup * (number of warps)
+// before a barrier that precedes the call (one shared atomic per 4096 rows).
+// The ranks of a group are consecutive: each lane holds one word of a chunk
+// and writes the word's rows, rank minus the group's first rank being the
+// slot, into the warp's kVisitStage-entry slice of `stage`; the warp then
+// stores the staged slots in order, one per lane, with kVisitUnroll map()
+// look-ups in flight per lane before their stores, so the stores are
+// coalesced and a group waits for few look-up latencies.  A group of more
+// than kVisitStage rows goes through the slice in pieces.  stage:
+// kVisitStage ints per warp of shared memory that nothing else uses during
+// the call.  Clears the bits when `clear`.  No barrier inside.
 // Chunks of 32 words a warp takes per grab in cta_bitmap_visit.
 constexpr int kVisitGroup = 4;
-// Rows a warp stages per piece of a chunk in cta_bitmap_visit.
+// Rows a warp stages per piece in cta_bitmap_visit.
 constexpr int kVisitStage = 160;
+// Look-ups per lane issued before their stores in cta_bitmap_visit.
+constexpr int kVisitUnroll = 4;
 
-template <typename F>
+template <typename M, typename P>
 __device__ __forceinline__ void cta_bitmap_visit(uint2 *bm, int64_t W64, bool clear, unsigned *s_next,
-                                                 int32_t *stage, F &&f) {
+                                                 int32_t *stage, M &&map, P &&put) {
     // m < 2^31, so words, chunks and ranks all fit 32-bit indices
     const int W = (int)W64;
     const int lane = threadIdx.x & 31;
     const int nchunks = (W + 31) >> 5;
     int32_t *slots = stage + (threadIdx.x >> 5) * kVisitStage;
+    // stores the slots of relative ranks [from, to), slot 0 holding `from`
+    auto flush = [&](int32_t r0, int from, int to) {
+        for (int o0 = from; o0 < to; o0 += 32 * kVisitUnroll) {
+            int32_t out[kVisitUnroll];
+#pragma unroll
+            for (int u = 0; u < kVisitUnroll; ++u) {
+                const int o = o0 + 32 * u + lane;
+                out[u] = o < to ? map(slots[o - from]) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kVisitUnroll; ++u) {
+                const int o = o0 + 32 * u + lane;
+                if (o < to) put(r0 + o, out[u]);
+            }
+        }
+    };
     for (int g = (threadIdx.x >> 5) * kVisitGroup; g < nchunks;) {
         const int gend = g + kVisitGroup < nchunks ? g + kVisitGroup : nchunks;
+        // the group's first word exists (g < nchunks); its prefix count is
+        // the group's first rank
+        const int32_t r0 = (int32_t)bm[g << 5].y;
+        int flushed = 0;  // relative ranks below this are stored
+        int top = 0;      // relative end of the rows staged so far
         for (int c = g; c < gend; ++c) {
             const int wd = (c << 5) + lane;
             const uint2 v = wd < W ? bm[wd] : make_uint2(0u, 0u);
             if (clear && v.x) bm[wd].x = 0u;
-            const int cnt = __popc(v.x);
-            const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
-            const int32_t row0 = wd << 5;
             uint32_t bits = v.x;
-            if (maxc <= kVisitLight) {
-                int32_t rank = (int32_t)v.y;
-                while (bits) {
-                    const int b = __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    f(row0 + b, rank++);
-                }
-                continue;
-            }
-            // lane 0's word always exists; lanes past W hold no bits
-            const uint32_t y0 = __shfl_sync(0xffffffffu, v.y, 0);
-            int pos = wd < W ? (int)(v.y - y0) : 0;
-            const int S = (int)__reduce_max_sync(0xffffffffu, (unsigned)(pos + cnt));
-            for (int base = 0; base < S; base += kVisitStage) {
-                const int lim = base + kVisitStage;
+            // lanes past W hold no bits
+            int pos = wd < W ? (int)v.y - r0 : 0;
+            const int32_t row0 = wd << 5;
+            const int end = (int)__reduce_max_sync(0xffffffffu, (unsigned)(pos + __popc(bits)));
+            for (;;) {
+                const int lim = flushed + kVisitStage;
                 while (bits && pos < lim) {
                     const int b = __ffs(bits) - 1;
                     bits &= bits - 1u;
-                    slots[pos - base] = row0 + b;
+                    slots[pos - flushed] = row0 + b;
                     ++pos;
                 }
+                if (end <= lim) break;  // uniform over the warp
                 __syncwarp();
-                const int end = S < lim ? S : lim;
-                for (int o = base + lane; o < end; o += 32) f(slots[o - base], (int32_t)y0 + o);
+                flush(r0, flushed, lim);
                 __syncwarp();
+                flushed = lim;
             }
+            top = end > top ? end : top;
         }
+        __syncwarp();
+        flush(r0, flushed, top);
+        __syncwarp();
         unsigned nc = 0;
         if (lane == 0) nc = atomicAdd(s_next, (unsigned)kVisitGroup);
         g = (int)__shfl_sync(0xffffffffu, nc, 0);
