@@ -102,8 +102,8 @@ __device__ __forceinline__ int64_t sym_dense_column(const TOps<float> &o, int32_
     if (threadIdx.x == 0) *s_cnt = 0;
     // the OR's old value is not needed: the rows are counted afterwards with
     // popcounts while the words are copied out and cleared
-    cta_walk<false, float>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
-                           [&](int32_t row, float) { atomicOr(&bm[row >> 5], 1u << (row & 31)); });
+    cta_walk<false, float, kSymWalkAhead>(o.Acp, o.Arow, nullptr, o.Brow, nullptr, o.Bcp[j], o.Bcp[j + 1], w,
+                                          [&](int32_t row, float) { atomicOr(&bm[row >> 5], 1u << (row & 31)); });
     unsigned long long cnt = 0;
     const bool vec = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(bm) & 15) == 0 &&
                      (!keep || (reinterpret_cast<uintptr_t>(keep) & 15) == 0);

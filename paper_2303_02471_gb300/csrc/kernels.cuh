@@ -122,6 +122,9 @@ constexpr int kLongEntry = 32;
 // walk (cta_walk's AHEAD; other callers keep one): four 256-thread CTAs per
 // SM leave 64 registers a thread, which hold five without spilling.
 constexpr int kWalkAhead = 5;
+// The same for the dense bin's flag walk (rows only, one register a window;
+// eight 256-thread CTAs per SM leave 32 registers a thread).
+constexpr int kSymWalkAhead = 4;
 
 // Inclusive block scan of four int32 counters packed as two int64 lanes
 // (each half < 2^31); totals returned.  Two barriers.
@@ -223,8 +226,10 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                                          const VT *__restrict__ Bval, int64_t p0, int64_t p1,
                                          const WalkSmem<VT> &w, F &&f) {
     // windows gathered per lane before any is consumed: with values, short
-    // entries take one at a time (the loop stays small enough not to spill)
-    // and long ones keep a ring of AHEAD windows in flight
+    // entries take one at a time (the loop stays small enough not to spill);
+    // long ones keep a ring of AHEAD windows in flight when the caller asks
+    // for one (AHEAD > 1) or values are walked, else take kWalkBatch windows
+    // at a time across entries
     constexpr int UB = VALS ? 1 : kWalkBatch;
     const int T = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
@@ -275,7 +280,7 @@ __device__ __forceinline__ void cta_walk(const int64_t *__restrict__ Acp, const 
                     const int mid = (li + hi + 1) >> 1;
                     if (w.key[mid] <= win0) li = mid; else hi = mid - 1;
                 }
-                if constexpr (UB == 1) {
+                if constexpr (UB == 1 || AHEAD > 1) {
                     // entry by entry: the entry's windows in [win, e_end)
                     // are one warp-uniform loop over idx = window * 32 + lane
                     // of its A column
