@@ -842,7 +842,9 @@ def run_t_sweep(args, dev, flush):
         out[str(k)] = {"GFLOPs": row, "speedup_vs_t0": {k2: round(v / base, 3) for k2, v in row.items()},
                        "autotuned_config": {"t": tuned.t, "hash_cta_max": tuned.hash_cta_max,
                                             "cta_threads": tuned.cta_threads,
-                                            "small_accumulator": tuned.small_accumulator}}
+                                            "small_accumulator": tuned.small_accumulator,
+                                            "table_slots_pct": tuned.table_slots_pct,
+                                            "group_promote": tuned.group_promote}}
     pairs = synth.batch_pairs(512, seed=0)
     As = [ops.CscMatrix.from_host(A, device=dev) for A, _ in pairs]
     Bs = [ops.CscMatrix.from_host(B, device=dev) for _, B in pairs]
@@ -871,7 +873,8 @@ def run_t_sweep(args, dev, flush):
     out["4"] = {"GFLOPs": row, "speedup_vs_t0": {k2: round(v / base, 3) for k2, v in row.items()
                                                   if isinstance(v, float) and isinstance(base, float)},
                 "autotuned_config": {"t": tuned.t, "hash_cta_max": tuned.hash_cta_max,
-                                     "cta_threads": tuned.cta_threads}}
+                                     "cta_threads": tuned.cta_threads, "table_slots_pct": tuned.table_slots_pct,
+                                     "group_promote": tuned.group_promote}}
     return out
 
 

@@ -129,6 +129,19 @@ typedef struct {
      * ESC unless SPG_ACC_HASH.  Only the single products use it; the batched
      * calls keep hash tables. */
     int32_t small_accumulator;
+    /* Size of the hash tables of the numeric and backward phases' CTA and
+     * global bins (Section 3.2's table size), in slots per output entry of
+     * the column, as a percentage: 125..400, default 150 (a load of at most
+     * 2/3).  Larger tables probe less but take more shared memory, so a
+     * bin's tables move to the workspace scratch sooner.  Results do not
+     * depend on it. */
+    int32_t table_slots_pct;
+    /* Lanes per column of the lane-group bins (columns with Op_j <= 256):
+     * 0 (default) gives a column the smallest group bin that holds its
+     * Op_j; 1 or 2 moves it that many group bins up (at most the
+     * Op_j <= 256 bin), so that it gets more lanes, registers and table
+     * slots, and a warp holds fewer columns.  Results do not depend on it. */
+    int32_t group_promote;
 } spg_config;
 
 enum { SPG_ACC_HASH = 0, SPG_ACC_ESC = 1, SPG_ACC_AUTO = 2 };

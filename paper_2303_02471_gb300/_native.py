@@ -36,7 +36,8 @@ class SpgCsr(ctypes.Structure):
 class SpgConfig(ctypes.Structure):
     _fields_ = [("t", i64), ("hash_cta_max", i32), ("cta_threads", i32), ("validate", i32),
                 ("table_shrink", i32), ("scratch_cap_bytes", i64), ("dense_cache_bytes", i64),
-                ("side_streams", i32), ("test_wait_timeout", i32), ("small_accumulator", i32)]
+                ("side_streams", i32), ("test_wait_timeout", i32), ("small_accumulator", i32),
+                ("table_slots_pct", i32), ("group_promote", i32)]
 
 
 class SpgError(RuntimeError):

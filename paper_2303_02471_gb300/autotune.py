@@ -2,7 +2,10 @@
 hash table hash_cta_max and the threads per CTA of the persistent kernels)
 and for a single product (t, hash_cta_max, the threads per CTA of the CTA
 bins and the accumulator of the light columns), each by timing candidate
-configurations on the products themselves.
+configurations on the products themselves.  A second stage then tries, around
+the best of the grid, the hash-table size (slots per output entry) and the
+lanes per light column (how many lane-group bins a light column moves up):
+the table sizes and threads per column of Section 3.2's hash accumulation.
 
 The paper fixes t = 40 for its vector unit and studies t, b_min and b_max by
 hand (Section 5.4); here the choice is measured on the GPU and cached per GPU
@@ -29,6 +32,37 @@ DEFAULT_GRID = {
     "hash_cta_max": [2048, 8192],
     "cta_threads": [128, 256, 512],
 }
+# Knobs tried in the second stage, one combination at a time around the best
+# configuration of the first (the first value of each is the library default).
+REFINE = {
+    "table_slots_pct": [150, 250],
+    "group_promote": [0, 1],
+}
+
+
+def _with_defaults(conf: dict, refine: dict) -> dict:
+    """conf with the second stage's knobs spelled out (their first values,
+    the library defaults, where the first stage's pick kept them)."""
+    out = dict(conf)
+    for n, values in refine.items():
+        out.setdefault(n, values[0])
+    return out
+
+
+def _refine(best_conf: dict, timed, results: list, refine: dict) -> None:
+    """Times best_conf with every combination of the refine values other than
+    the defaults (appending to results)."""
+    names = sorted(refine)
+    for values in itertools.product(*(refine[n] for n in names)):
+        conf = dict(best_conf)
+        conf.update(zip(names, values))
+        if all(v == refine[n][0] for n, v in zip(names, values)):
+            continue  # the first stage timed the defaults
+        try:
+            ms, err = timed(conf), None
+        except RuntimeError as e:  # a configuration the products do not support
+            ms, err = float("inf"), str(e)
+        results.append({"config": conf, "ms": ms, "error": err})
 
 
 def _cache_path(path: Optional[str]) -> str:
@@ -84,7 +118,7 @@ def tune(As, Bs, grid: Optional[dict] = None, repeats: int = 2, cache: Optional[
             table = {}
     if key in table and not refresh:
         return Config(**table[key]["config"]), table[key]
-    grid = grid or DEFAULT_GRID
+    grid = grid or dict(DEFAULT_GRID, **REFINE)
     results = []
     for t, hmax, thr in itertools.product(grid["t"], grid["hash_cta_max"], grid["cta_threads"]):
         cfg = Config(t=t, hash_cta_max=hmax, cta_threads=thr)
@@ -99,8 +133,13 @@ def tune(As, Bs, grid: Optional[dict] = None, repeats: int = 2, cache: Optional[
     ok = [r for r in results if np.isfinite(r["ms"])]
     if not ok:
         raise RuntimeError("no candidate configuration ran")
+    refine = {n: grid[n] for n in REFINE if n in grid}
+    if refine:
+        best = min(ok, key=lambda r: r["ms"])
+        _refine(best["config"], lambda conf: _time(As, Bs, Config(**conf), repeats), results, refine)
+        ok = [r for r in results if np.isfinite(r["ms"])]
     best = min(ok, key=lambda r: r["ms"])
-    entry = {"config": best["config"], "ms": best["ms"], "candidates": results}
+    entry = {"config": _with_defaults(best["config"], refine), "ms": best["ms"], "candidates": results}
     table[key] = entry
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)
@@ -167,8 +206,9 @@ def tune_product(A, B, grid: Optional[dict] = None, repeats: int = 2, cache: Opt
             table = {}
     if key in table and not refresh:
         return Config(**table[key]["config"]), table[key]
-    grid = grid or PRODUCT_GRID
-    names = sorted(grid)
+    grid = grid or dict(PRODUCT_GRID, **REFINE)
+    refine = {n: grid[n] for n in REFINE if n in grid}
+    names = sorted(n for n in grid if n not in refine)
     results = []
     for values in itertools.product(*(grid[n] for n in names)):
         conf = dict(zip(names, values))
@@ -181,8 +221,12 @@ def tune_product(A, B, grid: Optional[dict] = None, repeats: int = 2, cache: Opt
     ok = [r for r in results if np.isfinite(r["ms"])]
     if not ok:
         raise RuntimeError("no candidate configuration ran")
+    if refine:
+        best = min(ok, key=lambda r: r["ms"])
+        _refine(best["config"], lambda conf: _time_product(A, B, Config(**conf), repeats), results, refine)
+        ok = [r for r in results if np.isfinite(r["ms"])]
     best = min(ok, key=lambda r: r["ms"])
-    entry = {"config": best["config"], "ms": best["ms"], "candidates": results}
+    entry = {"config": _with_defaults(best["config"], refine), "ms": best["ms"], "candidates": results}
     table[key] = entry
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)

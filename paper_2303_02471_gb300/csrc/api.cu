@@ -90,10 +90,10 @@ Layout make_layout(int64_t m, int64_t nB, int64_t nnzA, int dtype, const spg_con
     // tables that do not fit shared memory, keys and values
     const int64_t reach = std::min<int64_t>(std::max<int64_t>(nnzA, 1), std::max<int64_t>(m, 1));
     // hash table keys + values + word list of the extraction (numeric)
-    size_t tab = (size_t)num_slots(std::min<int64_t>(hmax, reach)) * (8 + w) + 64;
+    size_t tab = (size_t)num_slots(std::min<int64_t>(hmax, reach), c.table_slots_pct) * (8 + w) + 64;
     if (effective_t(c, m) > hmax + 1) {
         const size_t sym = (size_t)global_sym_slots(reach, m) * 4;
-        const size_t num = (size_t)num_slots(reach) * (8 + w) + 64;
+        const size_t num = (size_t)num_slots(reach, c.table_slots_pct) * (8 + w) + 64;
         tab = std::max(tab, std::max(sym, num));
     }
     L.scratch_stride = align256((size_t)W * 8) + align256(tab);
@@ -207,6 +207,7 @@ struct spg_plan {
         t.count = (int64_t)host.hist[b];
         t.bin = b;
         t.shrink = cfg.table_shrink;
+        t.slots_pct = cfg.table_slots_pct;
         t.m = fwd ? mC : mA;
         t.W = ceil_div(t.m, 32);
         t.op = op();
@@ -253,6 +254,8 @@ spg_status spg_config_default(spg_config *cfg) {
     cfg->side_streams = 1;
     cfg->test_wait_timeout = 0;
     cfg->small_accumulator = SPG_ACC_AUTO;
+    cfg->table_slots_pct = kDefaultSlotsPct;
+    cfg->group_promote = 0;
     return SPG_OK;
 }
 
@@ -287,6 +290,8 @@ static spg_status check_config(const spg_config &c) {
     if (c.small_accumulator != SPG_ACC_HASH && c.small_accumulator != SPG_ACC_ESC &&
         c.small_accumulator != SPG_ACC_AUTO)
         return SPG_ERR_INVALID;
+    if (c.table_slots_pct < 125 || c.table_slots_pct > 400) return SPG_ERR_INVALID;
+    if (c.group_promote < 0 || c.group_promote > 2) return SPG_ERR_INVALID;
     return SPG_OK;
 }
 
@@ -415,7 +420,7 @@ static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B
     if (P->nB > 0) {
         // a warp per 32 columns, 8 warps per CTA
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(P->nB, 256), 16 * (int64_t)P->dev.sms));
-        k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, P->mC,
+        k_count_bin<<<g, 256, 0, s>>>(B->colptr, B->rowidx, A->colptr, P->nB, P->t_eff, hmax, c.group_promote, P->mC,
                                       column_deal_mult(P->nB), P->op(), C_colptr, ctrl);
         CK(cudaGetLastError());
     } else {
@@ -434,8 +439,8 @@ static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B
         P->off.v[b + 1] = P->off.v[b] + n;
     }
     if (scatter && P->nB > 0) {
-        k_bin_scatter<<<(unsigned)ceil_div(P->nB, 256), 256, 0, s>>>(P->op(), P->nB, P->t_eff, hmax, P->off,
-                                                                    P->cols(), ctrl);
+        k_bin_scatter<<<(unsigned)ceil_div(P->nB, 256), 256, 0, s>>>(P->op(), P->nB, P->t_eff, hmax, c.group_promote,
+                                                                     P->off, P->cols(), ctrl);
         CK(cudaGetLastError());
     }
     CK(cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s));
@@ -521,7 +526,7 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
     for (int b = 1; b < NBINS; ++b) {
         if (!P->host.hist[b]) continue;
         P->num_geo[b] = numeric_geometry(b, (int64_t)P->host.hist[b], P->mC, c.cta_threads, P->dev.sms,
-                                         P->dev.smem_optin, (int64_t)P->host.maxnnz[b], P->dtype, c.table_shrink,
+                                         P->dev.smem_optin, (int64_t)P->host.maxnnz[b], P->dtype, c.table_slots_pct,
                                          P->L.scratch_ctas);
     }
     P->num_geo_ready = true;
@@ -669,7 +674,7 @@ spg_status spgemm_single_pass(spg_handle *handle, const spg_csc *A, const spg_cs
         if (!P->host.hist[b]) continue;
         const int64_t bound = std::min<int64_t>((int64_t)P->host.maxop[b], P->mC);
         P->num_geo[b] = numeric_geometry(b, (int64_t)P->host.hist[b], P->mC, c.cta_threads, P->dev.sms,
-                                         P->dev.smem_optin, bound, P->dtype, c.table_shrink, P->L.scratch_ctas);
+                                         P->dev.smem_optin, bound, P->dtype, c.table_slots_pct, P->L.scratch_ctas);
     }
     P->num_geo_ready = true;
     Operands o{A->colptr, P->compact ? P->arow() : A->rowidx, A->values, B->colptr, B->rowidx, B->values,
@@ -718,7 +723,7 @@ spg_status spgemm_backward(spg_plan *P, const spg_csc *A, const spg_csc *B, cons
             if (!P->host.hist[b]) continue;
             P->bwd_geo[b] = backward_geometry(b, (int64_t)P->host.hist[b], P->mA, P->cfg.cta_threads, P->dev.sms,
                                               P->dev.smem_optin, (int64_t)P->host.maxnnz[b], P->dtype,
-                                              P->cfg.table_shrink, P->L.scratch_ctas);
+                                              P->cfg.table_slots_pct, P->L.scratch_ctas);
         }
         P->bwd_geo_ready = true;
     }

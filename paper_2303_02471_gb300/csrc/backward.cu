@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(1024, 1) k_bwd_cta(BinTask t, Operands o, cons
         if (ci >= t.count) break;
         const int32_t j = t.cols[ci];
         const int64_t c0 = Ccp[j], nn = Ccp[j + 1] - c0;
-        int64_t want = num_slots(nn);
+        int64_t want = num_slots(nn, t.slots_pct);
         if (want > cap) want = cap;
         if (!bwd_cta_column<VT>(ops, j, c0, nn, Crow, dC, keys, vals, (uint32_t)want, w, pidx, dA, dB))
             set_error(t.ctrl, SPG_ERR_TABLE_OVERFLOW, t.bin, j);
@@ -111,7 +111,7 @@ static inline int bwd_cta_threads(int bin, int cfg_threads) {
 
 template <typename VT>
 static Geo backward_geometry_t(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
-                               int64_t maxnnz, int64_t scratch_ctas) {
+                               int64_t maxnnz, int slots_pct, int64_t scratch_ctas) {
     Geo g;
     const int64_t W = ceil_div(m, 32);
     if (bin >= BIN_WARP0 && bin < BIN_CTA0) {
@@ -125,7 +125,7 @@ static Geo backward_geometry_t(int bin, int64_t count, int64_t m, int threads, i
     g.threads = bwd_cta_threads(bin, threads);
     const size_t fixed = walk_smem_bytes<VT>(g.threads) + al16((size_t)g.threads * 4);
     if (bin >= BIN_CTA0 && bin <= BIN_GLOBAL) {
-        g.slots = num_slots(maxnnz);
+        g.slots = num_slots(maxnnz, slots_pct);
         const size_t tab = al16((size_t)g.slots * 4) + al16((size_t)g.slots * sizeof(VT));
         const bool table_global = bin == BIN_GLOBAL || fixed + tab > smem_optin;
         g.cap = table_global ? 1 : 0;
@@ -152,10 +152,10 @@ static Geo backward_geometry_t(int bin, int64_t count, int64_t m, int threads, i
 }
 
 Geo backward_geometry(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin, int64_t maxnnz,
-                      int dtype, int shrink, int64_t scratch_ctas) {
-    (void)shrink;
-    return dtype == SPG_F64 ? backward_geometry_t<double>(bin, count, m, threads, sms, smem_optin, maxnnz, scratch_ctas)
-                            : backward_geometry_t<float>(bin, count, m, threads, sms, smem_optin, maxnnz, scratch_ctas);
+                      int dtype, int slots_pct, int64_t scratch_ctas) {
+    return dtype == SPG_F64
+               ? backward_geometry_t<double>(bin, count, m, threads, sms, smem_optin, maxnnz, slots_pct, scratch_ctas)
+               : backward_geometry_t<float>(bin, count, m, threads, sms, smem_optin, maxnnz, slots_pct, scratch_ctas);
 }
 
 template <typename VT>

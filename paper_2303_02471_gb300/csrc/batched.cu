@@ -71,6 +71,8 @@ struct BTask {
     int64_t cap_sym;       // symbolic CTA key table slots
     const int64_t *op;     // Op of every global column
     int shrink;
+    int promote;           // group_promote: lane-group bins moved up
+    int slots_pct;         // numeric / backward table slots per output entry, per cent
     unsigned long long *counter;
     // flags of per-warp dense columns kept from the symbolic phase: column k
     // of the dense list owns words [coff[k], coff[k] + W) of `cache` when
@@ -111,7 +113,7 @@ __global__ void k_bcount(BTask b, int64_t ntot, int64_t *op) {
             s += P.Acp[k + 1] - P.Acp[k];
         }
         op[g] = s;
-        const int bin = bin_of(s, P.t, b.hmax);
+        const int bin = bin_of(s, P.t, b.hmax, b.promote);
         atomicAdd(&s_hist[bin], 1ULL);
         atomicMax(&s_max[bin], (unsigned long long)s);
         if (s) atomicAdd(&s_prod[bin], (unsigned long long)s);
@@ -151,7 +153,7 @@ __global__ void k_bscatter(BTask b, int64_t ntot, const int64_t *op, int32_t *co
     unsigned r = 0;
     if (g < ntot) {
         const int p = find_prob(b.col0s, b.nb, g);
-        bin = bin_of(op[g], b.prob[p].t, b.hmax);
+        bin = bin_of(op[g], b.prob[p].t, b.hmax, b.promote);
         if (bin != BIN_EMPTY) r = atomicAdd(&s_cnt[bin], 1u);
     }
     __syncthreads();
@@ -412,7 +414,7 @@ __device__ __noinline__ void bnum_cta(const BTask &b, const BProb &P, int64_t j,
     for (int64_t i = threadIdx.x; i < W; i += blockDim.x) L0[i] = 0u;
     for (int64_t i = threadIdx.x; i < (W + 31) / 32; i += blockDim.x) L1[i] = 0u;
     __syncthreads();
-    int64_t want = num_slots(nn);
+    int64_t want = num_slots(nn, b.slots_pct);
     if (want > cap) want = cap;
     uint32_t H = (uint32_t)(want >> b.shrink);
     if (H < 1) H = 1;
@@ -672,6 +674,8 @@ struct spg_bplan {
         b.hmax = cfg.hash_cta_max;
         b.op = reinterpret_cast<const int64_t *>(ws + L.op);
         b.shrink = cfg.table_shrink;
+        b.promote = cfg.group_promote;
+        b.slots_pct = cfg.table_slots_pct;
         b.counter = &ctrl()->work[0];
         b.Wmax = Wmax;
         if (cache_words > 0) {
@@ -738,7 +742,7 @@ size_t phase_smem(const spg_bplan &P, int phase, int threads, int64_t &cap_cta, 
     const bool dense = P.host.hist[BIN_DENSE] != 0 && !wd;
     if (wd) need = std::max(need, (size_t)(threads / 32) * al16((size_t)P.Wmax * (phase == 0 ? 4 : 8)));
     cap_sym = cta ? global_sym_slots(maxop, P.mmax) : 0;
-    cap_cta = cta ? num_slots(maxnnz) : 0;
+    cap_cta = cta ? num_slots(maxnnz, P.cfg.table_slots_pct) : 0;
     if (phase == 0) {
         if (cta) need = std::max(need, walk_smem_bytes<float>(threads) + (size_t)cap_sym * 4);
         if (dense) need = std::max(need, walk_smem_bytes<float>(threads) + (size_t)P.Wmax * 4);
@@ -864,6 +868,8 @@ spg_status spgemm_batched_symbolic(spg_handle *handle, int32_t nb, const spg_csc
     if (c.cta_threads < 128 || c.cta_threads > 1024 || c.cta_threads % 32) return SPG_ERR_INVALID;
     if (!(c.hash_cta_max == 256 || c.hash_cta_max == 512 || c.hash_cta_max == 1024 || c.hash_cta_max == 2048 ||
           c.hash_cta_max == 4096 || c.hash_cta_max == 8192))
+        return SPG_ERR_INVALID;
+    if (c.table_slots_pct < 125 || c.table_slots_pct > 400 || c.group_promote < 0 || c.group_promote > 2)
         return SPG_ERR_INVALID;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return SPG_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -22,6 +22,10 @@ constexpr int kGroupBatch = 2;
 // Threads per CTA of the symbolic CTA-level kernels (several CTAs per SM).
 constexpr int kSymCtaThreads = 256;
 
+// Hash-table slots per output entry of a column in the numeric and backward
+// phases, per cent (spg_config.table_slots_pct's default).
+constexpr int kDefaultSlotsPct = 150;
+
 // ------------------------------------------------------ L2 residency
 // Gathers of A's rows and values carry an L2 evict-last policy: every column
 // of B reads A's columns again, while C (and the kept flags) stream through
@@ -798,15 +802,15 @@ int64_t scan_tile_count(int64_t n);
 __global__ void k_validate(const int64_t *cp, const int32_t *row, int64_t nrows, int64_t ncols,
                            int64_t nnz, int which, Ctrl *ctrl);
 __global__ void k_count_bin(const int64_t *Bcp, const int32_t *Brow, const int64_t *Acp, int64_t nB,
-                            int64_t t, int64_t hmax, int64_t mrows, int64_t mult, int64_t *op, int64_t *Ccp,
-                            Ctrl *ctrl);
+                            int64_t t, int64_t hmax, int promote, int64_t mrows, int64_t mult, int64_t *op,
+                            int64_t *Ccp, Ctrl *ctrl);
 // Multiplier coprime to n (n >= 1) near n times the golden ratio's fraction,
 // dealing the columns of k_count_bin over the warps.
 int64_t column_deal_mult(int64_t n);
 __global__ void k_slot_caps(const int64_t *op, int64_t nB, int64_t mrows, int64_t *caps);
 cudaError_t launch_slot_copy(int64_t nB, const int64_t *Ccp, const int64_t *soff, const int32_t *srow,
                              const void *sval, int32_t *Crow, void *Cval, int w, int sms, cudaStream_t s);
-__global__ void k_bin_scatter(const int64_t *op, int64_t nB, int64_t t, int64_t hmax,
+__global__ void k_bin_scatter(const int64_t *op, int64_t nB, int64_t t, int64_t hmax, int promote,
                               BinOffsets off, int32_t *bin_cols, Ctrl *ctrl);
 
 // Geometry of one phase (symbolic / numeric / backward) of one bin.
@@ -840,6 +844,7 @@ struct BinTask {
     // min(Op_j, m)) and its entry count to cnt_out[j + 1]; null otherwise
     // (the count is checked against the symbolic phase's)
     int64_t *cnt_out = nullptr;
+    int slots_pct = kDefaultSlotsPct;  // hash-table slots per output entry, per cent
 };
 
 struct Operands {
@@ -857,13 +862,13 @@ Geo symbolic_geometry(int bin, int64_t count, int64_t m, int threads, int sms, s
 cudaError_t launch_numeric_bin(const BinTask &t, const Operands &o, const int64_t *Ccp,
                                int32_t *Crow, void *Cval, int dtype, const Geo &g, cudaStream_t s);
 Geo numeric_geometry(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
-                     int64_t maxnnz, int dtype, int shrink, int64_t scratch_ctas);
+                     int64_t maxnnz, int dtype, int slots_pct, int64_t scratch_ctas);
 // backward.cu
 cudaError_t launch_backward_bin(const BinTask &t, const Operands &o, const int64_t *Ccp,
                                 const int32_t *Crow, const void *dC, void *dA, void *dB,
                                 int dtype, const Geo &g, cudaStream_t s);
 Geo backward_geometry(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
-                      int64_t maxnnz, int dtype, int shrink, int64_t scratch_ctas);
+                      int64_t maxnnz, int dtype, int slots_pct, int64_t scratch_ctas);
 
 // Table slots of the global-memory hash bin for a column with Op_j = op in a
 // matrix with m rows (symbolic: keys only, load <= 1/2).
@@ -873,9 +878,11 @@ __host__ __device__ inline int64_t global_sym_slots(int64_t op, int64_t m) {
     while (p < need) p <<= 1;
     return p;
 }
-// Table slots for a column with n outputs (numeric / backward, load <= 2/3).
-__host__ __device__ inline int64_t num_slots(int64_t n) {
-    int64_t s = (n * 3 + 1) / 2;
+// Table slots for a column with n outputs (numeric / backward): pct per
+// cent of n, rounded up to a multiple of 32, at least 64 (the default
+// kDefaultSlotsPct keeps the load at most 2/3).
+__host__ __device__ inline int64_t num_slots(int64_t n, int pct = kDefaultSlotsPct) {
+    int64_t s = (n * pct + 99) / 100;
     s = (s + 31) & ~int64_t(31);
     return s < 64 ? 64 : s;
 }

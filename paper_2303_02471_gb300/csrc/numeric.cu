@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_cta(BinTask t, Operands o, cons
         const int32_t j = t.cols[ci];
         const int64_t c0 = Ccp[j];
         const int64_t nn = Ccp[j + 1] - c0;
-        int64_t want = num_slots(nn);
+        int64_t want = num_slots(nn, t.slots_pct);
         if (want > cap) want = cap;
         uint32_t H = (uint32_t)(want >> t.shrink);
         if (H < 1) H = 1;
@@ -186,8 +186,7 @@ inline int cta_bin_threads(int bin, int cfg_threads) {
 
 template <typename VT>
 static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
-                              int64_t maxnnz, int shrink, int64_t scratch_ctas) {
-    (void)shrink;
+                              int64_t maxnnz, int slots_pct, int64_t scratch_ctas) {
     Geo g;
     const int64_t W = ceil_div(m, 32);
     const int64_t W1 = ceil_div(W, 32);
@@ -201,7 +200,7 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
     }
     g.threads = cta_bin_threads(bin, threads);
     if (bin >= BIN_CTA0 && bin <= BIN_GLOBAL) {
-        g.slots = num_slots(maxnnz);
+        g.slots = num_slots(maxnnz, slots_pct);
         // table (keys, values) and word list; L1 always in shared memory
         const size_t tab = al16((size_t)g.slots * 4) + al16((size_t)g.slots * sizeof(VT)) +
                            al16((size_t)g.slots * 4);
@@ -276,10 +275,10 @@ static Geo numeric_geometry_t(int bin, int64_t count, int64_t m, int threads, in
 }
 
 Geo numeric_geometry(int bin, int64_t count, int64_t m, int threads, int sms, size_t smem_optin,
-                     int64_t maxnnz, int dtype, int shrink, int64_t scratch_ctas) {
+                     int64_t maxnnz, int dtype, int slots_pct, int64_t scratch_ctas) {
     return dtype == SPG_F64
-               ? numeric_geometry_t<double>(bin, count, m, threads, sms, smem_optin, maxnnz, shrink, scratch_ctas)
-               : numeric_geometry_t<float>(bin, count, m, threads, sms, smem_optin, maxnnz, shrink, scratch_ctas);
+               ? numeric_geometry_t<double>(bin, count, m, threads, sms, smem_optin, maxnnz, slots_pct, scratch_ctas)
+               : numeric_geometry_t<float>(bin, count, m, threads, sms, smem_optin, maxnnz, slots_pct, scratch_ctas);
 }
 
 template <typename VT>

@@ -41,7 +41,8 @@ __global__ void k_validate(const int64_t *__restrict__ cp, const int32_t *__rest
 constexpr int kCountLong = 32;
 
 __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__restrict__ Brow,
-                            const int64_t *__restrict__ Acp, int64_t nB, int64_t t, int64_t hmax, int64_t mrows,
+                            const int64_t *__restrict__ Acp, int64_t nB, int64_t t, int64_t hmax, int promote,
+                            int64_t mrows,
                             int64_t mult, int64_t *__restrict__ op, int64_t *__restrict__ Ccp, Ctrl *ctrl) {
     __shared__ unsigned long long s_hist[NBINS];
     __shared__ unsigned long long s_max[NBINS];
@@ -134,7 +135,7 @@ __global__ void k_count_bin(const int64_t *__restrict__ Bcp, const int32_t *__re
             op[j] = s;
             mine += (unsigned long long)s;
             cap += (unsigned long long)(s < mrows ? s : mrows);
-            b = bin_of(s, t, hmax);
+            b = bin_of(s, t, hmax, promote);
             if (b == BIN_EMPTY) Ccp[j + 1] = 0;
         }
         // per-bin statistics, one group of lanes per bin present
@@ -262,7 +263,7 @@ cudaError_t launch_slot_copy(int64_t nB, const int64_t *Ccp, const int64_t *soff
 // Column ids into per-bin lists at off[bin] (each block reserves its slots
 // with one global atomic per bin, so columns of a bin stay roughly in
 // ascending order within a block's tile).
-__global__ void k_bin_scatter(const int64_t *__restrict__ op, int64_t nB, int64_t t, int64_t hmax,
+__global__ void k_bin_scatter(const int64_t *__restrict__ op, int64_t nB, int64_t t, int64_t hmax, int promote,
                               BinOffsets off, int32_t *__restrict__ bin_cols, Ctrl *ctrl) {
     __shared__ unsigned int s_cnt[NBINS];
     __shared__ unsigned long long s_base[NBINS];
@@ -272,7 +273,7 @@ __global__ void k_bin_scatter(const int64_t *__restrict__ op, int64_t nB, int64_
     int b = -1;
     unsigned r = 0;
     if (j < nB) {
-        b = bin_of(op[j], t, hmax);
+        b = bin_of(op[j], t, hmax, promote);
         if (b != BIN_EMPTY) r = atomicAdd(&s_cnt[b], 1u);
     }
     __syncthreads();

@@ -34,12 +34,15 @@ __host__ __device__ constexpr int warp_bin_R(int b) {
 __host__ __device__ constexpr int warp_bin_opmax(int b) { return warp_bin_G(b) * warp_bin_R(b); }
 __host__ __device__ constexpr int64_t cta_bin_opmax(int c) { return 512LL << c; }
 
-// Bin of a column with Op_j = op under threshold t and CTA-hash limit.
-__host__ __device__ inline int bin_of(int64_t op, int64_t t, int64_t hash_cta_max) {
+// Bin of a column with Op_j = op under threshold t and CTA-hash limit; a
+// column of a lane-group bin moves `promote` group bins up (more lanes and
+// table slots per column), at most to the last group bin.
+__host__ __device__ inline int bin_of(int64_t op, int64_t t, int64_t hash_cta_max, int promote = 0) {
     if (op <= 0) return BIN_EMPTY;
     if (op >= t) return BIN_DENSE;
     for (int b = 0; b < kNumWarpBins; ++b)
-        if (op <= warp_bin_opmax(b)) return BIN_WARP0 + b;
+        if (op <= warp_bin_opmax(b))
+            return BIN_WARP0 + (b + promote < kNumWarpBins ? b + promote : kNumWarpBins - 1);
     if (op <= hash_cta_max) {
         for (int c = 0; c < kNumCtaBins; ++c)
             if (op <= cta_bin_opmax(c)) return BIN_CTA0 + c;

@@ -114,12 +114,14 @@ class Config:
     side_streams: Optional[bool] = None
     test_wait_timeout: Optional[bool] = None
     small_accumulator: Optional[str] = None  # "hash", "esc" or "auto"
+    table_slots_pct: Optional[int] = None    # hash-table slots per output entry, per cent (125..400)
+    group_promote: Optional[int] = None      # lane-group bins a light column moves up (0..2)
 
     def native(self) -> N.SpgConfig:
         c = N.SpgConfig()
         N.check(N.lib().spg_config_default(ctypes.byref(c)), "spg_config_default")
         for f in ("t", "hash_cta_max", "cta_threads", "table_shrink", "scratch_cap_bytes",
-                  "dense_cache_bytes"):
+                  "dense_cache_bytes", "table_slots_pct", "group_promote"):
             v = getattr(self, f)
             if v is not None:
                 setattr(c, f, int(v))

@@ -44,10 +44,11 @@ def test_struct_layouts():
     from paper_2303_02471_gb300 import _native as N
     assert ctypes.sizeof(N.SpgCsc) == 56 and ctypes.sizeof(N.SpgCsr) == 56
     assert N.SpgCsc.values.offset == 40 and N.SpgCsc.dtype.offset == 48
-    assert ctypes.sizeof(N.SpgConfig) == 56
+    assert ctypes.sizeof(N.SpgConfig) == 64
     assert N.SpgConfig.dense_cache_bytes.offset == 32
     assert N.SpgConfig.side_streams.offset == 40 and N.SpgConfig.test_wait_timeout.offset == 44
     assert N.SpgConfig.small_accumulator.offset == 48
+    assert N.SpgConfig.table_slots_pct.offset == 52 and N.SpgConfig.group_promote.offset == 56
 
 
 def test_status_strings_and_defaults(lib):
@@ -58,7 +59,28 @@ def test_status_strings_and_defaults(lib):
     assert lib.spg_config_default(ctypes.byref(c)) == 0
     assert c.t == -1 and c.validate == 1 and c.hash_cta_max == 8192
     assert c.side_streams == 1 and c.test_wait_timeout == 0 and c.small_accumulator == N.SPG_ACC_AUTO
+    assert c.table_slots_pct == 150 and c.group_promote == 0
     assert lib.spg_config_default(None) == 1
+
+
+def test_config_range_checks(lib):
+    """Out-of-range table sizes and group promotions are rejected before any
+    device call (the descriptors are only checked, never read)."""
+    from paper_2303_02471_gb300 import _native as N
+    M = N.SpgCsc(10, 10, 0, 256, None, None, N.SPG_F64)
+    nbytes = ctypes.c_size_t()
+    for field, value in (("table_slots_pct", 124), ("table_slots_pct", 401), ("group_promote", -1),
+                         ("group_promote", 3)):
+        c = N.SpgConfig()
+        assert lib.spg_config_default(ctypes.byref(c)) == 0
+        setattr(c, field, value)
+        assert lib.spgemm_workspace_size(ctypes.byref(M), ctypes.byref(M), ctypes.byref(c),
+                                         ctypes.byref(nbytes)) == 1, (field, value)
+    c = N.SpgConfig()
+    lib.spg_config_default(ctypes.byref(c))
+    c.table_slots_pct, c.group_promote = 400, 2
+    # valid: passes the checks (and fails only for want of a GPU on a CPU box)
+    assert lib.spgemm_workspace_size(ctypes.byref(M), ctypes.byref(M), ctypes.byref(c), ctypes.byref(nbytes)) != 1
 
 
 def test_host_only_calls(lib):

@@ -61,6 +61,13 @@ def test_backward_rmat_every_bin(t):
     _check_backward(A, B, t=t, hash_cta_max=1024)
 
 
+@pytest.mark.parametrize("promote,pct", [(1, 125), (2, 400)])
+def test_backward_table_size_and_group_promotion(promote, pct):
+    A = synth.rmat(13, seed=2, col_cap=600)
+    B = synth.rmat(13, seed=3, col_cap=600)
+    _check_backward(A, B, t=3000, hash_cta_max=1024, table_slots_pct=pct, group_promote=promote)
+
+
 @pytest.mark.parametrize("t", [0, INF])
 def test_backward_tall_products(t):
     # 2^20 rows, nearly all holding entries: the backward's row bitmaps and

@@ -165,6 +165,33 @@ def test_batched_backward_matches_plain():
         assert np.all(np.abs(gb.cpu().numpy().astype(np.float64) - rB) <= tau * sB)
 
 
+@pytest.mark.parametrize("t", [None, INF])
+@pytest.mark.parametrize("promote,pct", [(1, 300), (2, 125)])
+def test_batched_table_size_and_group_promotion(t, promote, pct):
+    """The batched forward and backward with other table sizes and light
+    columns moved up the lane-group bins, against the oracle."""
+    import torch
+    from paper_2303_02471_gb300 import ops
+    pairs = synth.batch_pairs(16, seed=9, n_scale=0.05)
+    As, Bs = _upload_pairs(pairs)
+    cfg = ops.Config(t=t, table_slots_pct=pct, group_promote=promote)
+    Cs, plan = ops.spgemm_batched(As, Bs, cfg)
+    plan.check()
+    rng = np.random.default_rng(2)
+    dCs = [torch.as_tensor(rng.standard_normal(C.nnz), device="cuda").to(C.values.dtype) for C in Cs]
+    gA, gB = ops.spgemm_batched_backward(plan, As, Bs, Cs, dCs)
+    plan.check()
+    for (A, B), C, dc, ga, gb in zip(pairs, Cs, dCs, gA, gB):
+        assert_matches_oracle(C, A, B)
+        Ch = C.to_host()
+        d = dc.cpu().numpy()
+        rA, rB = oracle.backward(A, B, Ch, d)
+        sA, sB = oracle.backward(A.with_values(np.abs(A.values)), B.with_values(np.abs(B.values)), Ch, np.abs(d))
+        tau = TAU[np.dtype(A.values.dtype)]
+        assert np.all(np.abs(ga.cpu().numpy().astype(np.float64) - rA) <= tau * sA)
+        assert np.all(np.abs(gb.cpu().numpy().astype(np.float64) - rB) <= tau * sB)
+
+
 def test_batched_rejects_bad_input():
     from paper_2303_02471_gb300 import ops
     from paper_2303_02471_gb300._native import SpgError
@@ -208,6 +235,14 @@ def test_autotune_chooses_and_caches(tmp_path):
     assert rep2["config"] == rep["config"]
     from paper_2303_02471_gb300 import ops
     Cs, plan = ops.spgemm_batched(As, Bs, cfg)
+    for (A, B), C in zip(pairs, Cs):
+        assert_matches_oracle(C, A, B)
+    # second stage: table size and lanes per light column around the best
+    grid2 = dict(grid, table_slots_pct=[150, 250], group_promote=[0, 1])
+    cfg3, rep3 = autotune.tune(As, Bs, grid=grid2, repeats=1, cache=path, refresh=True)
+    assert len(rep3["candidates"]) == 4 + 3
+    assert {"table_slots_pct", "group_promote"} <= set(rep3["config"])
+    Cs, plan = ops.spgemm_batched(As, Bs, cfg3)
     for (A, B), C in zip(pairs, Cs):
         assert_matches_oracle(C, A, B)
 

@@ -84,6 +84,27 @@ def test_dense_flag_cache_budgets(cache):
     assert_matches_oracle(C, A, A, nthreads=NCPU)
 
 
+GROUP_OPMAX = (8, 16, 32, 64, 128, 256)  # Op_j bound of each lane-group bin
+
+
+@pytest.mark.parametrize("acc", ["hash", "auto"])
+@pytest.mark.parametrize("promote,pct", [(1, 125), (2, 400), (1, 300)])
+def test_table_size_and_group_promotion(promote, pct, acc):
+    """Larger or smaller hash tables and light columns moved up the lane-group
+    bins give the oracle's C; the bin histogram follows the shifted binning
+    rule (a column's smallest group bin, `promote` bins up, at most the last)."""
+    A = synth.rmat(13, seed=2, col_cap=600)
+    C, plan = _run(A, A, t=3000, hash_cta_max=1024, table_slots_pct=pct, group_promote=promote,
+                   small_accumulator=acc)
+    assert_matches_oracle(C, A, A, nthreads=NCPU)
+    op = oracle.op_counts(A, A)
+    want = np.zeros(6, dtype=np.int64)
+    light = op[(op > 0) & (op <= 256)]
+    first = np.searchsorted(np.array(GROUP_OPMAX), light)  # smallest bin with opmax >= Op_j
+    np.add.at(want, np.minimum(first + promote, 5), 1)
+    assert plan.info()["bins"][1:7] == want.tolist()
+
+
 def test_op_counts_and_bins():
     A = synth.rmat(12, seed=5, col_cap=300)
     B = synth.random_z(A.ncols, 0, 12, seed=6)
