@@ -167,7 +167,7 @@ struct spg_plan {
     // single pass: the columns' slots (offsets, rows, values) after the
     // regular layout, sum of the slot sizes
     bool single = false;
-    size_t soff_at = 0, srow_at = 0, sval_at = 0, slots_total = 0;
+    size_t soff_at = 0, srow_at = 0, sval_at = 0, tcol_at = 0, slots_total = 0;
     int64_t capsum = 0;
 
     ~spg_plan() {
@@ -330,7 +330,8 @@ spg_status spg_destroy(spg_handle *handle) {
 }
 
 // Slots of the single pass after the regular layout: offsets int64[nB + 1],
-// rows int32[capsum], values[capsum].
+// rows int32[capsum], values[capsum], and the copy's first column of every
+// tile of C's positions (nnz(C) <= capsum).
 static void slot_layout(spg_plan *P) {
     const size_t w = P->dtype == SPG_F64 ? 8 : 4;
     size_t off = align256(P->L.total);
@@ -340,6 +341,8 @@ static void slot_layout(spg_plan *P) {
     off = align256(off + (size_t)P->capsum * 4);
     P->sval_at = off;
     off = align256(off + (size_t)P->capsum * w);
+    P->tcol_at = off;
+    off = align256(off + (size_t)copy_tile_count(P->capsum) * 4);
     P->slots_total = off;
 }
 
@@ -697,7 +700,8 @@ spg_status spgemm_single_pass_copy(spg_plan *P, const int64_t *C_colptr, int32_t
                                    spg_stream stream) {
     if (!P || !P->single || !C_colptr || (P->nnzC > 0 && (!C_rowidx || !C_values))) return SPG_ERR_INVALID;
     const int w = P->dtype == SPG_F64 ? 8 : 4;
-    return cuda_status(launch_slot_copy(P->nB, C_colptr, reinterpret_cast<const int64_t *>(P->ws + P->soff_at),
+    return cuda_status(launch_slot_copy(P->nB, P->nnzC, C_colptr, reinterpret_cast<const int64_t *>(P->ws + P->soff_at),
+                                        reinterpret_cast<int32_t *>(P->ws + P->tcol_at),
                                         reinterpret_cast<const int32_t *>(P->ws + P->srow_at),
                                         P->ws + P->sval_at, C_rowidx, C_values, w, P->dev.sms,
                                         reinterpret_cast<cudaStream_t>(stream)));

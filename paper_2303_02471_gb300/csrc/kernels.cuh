@@ -808,8 +808,13 @@ __global__ void k_count_bin(const int64_t *Bcp, const int32_t *Brow, const int64
 // dealing the columns of k_count_bin over the warps.
 int64_t column_deal_mult(int64_t n);
 __global__ void k_slot_caps(const int64_t *op, int64_t nB, int64_t mrows, int64_t *caps);
-cudaError_t launch_slot_copy(int64_t nB, const int64_t *Ccp, const int64_t *soff, const int32_t *srow,
-                             const void *sval, int32_t *Crow, void *Cval, int w, int sms, cudaStream_t s);
+// Single pass: C's entries from the slots (two launches: the first column
+// of every tile of C's positions into tile_col, copy_tile_count(nnzC) ints,
+// then the tiles).
+cudaError_t launch_slot_copy(int64_t nB, int64_t nnzC, const int64_t *Ccp, const int64_t *soff, int32_t *tile_col,
+                             const int32_t *srow, const void *sval, int32_t *Crow, void *Cval, int w, int sms,
+                             cudaStream_t s);
+int64_t copy_tile_count(int64_t n);
 __global__ void k_bin_scatter(const int64_t *op, int64_t nB, int64_t t, int64_t hmax, int promote,
                               BinOffsets off, int32_t *bin_cols, Ctrl *ctrl);
 

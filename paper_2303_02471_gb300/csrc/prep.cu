@@ -211,54 +211,109 @@ __global__ void k_slot_caps(const int64_t *__restrict__ op, int64_t nB, int64_t 
     }
 }
 
-// Single pass: every column's entries from its slot (soff[j]) to its place
-// in C (Ccp[j]); a warp per column, W-byte values.
+// Single pass: every entry of C from its column's slot to its place in C.
+// The positions of C are cut into tiles of kCopyTile entries, each copied by
+// one CTA with coalesced stores, so a column of any length is spread over
+// as many CTAs as its tiles (a warp per column left the longest columns of
+// a power-law matrix to single warps).  k_tile_cols records the column
+// holding each tile's first position; k_tile_copy then takes the tile's
+// columns 256 at a time (their first positions and slot offsets staged in
+// shared memory), and every thread finds its positions' columns by a binary
+// search there.
+constexpr int64_t kCopyTile = 4096;
+constexpr int kCopyThreads = 256;
+
+__global__ void k_tile_cols(int64_t nB, const int64_t *__restrict__ Ccp, int32_t *__restrict__ tile_col) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nB; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c0 = Ccp[j], c1 = Ccp[j + 1];
+        for (int64_t k = (c0 + kCopyTile - 1) / kCopyTile; k * kCopyTile < c1; ++k) tile_col[k] = (int32_t)j;
+    }
+}
+
 template <typename W>
-__global__ void k_slot_copy(int64_t nB, const int64_t *__restrict__ Ccp, const int64_t *__restrict__ soff,
-                            const int32_t *__restrict__ srow, const W *__restrict__ sval, int32_t *__restrict__ Crow,
-                            W *__restrict__ Cval) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nB; j += nw) {
-        const int64_t c0 = Ccp[j], s0 = soff[j], cap = soff[j + 1] - s0;
-        int64_t n = Ccp[j + 1] - c0;
-        if (n > cap) n = cap;  // a count never exceeds its slot; reads stay inside the slots
-        // four loads in flight per lane before the stores
-        for (int64_t i = lane; i < n; i += 128) {
-            int32_t r[4];
-            W v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t x = i + 32 * u;
-                if (x < n) {
-                    r[u] = srow[s0 + x];
-                    v[u] = sval[s0 + x];
-                }
+__global__ void __launch_bounds__(kCopyThreads) k_tile_copy(int64_t nB, int64_t nnzC, const int64_t *__restrict__ Ccp,
+                                                           const int64_t *__restrict__ soff,
+                                                           const int32_t *__restrict__ tile_col,
+                                                           const int32_t *__restrict__ srow,
+                                                           const W *__restrict__ sval, int32_t *__restrict__ Crow,
+                                                           W *__restrict__ Cval) {
+    __shared__ int64_t s_c[kCopyThreads + 1];  // first positions in C of the group's columns, then its end
+    __shared__ int64_t s_s[kCopyThreads + 1];  // their slot offsets (slot of column i: [s_s[i], s_s[i + 1]))
+    for (int64_t k = blockIdx.x; k * kCopyTile < nnzC; k += gridDim.x) {
+        const int64_t p_lo = k * kCopyTile;
+        const int64_t p_hi = p_lo + kCopyTile < nnzC ? p_lo + kCopyTile : nnzC;
+        int64_t jg = tile_col[k];
+        for (;;) {
+            const int G = (int)(nB - jg < kCopyThreads ? nB - jg : kCopyThreads);
+            if (threadIdx.x < G) {
+                s_c[threadIdx.x] = Ccp[jg + threadIdx.x];
+                s_s[threadIdx.x] = soff[jg + threadIdx.x];
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t x = i + 32 * u;
-                if (x < n) {
-                    Crow[c0 + x] = r[u];
-                    Cval[c0 + x] = v[u];
-                }
+            if (threadIdx.x == 0) {  // the group's end (jg + G <= nB)
+                s_c[G] = Ccp[jg + G];
+                s_s[G] = soff[jg + G];
             }
+            __syncthreads();
+            const int64_t g_lo = p_lo > s_c[0] ? p_lo : s_c[0];
+            const int64_t g_hi = p_hi < s_c[G] ? p_hi : s_c[G];
+            for (int64_t p0 = g_lo; p0 < g_hi; p0 += 4 * kCopyThreads) {
+                int32_t r[4];
+                W v[4];
+                int64_t dst[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t p = p0 + u * kCopyThreads + threadIdx.x;
+                    dst[u] = -1;
+                    if (p < g_hi) {
+                        // the last column starting at or before p (s_c[0] <= p < s_c[G]): it holds p
+                        int lo = 0, hi = G - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_c[mid] <= p) lo = mid; else hi = mid - 1;
+                        }
+                        const int64_t off = p - s_c[lo];
+                        // a count never exceeds its slot; reads stay inside the slots
+                        if (off < s_s[lo + 1] - s_s[lo]) {
+                            r[u] = srow[s_s[lo] + off];
+                            v[u] = sval[s_s[lo] + off];
+                            dst[u] = p;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (dst[u] >= 0) {
+                        Crow[dst[u]] = r[u];
+                        Cval[dst[u]] = v[u];
+                    }
+            }
+            const bool more = s_c[G] < p_hi;  // uniform over the CTA
+            __syncthreads();
+            if (!more) break;
+            jg += G;
         }
     }
 }
 
-cudaError_t launch_slot_copy(int64_t nB, const int64_t *Ccp, const int64_t *soff, const int32_t *srow,
-                             const void *sval, int32_t *Crow, void *Cval, int w, int sms, cudaStream_t s) {
-    if (nB <= 0) return cudaSuccess;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nB, 8), 16 * (int64_t)sms));
+cudaError_t launch_slot_copy(int64_t nB, int64_t nnzC, const int64_t *Ccp, const int64_t *soff, int32_t *tile_col,
+                             const int32_t *srow, const void *sval, int32_t *Crow, void *Cval, int w, int sms,
+                             cudaStream_t s) {
+    if (nB <= 0 || nnzC <= 0) return cudaSuccess;
+    const int gc = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nB, 256), 8 * (int64_t)sms));
+    k_tile_cols<<<gc, 256, 0, s>>>(nB, Ccp, tile_col);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nnzC, kCopyTile), 8 * (int64_t)sms));
     if (w == 8)
-        k_slot_copy<uint64_t><<<g, 256, 0, s>>>(nB, Ccp, soff, srow, static_cast<const uint64_t *>(sval), Crow,
-                                                  static_cast<uint64_t *>(Cval));
+        k_tile_copy<uint64_t><<<g, kCopyThreads, 0, s>>>(nB, nnzC, Ccp, soff, tile_col, srow,
+                                                         static_cast<const uint64_t *>(sval), Crow,
+                                                         static_cast<uint64_t *>(Cval));
     else
-        k_slot_copy<uint32_t><<<g, 256, 0, s>>>(nB, Ccp, soff, srow, static_cast<const uint32_t *>(sval), Crow,
-                                                  static_cast<uint32_t *>(Cval));
+        k_tile_copy<uint32_t><<<g, kCopyThreads, 0, s>>>(nB, nnzC, Ccp, soff, tile_col, srow,
+                                                         static_cast<const uint32_t *>(sval), Crow,
+                                                         static_cast<uint32_t *>(Cval));
     return cudaGetLastError();
 }
+
+int64_t copy_tile_count(int64_t n) { return n / kCopyTile + 2; }
 
 // Column ids into per-bin lists at off[bin] (each block reserves its slots
 // with one global atomic per bin, so columns of a bin stay roughly in

@@ -487,6 +487,25 @@ def test_single_pass_workload1_and_tall():
         assert_matches_oracle(C, A, B, nthreads=NCPU)
 
 
+@pytest.mark.parametrize("t", [0, INF])
+def test_single_pass_long_columns_and_empty_runs(t):
+    """The copy into C spreads a column over as many tiles of C's positions
+    as it spans and skips runs of empty columns: a few columns of tens of
+    thousands of entries among runs of empty and one-entry columns."""
+    rng = np.random.default_rng(41)
+    A = _tall(60000, 64, 400, 800, seed=40)
+    n = 700
+    z = np.zeros(n, dtype=np.int64)
+    z[rng.choice(n, 150, replace=False)] = 1   # one-entry columns
+    z[[3, 350, 351, 699]] = 64                  # long columns of C
+    rows = np.concatenate([rng.choice(64, int(k), replace=False) for k in z])
+    cols = np.repeat(np.arange(n), z)
+    B = synth.from_coo(64, n, rows, cols, rng.standard_normal(rows.size))
+    C, _ = _single(A, B, t=t)
+    assert C.nnz > 4 * 40000
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
 def test_single_pass_plan_serves_numeric_and_backward():
     import torch
     from paper_2303_02471_gb300 import ops
