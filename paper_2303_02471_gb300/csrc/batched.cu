@@ -292,7 +292,8 @@ __device__ __forceinline__ bool warp_dense_numeric(const TOps<VT> &o, int32_t j,
                                       [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
     }
     __syncwarp();
-    const int per = (W + 31) >> 5;
+    // an odd run per lane: the lanes' words fall in different shared-memory banks
+    const int per = ((W + 31) >> 5) | 1;
     const int w0 = lane * per < W ? lane * per : W;
     const int w1 = w0 + per < W ? w0 + per : W;
     int cnt = 0;
