@@ -284,7 +284,16 @@ __device__ __forceinline__ bool warp_dense_numeric(const TOps<VT> &o, int32_t j,
                                                    int W, const uint32_t *keep, int32_t *Crow, VT *Cval) {
     const int lane = threadIdx.x & 31;
     if (keep) {
-        for (int w = lane; w < W; w += 32) bm[w] = make_uint2(keep[w], 0u);
+        // four loads in flight per lane before their stores (the kept flags
+        // come from DRAM)
+        for (int w0 = lane; w0 < W; w0 += 128) {
+            uint32_t x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = w0 + 32 * u < W ? __ldg(keep + w0 + 32 * u) : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (w0 + 32 * u < W) bm[w0 + 32 * u] = make_uint2(x[u], 0u);
+        }
     } else {
         for (int w = lane; w < W; w += 32) bm[w] = make_uint2(0u, 0u);
         __syncwarp();
