@@ -607,7 +607,8 @@ def run_ours(args, rank, world):
                     entry[acc] = measure_workload(k, args, dev, flush, ksteps, 3, *peak_w,
                                                   cfg=ops.Config(small_accumulator=acc))
             aux = {"workloads": others, "batched": run_batched(args, dev, *peak_w),
-                   "backward": run_backward(args, dev, *peak_w)}
+                   "backward": run_backward(args, dev, *peak_w),
+                   "shards": run_shards(A_h, B_h, dev, flush, ms, prod)}
             if not args.no_sweep:
                 aux["t_sweep"] = run_t_sweep(args, dev, flush)
         line = {"metric": METRIC, "value": round(value, 3),
@@ -750,6 +751,33 @@ def run_batched(args, dev, peak, peak_kind):
                          "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                          "algorithmic_bytes": int(alg), "ms": round(num_ms, 4), "peak_kind": peak_kind},
             "launches_symbolic_numeric": launches[:2]}
+
+
+def run_shards(A_h, B_h, dev, flush, whole_ms, prod):
+    """Column shards of the headline product (the columns of C are
+    independent, Section 2.1): B cut into 2, 4 and 8 column blocks of about
+    equal sum of Op_j (shard.column_ranges), each block's product (A
+    replicated) timed on this GPU as a whole step.  The slowest block bounds a
+    run of that many GPUs, one block each, with no collective; `balance` is
+    the mean block time over the slowest."""
+    from paper_2303_02471_gb300 import ops, shard
+    plan = prod.plan()
+    op = plan.op_counts().cpu().numpy()
+    plan.destroy()
+    out = {}
+    for world in (2, 4, 8):
+        ms = []
+        for s, e in shard.column_ranges(op, world):
+            blk = Product(A_h, shard.column_block(B_h, s, e), dev, ops.Config())
+            res = time_steps(blk, 3, 1, flush, bin_timing=False)
+            ms.append(float(np.median(res["step"])))
+            del blk
+        mx = max(ms)
+        out[str(world)] = {"ms_per_block": [round(x, 4) for x in ms], "ms_slowest": round(mx, 4),
+                           "ms_sum": round(sum(ms), 4), "speedup_bound": round(whole_ms / mx, 3),
+                           "balance": round(float(np.mean(ms)) / mx, 3)}
+    out["whole_ms"] = round(whole_ms, 4)
+    return out
 
 
 def run_backward(args, dev, peak, peak_kind):

@@ -149,7 +149,7 @@ def tune(As, Bs, grid: Optional[dict] = None, repeats: int = 2, cache: Optional[
         os.replace(tmp, path)
     except OSError:
         pass
-    return Config(**best["config"]), entry
+    return Config(**entry["config"]), entry
 
 
 PRODUCT_GRID = {
@@ -236,4 +236,4 @@ def tune_product(A, B, grid: Optional[dict] = None, repeats: int = 2, cache: Opt
         os.replace(tmp, path)
     except OSError:
         pass
-    return Config(**best["config"]), entry
+    return Config(**entry["config"]), entry
