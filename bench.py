@@ -92,8 +92,8 @@ def peaks():
 # algorithmic bytes.  Valid only for the kernel sources it was taken with:
 # the hash below covers the files that define that kernel, and any change
 # there reports null.
-MEASURED_TRAFFIC = {"bin": 13, "scale": 17, "bytes": 425817088 + 1974770944, "algorithmic_bytes": 5313831440,
-                    "sources_sha256_16": "680ad82e7be2f523",
+MEASURED_TRAFFIC = {"bin": 13, "scale": 17, "bytes": 426855936 + 1975134720, "algorithmic_bytes": 5313831440,
+                    "sources_sha256_16": "fa872616b299795e",
                     "sources": ("spgemm_internal.cuh", "kernels.cuh", "columns.cuh", "numeric.cu")}
 
 

@@ -284,7 +284,7 @@ __device__ __forceinline__ bool num_dense_column(const TOps<VT> &o, int32_t j, i
     // flags kept from the symbolic phase are read straight into the prefix
     // pass; otherwise the walk sets them again
     if (!keep)
-        cta_walk<false, VT>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
+        cta_walk<false, VT, kSymWalkAhead>(o.Acp, o.Arow, o.Aval, o.Brow, o.Bval, o.Bcp[j], o.Bcp[j + 1], w,
                             [&](int32_t row, VT) { atomicOr(&bm[row >> 5].x, 1u << (row & 31)); });
     const int64_t total = cta_bitmap_prefix(bm, W, keep, s_warp);
     after_prefix();

@@ -126,8 +126,10 @@ constexpr int kLongEntry = 32;
 // walk (cta_walk's AHEAD; other callers keep one): four 256-thread CTAs per
 // SM leave 64 registers a thread, which hold five without spilling.
 constexpr int kWalkAhead = 5;
-// The same for the dense bin's flag walk (rows only, one register a window;
-// eight 256-thread CTAs per SM leave 32 registers a thread).
+// The same for the dense bin's flag walks (rows only, one register a window;
+// eight 256-thread CTAs per SM leave the symbolic kernel 32 registers a
+// thread): the symbolic phase's, and the numeric kernel's when no flags were
+// kept (the single pass).
 constexpr int kSymWalkAhead = 4;
 
 // Inclusive block scan of four int32 counters packed as two int64 lanes

@@ -256,6 +256,9 @@ __global__ void __launch_bounds__(kCopyThreads) k_tile_copy(int64_t nB, int64_t 
             __syncthreads();
             const int64_t g_lo = p_lo > s_c[0] ? p_lo : s_c[0];
             const int64_t g_hi = p_hi < s_c[G] ? p_hi : s_c[G];
+            // every position of the tile in the group's first column (a long
+            // column): no search
+            const bool one = G == 1 || s_c[1] >= g_hi;
             for (int64_t p0 = g_lo; p0 < g_hi; p0 += 4 * kCopyThreads) {
                 int32_t r[4];
                 W v[4];
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(kCopyThreads) k_tile_copy(int64_t nB, int64_t 
                     dst[u] = -1;
                     if (p < g_hi) {
                         // the last column starting at or before p (s_c[0] <= p < s_c[G]): it holds p
-                        int lo = 0, hi = G - 1;
+                        int lo = 0, hi = one ? 0 : G - 1;
                         while (lo < hi) {
                             const int mid = (lo + hi + 1) >> 1;
                             if (s_c[mid] <= p) lo = mid; else hi = mid - 1;
