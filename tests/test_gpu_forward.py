@@ -487,8 +487,9 @@ def test_single_pass_workload1_and_tall():
         assert_matches_oracle(C, A, B, nthreads=NCPU)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
 @pytest.mark.parametrize("t", [0, INF])
-def test_single_pass_long_columns_and_empty_runs(t):
+def test_single_pass_long_columns_and_empty_runs(t, dtype):
     """The copy into C spreads a column over as many tiles of C's positions
     as it spans and skips runs of empty columns: a few columns of tens of
     thousands of entries among runs of empty and one-entry columns."""
@@ -501,6 +502,7 @@ def test_single_pass_long_columns_and_empty_runs(t):
     rows = np.concatenate([rng.choice(64, int(k), replace=False) for k in z])
     cols = np.repeat(np.arange(n), z)
     B = synth.from_coo(64, n, rows, cols, rng.standard_normal(rows.size))
+    A, B = A.with_values(A.values.astype(dtype)), B.with_values(B.values.astype(dtype))
     C, _ = _single(A, B, t=t)
     assert C.nnz > 4 * 40000
     assert_matches_oracle(C, A, B, nthreads=NCPU)
