@@ -61,6 +61,9 @@ def parse(argv=None):
     p.add_argument("--no-aux", action="store_true",
                    help="skip the other workloads (random 2^20, batch, backward) and the t sweep")
     p.add_argument("--no-sweep", action="store_true", help="skip the sweep of the threshold t")
+    p.add_argument("--batched-only", type=int, default=0, metavar="N",
+                   help="only the batched measurement, on the first N products of the seeded batch, "
+                        "with t=33, 128 threads (no tuner); for a small profiling case")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU seconds of the oracle sample")
     p.add_argument("--t", type=int, default=None,
@@ -634,18 +637,24 @@ def _events(n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
-def run_batched(args, dev, peak, peak_kind):
+def run_batched(args, dev, peak, peak_kind, count=512, fixed=None):
     """The 512-product batch: autotuned persistent launches (symbolic + numeric,
     numeric replayed from a CUDA graph) against the plain per-matrix calls
-    through the C ABI with preallocated workspaces and outputs."""
+    through the C ABI with preallocated workspaces and outputs.  `count`
+    takes the first products of the seeded batch; `fixed` (a Config) skips the
+    tuner."""
     import torch
     from paper_2303_02471_gb300 import _native as N
     from paper_2303_02471_gb300 import autotune, ops, synth
-    pairs = synth.batch_pairs(512, seed=0)
+    pairs = synth.batch_pairs(512, seed=0)[:count]
     As = [ops.CscMatrix.from_host(A, device=dev) for A, _ in pairs]
     Bs = [ops.CscMatrix.from_host(B, device=dev) for _, B in pairs]
     products = int(sum(A.ncols * (A.colptr[1] - A.colptr[0]) ** 2 for A, _ in pairs))
-    cfg, rep = autotune.tune(As, Bs, repeats=1)
+    if fixed is not None:
+        cfg, rep = fixed, {"config": {"t": fixed.t, "hash_cta_max": fixed.hash_cta_max,
+                                      "cta_threads": fixed.cta_threads}}
+    else:
+        cfg, rep = autotune.tune(As, Bs, repeats=1)
     side = torch.cuda.Stream(device=dev)
     steps = max(3, min(args.steps, 10))
     lib = N.lib()
@@ -746,7 +755,7 @@ def run_batched(args, dev, peak, peak_kind):
             "GFLOPs_batched_numeric_graph": gf(num_ms), "ms_batched_numeric_graph": round(num_ms, 3),
             "GFLOPs_plain_per_matrix": gf(plain_ms), "ms_plain_per_matrix": round(plain_ms, 3),
             "GFLOPs_plain_numeric_only": gf(plain_num_ms), "ms_plain_numeric_only": round(plain_num_ms, 3),
-            "plain": "512 x (spgemm_symbolic + spgemm_numeric) through the C ABI, buffers preallocated",
+            "plain": f"{count} x (spgemm_symbolic + spgemm_numeric) through the C ABI, buffers preallocated",
             "roofline": {"bound": "hbm", "kernel": "k_batched numeric (one persistent launch, graph replay)",
                          "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                          "algorithmic_bytes": int(alg), "ms": round(num_ms, 4), "peak_kind": peak_kind},
@@ -1023,7 +1032,13 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    line = run_ours(args, rank, world)
+    if args.batched_only > 0:
+        from paper_2303_02471_gb300 import ops
+        peak, kind = peaks()
+        line = {"batched": run_batched(args, "cuda:0", peak, kind, count=args.batched_only,
+                                       fixed=ops.Config(t=33, hash_cta_max=8192, cta_threads=128))}
+    else:
+        line = run_ours(args, rank, world)
     if line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
