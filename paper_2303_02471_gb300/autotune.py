@@ -6,6 +6,8 @@ configurations on the products themselves.  A second stage then tries, around
 the best of the grid, the hash-table size (slots per output entry) and the
 lanes per light column (how many lane-group bins a light column moves up):
 the table sizes and threads per column of Section 3.2's hash accumulation.
+For a single product a last stage times the pick in the single-pass form too
+and reports the faster form (`form` in the report).
 
 The paper fixes t = 40 for its vector unit and studies t, b_min and b_max by
 hand (Section 5.4); here the choice is measured on the GPU and cached per GPU
@@ -38,6 +40,9 @@ REFINE = {
     "table_slots_pct": [150, 250],
     "group_promote": [0, 1],
 }
+# Forms of a single product tried last with the pick (grid key "form"): both
+# phases, or the single pass (Op_j-sized slots, then a copy into C).
+FORMS = ["two_pass", "single_pass"]
 
 
 def _with_defaults(conf: dict, refine: dict) -> dict:
@@ -190,6 +195,26 @@ def _time_product(A, B, cfg: Config, repeats: int) -> float:
     return best
 
 
+def _time_single_pass(A, B, cfg: Config, repeats: int) -> float:
+    ws = torch.empty(max(ops.single_pass_workspace_size(A, B, cfg), 256), dtype=torch.uint8, device=A.device)
+    C, plan = ops.spgemm_single_pass(A, B, cfg, workspace=ws)
+    plan.check()
+    plan.destroy()
+    del C
+    stream = torch.cuda.current_stream()
+    best = float("inf")
+    for _ in range(repeats):
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        C, p = ops.spgemm_single_pass(A, B, cfg, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+        p.destroy()
+        del C
+    return best
+
+
 def tune_product(A, B, grid: Optional[dict] = None, repeats: int = 2, cache: Optional[str] = None,
                  refresh: bool = False):
     """Best Config for one product C = A B, timed as a whole step (symbolic
@@ -206,9 +231,10 @@ def tune_product(A, B, grid: Optional[dict] = None, repeats: int = 2, cache: Opt
             table = {}
     if key in table and not refresh:
         return Config(**table[key]["config"]), table[key]
-    grid = grid or dict(PRODUCT_GRID, **REFINE)
+    grid = grid or dict(PRODUCT_GRID, **REFINE, form=FORMS)
     refine = {n: grid[n] for n in REFINE if n in grid}
-    names = sorted(n for n in grid if n not in refine)
+    forms = grid.get("form", [])
+    names = sorted(n for n in grid if n not in refine and n != "form")
     results = []
     for values in itertools.product(*(grid[n] for n in names)):
         conf = dict(zip(names, values))
@@ -226,7 +252,17 @@ def tune_product(A, B, grid: Optional[dict] = None, repeats: int = 2, cache: Opt
         _refine(best["config"], lambda conf: _time_product(A, B, Config(**conf), repeats), results, refine)
         ok = [r for r in results if np.isfinite(r["ms"])]
     best = min(ok, key=lambda r: r["ms"])
-    entry = {"config": _with_defaults(best["config"], refine), "ms": best["ms"], "candidates": results}
+    form, best_ms = "two_pass", best["ms"]
+    if "single_pass" in forms:
+        # the pick's configuration in the single pass (whole call, copy included)
+        try:
+            ms, err = _time_single_pass(A, B, Config(**best["config"]), repeats), None
+        except RuntimeError as e:
+            ms, err = float("inf"), str(e)
+        results.append({"config": dict(best["config"], form="single_pass"), "ms": ms, "error": err})
+        if ms < best_ms:
+            form, best_ms = "single_pass", ms
+    entry = {"config": _with_defaults(best["config"], refine), "form": form, "ms": best_ms, "candidates": results}
     table[key] = entry
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)

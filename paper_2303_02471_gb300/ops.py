@@ -357,8 +357,8 @@ def spgemm_single_pass(A: CscMatrix, B: CscMatrix, config: Optional[Config] = No
     config = config or Config()
     hd = lib_handle if lib_handle is not None else handle(A.device)
     cA, cB = _csc(A), _csc(B, A.dtype)
-    need = single_pass_workspace_size(A, B, config, hd)
-    if workspace is None or workspace.numel() < need:
+    if workspace is None:  # a workspace given is checked by the call itself
+        need = single_pass_workspace_size(A, B, config, hd)
         workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
     colptr = torch.empty(B.ncols + 1, dtype=torch.int64, device=A.device)
     nnz = ctypes.c_int64()

@@ -262,3 +262,10 @@ def test_product_autotune_chooses_and_caches(tmp_path):
     C, plan = ops.spgemm(dA, dA, cfg)
     plan.check()
     assert_matches_oracle(C, A, A)
+    # last stage: the pick timed in the single-pass form too
+    cfg3, rep3 = autotune.tune_product(dA, dA, grid=dict(grid, form=["two_pass", "single_pass"]), repeats=1,
+                                       cache=path, refresh=True)
+    assert len(rep3["candidates"]) == 4 + 1 and rep3["form"] in ("two_pass", "single_pass")
+    C, plan = ops.spgemm_single_pass(dA, dA, cfg3)
+    plan.check()
+    assert_matches_oracle(C, A, A)
