@@ -10,8 +10,14 @@
 //             its value;
 //   Sort      a stable LSD radix sort of the keys (digits of kEscRadixBits
 //             bits; a lane's place among the lanes with the same digit comes
-//             from __match_any_sync), which orders the products by column
-//             and, inside a column, by row;
+//             from one ballot per digit bit), which orders the products by
+//             column and, inside a column, by row.  In bins of short columns
+//             (Op_j <= kEscRankOpMax) each product instead counts the
+//             products of its own column that precede it in (row, position
+//             of expansion) order: the products are expanded column after
+//             column, so that count plus the column's first position is the
+//             product's place in the sorted tile, the same place the stable
+//             radix sort gives it;
 //   Compress  equal keys are neighbours: the first of each run sums the run
 //             in sorted order and writes one entry of C at its column's
 //             pointer plus its rank among the column's runs.
@@ -157,6 +163,8 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 over = true;
                 break;
             }
+            // products per column place (the rank sort's column bounds)
+            if (e.rank && en < E && z > 0) atomicAdd(&S.cnt[0][c], (uint32_t)z);
             for (int q0 = 0; q0 < total; q0 += 32) {
                 const int q = q0 + lane;
                 const int s = esc_owner(zexcl, q < total ? q : total - 1);
@@ -169,12 +177,16 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                     const int64_t qa = a0s + (q - exs);
                     const int32_t row = ld_keep(ops.Arow + qa, pol);
                     const uint32_t key = ((uint32_t)cs << e.rb) | ((uint32_t)row & rowmask);
-                    S.key[0][n + q] = key;
-                    atomicAdd(&S.cnt[0][key & DM], 1u);
-                    if constexpr (VALS) {
-                        S.val[n + q] = ld_keep(ops.Aval + qa, pol) * bs;
-                        S.idx[0][n + q] = (uint8_t)(n + q);
+                    if (e.rank) {
+                        // the key with its position of expansion below it:
+                        // distinct, ordered as the stable sort orders them
+                        S.key[1][n + q] = (key << 8) | (uint32_t)(n + q);
+                    } else {
+                        S.key[0][n + q] = key;
+                        atomicAdd(&S.cnt[0][key & DM], 1u);
+                        if constexpr (VALS) S.idx[0][n + q] = (uint8_t)(n + q);
                     }
+                    if constexpr (VALS) S.val[n + q] = ld_keep(ops.Aval + qa, pol) * bs;
                 }
             }
             n += total;
@@ -187,6 +199,43 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
         // ---- sort: stable LSD radix over the key bits.  The counts of pass
         // p + 1's digits are taken while pass p scatters the keys.
         int cur = 0;
+        if (e.rank) {
+            // column place l's products are positions [beg, end) of lane l
+            const int pc = lane < nc ? (int)S.cnt[0][lane] : 0;
+            int pincl = pc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, pincl, d);
+                if (lane >= d) pincl += v;
+            }
+            const int pbeg = pincl - pc;
+            // keys above every composite key up to the next multiple of 4
+            const int n4 = (n + 3) & ~3;
+            if (n + lane < n4) S.key[1][n + lane] = 0xffffffffu;
+            __syncwarp();
+            for (int i0 = 0; i0 < n; i0 += 32) {
+                const int i = i0 + lane;
+                const bool valid = i < n;
+                const uint32_t me = valid ? S.key[1][i] : 0u;
+                const int c = (int)(me >> (e.rb + 8)) & 31;
+                const int b = __shfl_sync(0xffffffffu, pbeg, c);
+                const int en = __shfl_sync(0xffffffffu, pincl, c);
+                if (valid) {
+                    // every position before lo holds an earlier column (a
+                    // smaller key) and every one from hi on a later column or
+                    // a pad: the count over [lo, hi) completes the place
+                    const int lo = b & ~3, hi = (en + 3) & ~3;
+                    int at = lo;
+                    for (int q = lo; q < hi; q += 4) {
+                        const uint4 k4 = *reinterpret_cast<const uint4 *>(&S.key[1][q]);
+                        at += (int)(k4.x < me) + (int)(k4.y < me) + (int)(k4.z < me) + (int)(k4.w < me);
+                    }
+                    S.key[0][at] = me >> 8;
+                    if constexpr (VALS) S.idx[0][at] = (uint8_t)(me & 0xffu);
+                }
+            }
+            __syncwarp();
+        }
         const unsigned vm_all = 0xffffffffu;
         for (int pass = 0; pass < e.passes; ++pass) {
             const int sh = pass * kEscRadixBits;
@@ -343,7 +392,9 @@ bool esc_shape(int bin, int64_t m, EscShape &e) {
     e.rb = rb;
     const int bits = rb + cb;
     if (bits > 32) return false;
-    e.passes = (bits + kEscRadixBits - 1) / kEscRadixBits;
+    // the rank sort's composite keys carry 8 bits of position (kEscTile)
+    e.rank = opmax <= kEscRankOpMax && bits + 8 <= 32;
+    e.passes = e.rank ? 0 : (bits + kEscRadixBits - 1) / kEscRadixBits;
     return true;
 }
 

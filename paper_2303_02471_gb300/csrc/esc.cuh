@@ -8,13 +8,18 @@ namespace spg {
 constexpr int kEscWarps = 8;       // warps per CTA, each working its own tiles
 constexpr int kEscTile = 256;      // products one warp tile holds
 constexpr int kEscRadixBits = 8;   // digit width of the radix sort
+// Bins whose largest Op_j is at most this sort by counting within columns
+// (see k_esc) instead of the radix sort.
+constexpr int kEscRankOpMax = 32;
 
-// Tile shape of one lane-group bin: columns per tile, row bits of the keys
-// and radix passes over the key bits.
+// Tile shape of one lane-group bin: columns per tile, row bits of the keys,
+// radix passes over the key bits, and whether the tile is sorted by ranks
+// counted within columns (rank != 0) instead.
 struct EscShape {
     int ct = 0;
     int rb = 0;
     int passes = 0;
+    int rank = 0;
 };
 
 // Shape of bin `bin` for a product whose forward passes number m rows; false
