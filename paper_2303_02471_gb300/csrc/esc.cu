@@ -17,7 +17,10 @@
 //             of expansion) order: the products are expanded column after
 //             column, so that count plus the column's first position is the
 //             product's place in the sorted tile, the same place the stable
-//             radix sort gives it;
+//             radix sort gives it.  Where (column, row, position) fits 32
+//             bits the count runs over 16-byte words of an aligned window
+//             around the column, else over the column's (row, position)
+//             pairs alone;
 //   Compress  equal keys are neighbours: the first of each run sums the run
 //             in sorted order and writes one entry of C at its column's
 //             pointer plus its rank among the column's runs.
@@ -55,6 +58,9 @@ struct EscWarp<true, VT> {
     uint8_t idx[2][kEscTile];
 };
 
+// the exact-form rank sort keeps the sorted keys in cnt[1]
+static_assert((1 << kEscRadixBits) >= kEscTile, "radix count space holds a tile");
+
 template <bool VALS, typename VT>
 __host__ __device__ constexpr size_t esc_warp_bytes() {
     return (sizeof(EscWarp<VALS, VT>) + 15) & ~size_t(15);
@@ -77,7 +83,7 @@ __device__ __forceinline__ int esc_owner(int excl, int q) {
     return s;
 }
 
-template <bool VALS, typename VT>
+template <bool VALS, typename VT, int FORM>
 __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
     k_esc(BinTask t, Operands o, const int64_t *base, int64_t *cnt_out, int32_t *Crow, VT *Cval, EscShape e) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 break;
             }
             // products per column place (the rank sort's column bounds)
-            if (e.rank && en < E && z > 0) atomicAdd(&S.cnt[0][c], (uint32_t)z);
+            if (FORM != kEscRadix && en < E && z > 0) atomicAdd(&S.cnt[0][c], (uint32_t)z);
             for (int q0 = 0; q0 < total; q0 += 32) {
                 const int q = q0 + lane;
                 const int s = esc_owner(zexcl, q < total ? q : total - 1);
@@ -177,10 +183,14 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                     const int64_t qa = a0s + (q - exs);
                     const int32_t row = ld_keep(ops.Arow + qa, pol);
                     const uint32_t key = ((uint32_t)cs << e.rb) | ((uint32_t)row & rowmask);
-                    if (e.rank) {
-                        // the key with its position of expansion below it:
-                        // distinct, ordered as the stable sort orders them
+                    // rank sort: the key (window form) or the row (exact
+                    // form) with the position of expansion below it: distinct,
+                    // and ordered as the stable radix sort orders the keys
+                    if constexpr (FORM == kEscRankWindow) {
                         S.key[1][n + q] = (key << 8) | (uint32_t)(n + q);
+                    } else if constexpr (FORM == kEscRankExact) {
+                        S.key[0][n + q] = key;
+                        S.key[1][n + q] = (((uint32_t)row & rowmask) << 8) | (uint32_t)(n + q);
                     } else {
                         S.key[0][n + q] = key;
                         atomicAdd(&S.cnt[0][key & DM], 1u);
@@ -196,10 +206,11 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
             continue;
         }
         __syncwarp();
-        // ---- sort: stable LSD radix over the key bits.  The counts of pass
-        // p + 1's digits are taken while pass p scatters the keys.
+        // ---- sort: ranks counted within columns, or a stable LSD radix sort
+        // over the key bits (the counts of pass p + 1's digits are taken while
+        // pass p scatters the keys)
         int cur = 0;
-        if (e.rank) {
+        if constexpr (FORM != kEscRadix) {
             // column place l's products are positions [beg, end) of lane l
             const int pc = lane < nc ? (int)S.cnt[0][lane] : 0;
             int pincl = pc;
@@ -209,35 +220,59 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 if (lane >= d) pincl += v;
             }
             const int pbeg = pincl - pc;
-            // keys above every composite key up to the next multiple of 4
-            const int n4 = (n + 3) & ~3;
-            if (n + lane < n4) S.key[1][n + lane] = 0xffffffffu;
-            __syncwarp();
+            if constexpr (FORM == kEscRankWindow) {
+                // composite keys above every other up to the next multiple of 4
+                const int n4 = (n + 3) & ~3;
+                if (n + lane < n4) S.key[1][n + lane] = 0xffffffffu;
+                __syncwarp();
+            }
             for (int i0 = 0; i0 < n; i0 += 32) {
                 const int i = i0 + lane;
                 const bool valid = i < n;
                 const uint32_t me = valid ? S.key[1][i] : 0u;
-                const int c = (int)(me >> (e.rb + 8)) & 31;
-                const int b = __shfl_sync(0xffffffffu, pbeg, c);
-                const int en = __shfl_sync(0xffffffffu, pincl, c);
-                if (valid) {
-                    // every position before lo holds an earlier column (a
-                    // smaller key) and every one from hi on a later column or
-                    // a pad: the count over [lo, hi) completes the place
-                    const int lo = b & ~3, hi = (en + 3) & ~3;
-                    int at = lo;
-                    for (int q = lo; q < hi; q += 4) {
-                        const uint4 k4 = *reinterpret_cast<const uint4 *>(&S.key[1][q]);
-                        at += (int)(k4.x < me) + (int)(k4.y < me) + (int)(k4.z < me) + (int)(k4.w < me);
+                if constexpr (FORM == kEscRankWindow) {
+                    const int c = (int)(me >> (e.rb + 8)) & 31;
+                    const int b = __shfl_sync(0xffffffffu, pbeg, c);
+                    const int en = __shfl_sync(0xffffffffu, pincl, c);
+                    if (valid) {
+                        // every position before lo holds an earlier column
+                        // (a smaller composite key) and every one from hi on
+                        // a later column or a pad: counting the smaller keys
+                        // in [lo, hi) completes the place
+                        const int lo = b & ~3, hi = (en + 3) & ~3;
+                        int at = lo;
+                        for (int q = lo; q < hi; q += 4) {
+                            const uint4 k4 = *reinterpret_cast<const uint4 *>(&S.key[1][q]);
+                            at += (int)(k4.x < me) + (int)(k4.y < me) + (int)(k4.z < me) + (int)(k4.w < me);
+                        }
+                        S.key[0][at] = me >> 8;
+                        if constexpr (VALS) S.idx[0][at] = (uint8_t)(me & 0xffu);
                     }
-                    S.key[0][at] = me >> 8;
-                    if constexpr (VALS) S.idx[0][at] = (uint8_t)(me & 0xffu);
+                } else {
+                    const uint32_t k = valid ? S.key[0][i] : 0u;
+                    const int c = (int)(k >> e.rb) & 31;
+                    const int b = __shfl_sync(0xffffffffu, pbeg, c);
+                    const int en = __shfl_sync(0xffffffffu, pincl, c);
+                    if (valid) {
+                        // the row composites of the column alone
+                        int at = b, q = b;
+                        for (; q + 4 <= en; q += 4) {
+                            const uint32_t x0 = S.key[1][q], x1 = S.key[1][q + 1];
+                            const uint32_t x2 = S.key[1][q + 2], x3 = S.key[1][q + 3];
+                            at += (int)(x0 < me) + (int)(x1 < me) + (int)(x2 < me) + (int)(x3 < me);
+                        }
+                        for (; q < en; ++q) at += (int)(S.key[1][q] < me);
+                        // key[0] is still being read: the sorted keys go to the
+                        // radix counts' space, free here
+                        S.cnt[1][at] = k;
+                        if constexpr (VALS) S.idx[1][at] = (uint8_t)i;
+                    }
                 }
             }
             __syncwarp();
         }
         const unsigned vm_all = 0xffffffffu;
-        for (int pass = 0; pass < e.passes; ++pass) {
+        for (int pass = 0; FORM == kEscRadix && pass < e.passes; ++pass) {
             const int sh = pass * kEscRadixBits;
             uint32_t *cnt = S.cnt[pass & 1];
             uint32_t *ncnt = S.cnt[(pass + 1) & 1];
@@ -299,14 +334,18 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
             cur ^= 1;
         }
         // ---- compress: the first key of each run writes the run's sum
+        constexpr bool moved = FORM == kEscRankExact;
+        const uint32_t *skey = moved ? S.cnt[1] : S.key[cur];
+        const uint8_t *sidx = nullptr;
+        if constexpr (VALS) sidx = moved ? S.idx[1] : S.idx[cur];
         if (lane < 32) S.hstart[lane] = 0x7fffffff;  // columns without runs stay unset
         __syncwarp();
         int hbase = 0;
         for (int i0 = 0; i0 < n; i0 += 32) {
             const int i = i0 + lane;
             const bool valid = i < n;
-            const uint32_t k = valid ? S.key[cur][i] : 0u;
-            const uint32_t kp = valid && i > 0 ? S.key[cur][i - 1] : 0u;
+            const uint32_t k = valid ? skey[i] : 0u;
+            const uint32_t kp = valid && i > 0 ? skey[i - 1] : 0u;
             const bool head = valid && (i == 0 || kp != k);
             const unsigned hm = __ballot_sync(0xffffffffu, head);
             const int hr = hbase + __popc(hm & lt);
@@ -318,8 +357,8 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 const int64_t cbase = __shfl_sync(0xffffffffu, cb, c & 31);
                 const int64_t cc = __shfl_sync(0xffffffffu, ccap, c & 31);
                 if (head) {
-                    VT sum = S.val[S.idx[cur][i]];
-                    for (int m2 = i + 1; m2 < n && S.key[cur][m2] == k; ++m2) sum += S.val[S.idx[cur][m2]];
+                    VT sum = S.val[sidx[i]];
+                    for (int m2 = i + 1; m2 < n && skey[m2] == k; ++m2) sum += S.val[sidx[m2]];
                     const int64_t r = hr - S.hstart[c];
                     // a column with more runs than its place holds is reported
                     // below and not written past its place
@@ -393,7 +432,10 @@ bool esc_shape(int bin, int64_t m, EscShape &e) {
     const int bits = rb + cb;
     if (bits > 32) return false;
     // the rank sort's composite keys carry 8 bits of position (kEscTile)
-    e.rank = opmax <= kEscRankOpMax && bits + 8 <= 32;
+    e.rank = opmax > kEscRankOpMax ? kEscRadix
+             : bits + 8 <= 32      ? kEscRankWindow
+             : rb + 8 <= 32        ? kEscRankExact
+                                   : kEscRadix;
     e.passes = e.rank ? 0 : (bits + kEscRadixBits - 1) / kEscRadixBits;
     return true;
 }
@@ -402,7 +444,9 @@ template <bool VALS, typename VT>
 static cudaError_t launch_esc_t(const BinTask &t, const Operands &o, const int64_t *base, int64_t *cnt_out,
                                 int32_t *Crow, VT *Cval, const EscShape &e, int sms, cudaStream_t s) {
     if (t.count <= 0) return cudaSuccess;
-    auto k = k_esc<VALS, VT>;
+    auto k = e.rank == kEscRankWindow ? k_esc<VALS, VT, kEscRankWindow>
+             : e.rank == kEscRankExact ? k_esc<VALS, VT, kEscRankExact>
+                                       : k_esc<VALS, VT, kEscRadix>;
     const size_t smem = (size_t)kEscWarps * esc_warp_bytes<VALS, VT>();
     esc_allow_smem(k, smem);
     int occ = 0;

@@ -10,16 +10,21 @@ constexpr int kEscTile = 256;      // products one warp tile holds
 constexpr int kEscRadixBits = 8;   // digit width of the radix sort
 // Bins whose largest Op_j is at most this sort by counting within columns
 // (see k_esc) instead of the radix sort.
-constexpr int kEscRankOpMax = 32;
+constexpr int kEscRankOpMax = 64;
+// How a tile is sorted: radix passes; ranks counted over an aligned window
+// around the column (composite keys of column, row and position fit 32
+// bits); ranks counted over the column alone (row and position fit).
+constexpr int kEscRadix = 0;
+constexpr int kEscRankWindow = 1;
+constexpr int kEscRankExact = 2;
 
 // Tile shape of one lane-group bin: columns per tile, row bits of the keys,
-// radix passes over the key bits, and whether the tile is sorted by ranks
-// counted within columns (rank != 0) instead.
+// radix passes over the key bits (none when ranked) and the sort's form.
 struct EscShape {
     int ct = 0;
     int rb = 0;
     int passes = 0;
-    int rank = 0;
+    int rank = kEscRadix;
 };
 
 // Shape of bin `bin` for a product whose forward passes number m rows; false

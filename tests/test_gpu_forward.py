@@ -423,6 +423,35 @@ def test_esc_tall_and_unsorted():
     assert_matches_oracle(C, A, B, nthreads=NCPU)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_esc_sort_forms(dtype):
+    # 2^21 rows, 15/16 of them holding entries (no row compaction: 21-bit rows
+    # in the keys).  Composite keys of (column place, row, position) fit 32
+    # bits in the bins of Op_j <= 32 and <= 64 (the count over a window) but
+    # not in those of <= 8 and <= 16 (the count over the column alone); the
+    # bins of <= 128 and <= 256 keep the radix sort.
+    rng = np.random.default_rng(31)
+    m, k = 1 << 21, 1 << 18
+    arow = rng.permutation(m).reshape(k, 8)
+    arow[1::2, 0] = arow[0::2, 0]  # A's columns 2q and 2q + 1 share a row
+    A = synth.from_coo(m, k, arow.ravel(), np.repeat(np.arange(k), 8), rng.standard_normal(m))
+    n = 6000
+    z = rng.integers(1, 9, size=n)  # Op_j = 8 z: the bins of <= 8 .. <= 64
+    z[:60] = rng.integers(9, 33, size=60)  # Op_j of 72..256
+    cols = []
+    for j in range(n):
+        r = 2 * rng.choice(k // 2, int(z[j]), replace=False) + rng.integers(0, 2, int(z[j]))
+        if j % 3 == 0 and z[j] >= 2:
+            r[1] = r[0] ^ 1  # both columns of a pair: C rows met twice
+        cols.append(r)
+    B = synth.from_coo(k, n, np.concatenate(cols), np.repeat(np.arange(n), z), rng.standard_normal(int(z.sum())))
+    C, plan = _run(A, B, dtype=dtype, small_accumulator="esc")
+    bins = plan.info()["bins"]
+    assert all(bins[b] > 0 for b in range(1, 7)), bins
+    assert C.rowidx.numel() < int(plan.op_counts().sum())  # equal keys were merged
+    assert_matches_oracle(C, A, B, nthreads=NCPU)
+
+
 def test_esc_sums_do_not_depend_on_timing():
     # every column light (Op_j <= 225): the whole C comes from ESC, whose sums
     # run in sorted order, so two calls agree bit for bit
