@@ -58,8 +58,16 @@ struct EscWarp<true, VT> {
     uint8_t idx[2][kEscTile];
 };
 
-// the exact-form rank sort keeps the sorted keys in cnt[1]
-static_assert((1 << kEscRadixBits) >= kEscTile, "radix count space holds a tile");
+// the exact-form rank sort keeps the sorted keys in cnt[1], the window form
+// the sorted values in cnt[0..1]
+static_assert((1 << kEscRadixBits) >= kEscTile, "radix count space holds a tile's keys");
+static_assert(sizeof(uint32_t) * 2 * (1 << kEscRadixBits) >= sizeof(double) * kEscTile,
+              "radix count space holds a tile's values");
+
+template <typename VT, typename W>
+__device__ __forceinline__ VT *wval(W &S) {
+    return reinterpret_cast<VT *>(&S.cnt[0][0]);
+}
 
 template <bool VALS, typename VT>
 __host__ __device__ constexpr size_t esc_warp_bytes() {
@@ -246,7 +254,9 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                             at += (int)(k4.x < me) + (int)(k4.y < me) + (int)(k4.z < me) + (int)(k4.w < me);
                         }
                         S.key[0][at] = me >> 8;
-                        if constexpr (VALS) S.idx[0][at] = (uint8_t)(me & 0xffu);
+                        // the value moves with its key, into the radix counts'
+                        // space (read above, free from here on)
+                        if constexpr (VALS) wval<VT>(S)[at] = S.val[me & 0xffu];
                     }
                 } else {
                     const uint32_t k = valid ? S.key[0][i] : 0u;
@@ -337,7 +347,7 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
         constexpr bool moved = FORM == kEscRankExact;
         const uint32_t *skey = moved ? S.cnt[1] : S.key[cur];
         const uint8_t *sidx = nullptr;
-        if constexpr (VALS) sidx = moved ? S.idx[1] : S.idx[cur];
+        if constexpr (VALS && FORM != kEscRankWindow) sidx = moved ? S.idx[1] : S.idx[cur];
         if (lane < 32) S.hstart[lane] = 0x7fffffff;  // columns without runs stay unset
         __syncwarp();
         int hbase = 0;
@@ -357,8 +367,15 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 const int64_t cbase = __shfl_sync(0xffffffffu, cb, c & 31);
                 const int64_t cc = __shfl_sync(0xffffffffu, ccap, c & 31);
                 if (head) {
-                    VT sum = S.val[sidx[i]];
-                    for (int m2 = i + 1; m2 < n && skey[m2] == k; ++m2) sum += S.val[sidx[m2]];
+                    VT sum;
+                    if constexpr (FORM == kEscRankWindow) {  // values in sorted order
+                        const VT *sv = wval<VT>(S);
+                        sum = sv[i];
+                        for (int m2 = i + 1; m2 < n && skey[m2] == k; ++m2) sum += sv[m2];
+                    } else {
+                        sum = S.val[sidx[i]];
+                        for (int m2 = i + 1; m2 < n && skey[m2] == k; ++m2) sum += S.val[sidx[m2]];
+                    }
                     const int64_t r = hr - S.hstart[c];
                     // a column with more runs than its place holds is reported
                     // below and not written past its place
