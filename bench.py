@@ -41,7 +41,8 @@ WORKLOADS = {
 L2_FLUSH_BYTES = 512 << 20
 METRIC = "SpGEMM GFLOP/s (2 x intermediate products / s)"
 INF = (1 << 63) - 1
-BIN_NAMES = (["empty"] + [f"hash_group_op<={o}" for o in (8, 16, 32, 64, 128, 256)]
+# light bins: ESC or lane-group hash tables, by the light-column accumulator
+BIN_NAMES = (["empty"] + [f"light_op<={o}" for o in (8, 16, 32, 64, 128, 256)]
              + [f"hash_cta_op<={o}" for o in (512, 1024, 2048, 4096, 8192)] + ["hash_global", "dense_spa"])
 DENSE_BIN = 13
 # thresholds of the sweep (Section 5.4 varies t the same way; t = 0 sends
@@ -88,38 +89,53 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# DRAM bytes (read + write) of one launch of the dominant kernel from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the R-MAT
-# workload at `scale`, with the algorithmic bytes of that launch; a
-# launch of another size reports the captured bytes scaled by its
-# algorithmic bytes.  Valid only for the kernel sources it was taken with:
-# the hash below covers the files that define that kernel, and any change
-# there reports null.
-MEASURED_TRAFFIC = {"bin": 13, "scale": 17, "bytes": 426855936 + 1975134720, "algorithmic_bytes": 5313831440,
-                    "sources_sha256_16": "fa872616b299795e",
-                    "sources": ("spgemm_internal.cuh", "kernels.cuh", "columns.cuh", "numeric.cu")}
+# DRAM bytes (read + write) of one launch of a dominant kernel from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), with the
+# algorithmic bytes of that launch; a launch of another size reports the
+# captured bytes scaled by its algorithmic bytes.  A record holds for its
+# workload, bin and light-column accumulators (None: the library's default)
+# in the default configuration otherwise, and only for the kernel sources
+# it was taken with: the hash covers the files that define the kernel, and
+# any change there reports null.
+MEASURED_TRAFFIC = (
+    {"workload": 3, "bin": 13, "capture": "R-MAT 2^17", "accumulators": (None,),
+     "bytes": 426855936 + 1975134720, "algorithmic_bytes": 5313831440,
+     "sources_sha256_16": "fa872616b299795e",
+     "sources": ("spgemm_internal.cuh", "kernels.cuh", "columns.cuh", "numeric.cu")},
+    {"workload": 2, "bin": 3, "capture": "random 2^20 (the same launch, ESC)", "accumulators": (None, "auto", "esc"),
+     "bytes": 304956928 + 120092928, "algorithmic_bytes": 338467476,
+     "sources_sha256_16": "07e8b77962cf6c76",
+     "sources": ("spgemm_internal.cuh", "kernels.cuh", "columns.cuh", "esc.cuh", "esc.cu")},
+)
 
 
-def measured_traffic(top_bin, top_bytes, args):
-    """(bytes, source) of the dominant kernel's DRAM traffic, or (None, why)."""
+def measured_traffic(top_bin, top_bytes, args, workload=None, accumulator=None):
+    """(bytes, source) of the dominant kernel's DRAM traffic, or (None, why).
+    `args`: the command line of the main workload; a side workload passes
+    args=None with its number and light-column accumulator."""
     import hashlib
-    t = MEASURED_TRAFFIC
-    if t is None:
+    if args is not None:
+        workload = args.workload
+        accumulator = getattr(args, "accumulator", None)
+        default_cfg = args.t is None and args.cta_threads is None and args.dense_cache is None
+    else:
+        default_cfg = True
+    if not MEASURED_TRAFFIC:
         return None, "no capture of the current kernel sources"
-    default_cfg = (args.t is None and args.cta_threads is None and args.dense_cache is None
-                   and getattr(args, "accumulator", None) is None)
-    if args.workload != 3 or top_bin != t["bin"] or not default_cfg:
-        return None, "no capture of this kernel, workload or configuration"
-    h = hashlib.sha256()
-    root = os.path.join(ROOT, "paper_2303_02471_gb300", "csrc")
-    for f in t["sources"]:
-        with open(os.path.join(root, f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest()[:16] != t["sources_sha256_16"]:
-        return None, "kernel sources changed since the capture"
-    scaled = int(round(t["bytes"] * top_bytes / t["algorithmic_bytes"]))
-    return scaled, (f"ncu capture of R-MAT 2^{t['scale']}, {t['bytes']:.4g} B per launch, "
-                    f"scaled by algorithmic bytes {top_bytes:.4g} / {t['algorithmic_bytes']:.4g}")
+    for t in MEASURED_TRAFFIC:
+        if t["workload"] != workload or t["bin"] != top_bin or not default_cfg or accumulator not in t["accumulators"]:
+            continue
+        h = hashlib.sha256()
+        root = os.path.join(ROOT, "paper_2303_02471_gb300", "csrc")
+        for f in t["sources"]:
+            with open(os.path.join(root, f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] != t["sources_sha256_16"]:
+            return None, "kernel sources changed since the capture"
+        scaled = int(round(t["bytes"] * top_bytes / t["algorithmic_bytes"]))
+        return scaled, (f"ncu capture of {t['capture']}, {t['bytes']:.4g} B per launch, "
+                        f"scaled by algorithmic bytes {top_bytes:.4g} / {t['algorithmic_bytes']:.4g}")
+    return None, "no capture of this kernel, workload or configuration"
 
 
 def algorithmic_bytes(A, B, products, nnzC, w):
@@ -440,7 +456,7 @@ def serial_bin_times(A_h, B_h, dev, cfg, flush, repeats=3):
     return np.median(np.array(out), axis=0)
 
 
-def product_report(prod, res, serial, peak, peak_kind, args, w=8):
+def product_report(prod, res, serial, peak, peak_kind, args, w=8, workload=None, accumulator=None):
     """Roofline of the dominant bin kernel and of the whole numeric pass,
     phase medians and per-bin figures of one product."""
     st = prod.stats
@@ -454,7 +470,7 @@ def product_report(prod, res, serial, peak, peak_kind, args, w=8):
     alg = algorithmic_bytes(prod.A_h, prod.B_h, prod.products, prod.nnz, w)
     num_ms = float(np.median(res["num"]))
     achieved = alg / (num_ms * 1e-3) / 1e9
-    traffic, tsrc = measured_traffic(top, top_bytes, args) if args is not None else (None, "not captured")
+    traffic, tsrc = measured_traffic(top, top_bytes, args, workload, accumulator)
     roof = {"bound": "hbm", "achieved": round(top_ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(top_ach / peak, 4), "traffic": traffic, "traffic_source": tsrc,
             "kernel": f"numeric bin {top} ({BIN_NAMES[top]})", "ms": round(top_ms, 4),
@@ -538,7 +554,8 @@ def measure_workload(k, args, dev, flush, steps, warmup, peak, peak_kind, cfg=No
     prod = Product(A_h, B_h, dev, cfg)
     res = time_steps(prod, steps, warmup, flush)
     serial = serial_bin_times(A_h, B_h, dev, cfg, flush)
-    roof, per_bin = product_report(prod, res, serial, peak, peak_kind, None)
+    roof, per_bin = product_report(prod, res, serial, peak, peak_kind, None, workload=k,
+                                   accumulator=cfg.small_accumulator)
     ms = float(np.median(res["step"]))
     out = {"workload": WORKLOADS[k], "products": int(prod.products), "nnz_C": int(prod.nnz), "t": prod.t,
            "value": round(2.0 * prod.products / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",

@@ -53,19 +53,32 @@ def _sources_hash(files):
 
 def test_traffic_is_reported_only_for_the_captured_kernel_and_case(monkeypatch):
     files = ("kernels.cuh", "numeric.cu")
-    rec = {"bin": 13, "scale": 17, "bytes": 4.0e9, "algorithmic_bytes": 5.0e9, "sources": files,
-           "sources_sha256_16": _sources_hash(files)}
-    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", rec)
+    rec = {"workload": 3, "bin": 13, "capture": "c", "accumulators": (None,), "bytes": 4.0e9,
+           "algorithmic_bytes": 5.0e9, "sources": files, "sources_sha256_16": _sources_hash(files)}
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", (rec,))
     got, src = bench.measured_traffic(13, 10.0e9, _args())
     assert got == 8 * 10 ** 9 and "scaled" in src  # scaled by the algorithmic bytes
     assert bench.measured_traffic(12, 10.0e9, _args())[0] is None
     assert bench.measured_traffic(13, 10.0e9, _args(t=100))[0] is None
     assert bench.measured_traffic(13, 10.0e9, _args(cta_threads=256))[0] is None
     assert bench.measured_traffic(13, 10.0e9, _args(workload=2))[0] is None
-    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", dict(rec, sources_sha256_16="0" * 16))
+    assert bench.measured_traffic(13, 10.0e9, _args(accumulator="hash"))[0] is None
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", (dict(rec, sources_sha256_16="0" * 16),))
     assert bench.measured_traffic(13, 10.0e9, _args())[0] is None
     monkeypatch.setattr(bench, "MEASURED_TRAFFIC", None)
     assert bench.measured_traffic(13, 10.0e9, _args())[0] is None
+
+
+def test_traffic_of_a_side_workload_by_its_accumulator(monkeypatch):
+    files = ("esc.cu",)
+    rec = {"workload": 2, "bin": 3, "capture": "c", "accumulators": (None, "esc"), "bytes": 3.0e8,
+           "algorithmic_bytes": 3.0e8, "sources": files, "sources_sha256_16": _sources_hash(files)}
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", (rec,))
+    assert bench.measured_traffic(3, 3.0e8, None, workload=2)[0] == 3 * 10 ** 8
+    assert bench.measured_traffic(3, 3.0e8, None, workload=2, accumulator="esc")[0] == 3 * 10 ** 8
+    assert bench.measured_traffic(3, 3.0e8, None, workload=2, accumulator="hash")[0] is None
+    assert bench.measured_traffic(3, 3.0e8, None, workload=3)[0] is None
+    assert bench.measured_traffic(3, 3.0e8, _args(workload=2))[0] == 3 * 10 ** 8
 
 
 def test_backward_bytes_count_each_array_once():
