@@ -104,7 +104,7 @@ MEASURED_TRAFFIC = (
      "sources": ("spgemm_internal.cuh", "kernels.cuh", "columns.cuh", "numeric.cu")},
     {"workload": 2, "bin": 3, "capture": "random 2^20 (the same launch, ESC)", "accumulators": (None, "auto", "esc"),
      "bytes": 304956928 + 120092928, "algorithmic_bytes": 338467476,
-     "sources_sha256_16": "07e8b77962cf6c76",
+     "sources_sha256_16": "f5428d17c03e75ac",
      "sources": ("spgemm_internal.cuh", "kernels.cuh", "columns.cuh", "esc.cuh", "esc.cu")},
 )
 

@@ -41,8 +41,10 @@
 
 namespace spg {
 
-// Shared memory of one warp.  The sort moves (key, index) pairs; the values
-// stay where the expansion put them and are read through the index.
+// Shared memory of one warp.  The radix sort and the exact rank form move
+// (key, index) pairs, the values staying where the expansion put them and
+// read through the index; the window rank form moves each value with its key
+// (into the bucket counters' space, free once the column bounds are read).
 template <bool VALS, typename VT>
 struct EscWarp {
     uint32_t key[2][kEscTile];
