@@ -619,7 +619,8 @@ def run_ours(args, rank, world):
                     others[str(k)] = measure_workload(k, args, dev, flush, max(3, min(args.steps, 10)), 3, *peak_w)
             # the light columns with hash tables in both phases (Section 3.2)
             # and with ESC in both phases (Section 4), beside the default
-            # (hash-table counts, ESC values)
+            # (ESC values, ESC counts in the bins of Op_j <= 64, hash-table
+            # counts in the larger ones)
             ksteps = max(3, min(args.steps, 10))
             for k in (2, 3):
                 entry = others.setdefault(str(k), {})

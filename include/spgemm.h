@@ -120,11 +120,12 @@ typedef struct {
     /* Accumulator of the lane-group bins (columns with Op_j <= 256):
      * SPG_ACC_HASH, the hash tables of Section 3.2, in both phases;
      * SPG_ACC_ESC, the ESC algorithm of Section 4 (the products of a tile of
-     * columns are expanded into shared memory, radix-sorted by (column, row)
-     * and compressed), in both phases; SPG_ACC_AUTO (default), hash tables
-     * for the symbolic phase's counts and ESC for the numeric phase (the
-     * cheaper of the two in each phase, measured on GB300).  A bin whose
-     * (column, row) keys do not fit 32 bits keeps hash tables.  All give the
+     * columns are expanded into shared memory, sorted by (column, row) and
+     * compressed), in both phases; SPG_ACC_AUTO (default), ESC for the
+     * numeric phase and, for the symbolic phase's counts, ESC in the bins of
+     * Op_j <= 64 (sorted by rank) and hash tables in the larger ones (the
+     * cheaper in each case, measured on GB300).  A bin whose (column, row)
+     * keys do not fit 32 bits keeps hash tables.  All give the
      * same C (the ESC sums do not depend on timing).  The single pass uses
      * ESC unless SPG_ACC_HASH.  Only the single products use it; the batched
      * calls keep hash tables. */

@@ -449,7 +449,8 @@ static spg_status prepare(spg_handle *handle, const spg_csc *A, const spg_csc *B
     CK(cudaMemsetAsync(&ctrl->work, 0, sizeof(ctrl->work), s));
 #undef CK
     // the numeric phase (and the single pass) take ESC unless hash tables
-    // were asked for; the symbolic phase counts with ESC only when asked
+    // were asked for; the symbolic phase counts with ESC when asked, and by
+    // default in the bins that ESC sorts by rank (sym_bin)
     if (c.small_accumulator != SPG_ACC_HASH)
         for (int b = BIN_WARP0; b < BIN_CTA0; ++b) P->esc[b] = esc_shape(b, P->mC, P->esc_shape_of[b]);
     // validation, row marks (mark, 3 scan kernels) and, when compacting,
@@ -491,7 +492,11 @@ spg_status spgemm_symbolic(spg_handle *handle, const spg_csc *A, const spg_csc *
         CK(cudaEventRecord(P->ss().fork, s));
     }
     auto sym_bin = [&](int b, cudaStream_t sb) {
-        if (P->esc[b] && c.small_accumulator == SPG_ACC_ESC)
+        // counting by rank (no sort, no compress) beat the hash tables on
+        // GB300; counting through the radix sort did not
+        const bool esc_counts = c.small_accumulator == SPG_ACC_ESC ||
+                                (c.small_accumulator == SPG_ACC_AUTO && P->esc_shape_of[b].rank != kEscRadix);
+        if (P->esc[b] && esc_counts)
             return launch_esc_bin(P->task(b), o, C_colptr, C_colptr, nullptr, nullptr, false, P->dtype,
                                   P->esc_shape_of[b], P->dev.sms, sb);
         // the symbolic CTA kernels carry no values: CTAs of up to 256 threads,

@@ -31,7 +31,9 @@
 // differs is reported); without values it counts the runs of each column
 // into cnt_out[j + 1] (the symbolic phase); with values and a count output it
 // writes each column at base[j] and its count into cnt_out[j + 1] (the
-// single-pass form, where base holds slots sized by Op_j).
+// single-pass form, where base holds slots sized by Op_j).  Counting with a
+// rank form needs no order: a product opens a run unless an earlier product
+// of its column has its row, so the same comparisons count the runs.
 //
 // Keys are 32-bit: the forward passes' rows and the tile's column places must
 // fit (rb + log2(columns per tile) <= 32); the host keeps hash tables
@@ -234,8 +236,13 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                 // composite keys above every other up to the next multiple of 4
                 const int n4 = (n + 3) & ~3;
                 if (n + lane < n4) S.key[1][n + lane] = 0xffffffffu;
-                __syncwarp();
             }
+            // counting only: no order is needed; a product repeats a row when
+            // an earlier product of its column has it (the same key above a
+            // smaller position), and a column's runs are its products less
+            // its repeats
+            if constexpr (!VALS) S.hstart[lane] = 0;
+            __syncwarp();
             for (int i0 = 0; i0 < n; i0 += 32) {
                 const int i = i0 + lane;
                 const bool valid = i < n;
@@ -250,22 +257,34 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                         // a later column or a pad: counting the smaller keys
                         // in [lo, hi) completes the place
                         const int lo = b & ~3, hi = (en + 3) & ~3;
-                        int at = lo;
-                        for (int q = lo; q < hi; q += 4) {
-                            const uint4 k4 = *reinterpret_cast<const uint4 *>(&S.key[1][q]);
-                            at += (int)(k4.x < me) + (int)(k4.y < me) + (int)(k4.z < me) + (int)(k4.w < me);
+                        if constexpr (VALS) {
+                            int at = lo;
+                            for (int q = lo; q < hi; q += 4) {
+                                const uint4 k4 = *reinterpret_cast<const uint4 *>(&S.key[1][q]);
+                                at += (int)(k4.x < me) + (int)(k4.y < me) + (int)(k4.z < me) + (int)(k4.w < me);
+                            }
+                            S.key[0][at] = me >> 8;
+                            // the value moves with its key, into the radix
+                            // counts' space (read above, free from here on)
+                            wval<VT>(S)[at] = S.val[me & 0xffu];
+                        } else {
+                            // x in [me - pos, me): the same key, earlier
+                            const uint32_t base = me & ~0xffu, pm = me & 0xffu;
+                            bool dup = false;
+                            for (int q = lo; q < hi; q += 4) {
+                                const uint4 k4 = *reinterpret_cast<const uint4 *>(&S.key[1][q]);
+                                dup |= (k4.x - base < pm) | (k4.y - base < pm) | (k4.z - base < pm) |
+                                       (k4.w - base < pm);
+                            }
+                            if (dup) atomicAdd(&S.hstart[c], 1);
                         }
-                        S.key[0][at] = me >> 8;
-                        // the value moves with its key, into the radix counts'
-                        // space (read above, free from here on)
-                        if constexpr (VALS) wval<VT>(S)[at] = S.val[me & 0xffu];
                     }
                 } else {
                     const uint32_t k = valid ? S.key[0][i] : 0u;
                     const int c = (int)(k >> e.rb) & 31;
                     const int b = __shfl_sync(0xffffffffu, pbeg, c);
                     const int en = __shfl_sync(0xffffffffu, pincl, c);
-                    if (valid) {
+                    if (valid && VALS) {
                         // the row composites of the column alone
                         int at = b, q = b;
                         for (; q + 4 <= en; q += 4) {
@@ -278,6 +297,11 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
                         // radix counts' space, free here
                         S.cnt[1][at] = k;
                         if constexpr (VALS) S.idx[1][at] = (uint8_t)i;
+                    } else if (valid) {
+                        const uint32_t base = me & ~0xffu, pm = me & 0xffu;
+                        bool dup = false;
+                        for (int q = b; q < en; ++q) dup |= S.key[1][q] - base < pm;
+                        if (dup) atomicAdd(&S.hstart[c], 1);
                     }
                 }
             }
@@ -345,63 +369,70 @@ __global__ void __launch_bounds__(kEscWarps * 32, esc_min_blocks<VALS>())
             }
             cur ^= 1;
         }
-        // ---- compress: the first key of each run writes the run's sum
-        constexpr bool moved = FORM == kEscRankExact;
-        const uint32_t *skey = moved ? S.cnt[1] : S.key[cur];
-        const uint8_t *sidx = nullptr;
-        if constexpr (VALS && FORM != kEscRankWindow) sidx = moved ? S.idx[1] : S.idx[cur];
-        if (lane < 32) S.hstart[lane] = 0x7fffffff;  // columns without runs stay unset
-        __syncwarp();
-        int hbase = 0;
-        for (int i0 = 0; i0 < n; i0 += 32) {
-            const int i = i0 + lane;
-            const bool valid = i < n;
-            const uint32_t k = valid ? skey[i] : 0u;
-            const uint32_t kp = valid && i > 0 ? skey[i - 1] : 0u;
-            const bool head = valid && (i == 0 || kp != k);
-            const unsigned hm = __ballot_sync(0xffffffffu, head);
-            const int hr = hbase + __popc(hm & lt);
-            hbase += __popc(hm);
-            const int c = (int)(k >> e.rb);
-            if (head && (i == 0 || (int)(kp >> e.rb) != c)) S.hstart[c] = hr;
+        // ---- compress: the first key of each run writes the run's sum (not
+        // needed when the ranks only counted runs)
+        constexpr bool ranked_counts = !VALS && FORM != kEscRadix;
+        int64_t cnt = 0;
+        if constexpr (ranked_counts) {
+            cnt = lane < nc ? (int64_t)S.cnt[0][lane] - S.hstart[lane] : 0;
+        } else {
+            constexpr bool moved = FORM == kEscRankExact;
+            const uint32_t *skey = moved ? S.cnt[1] : S.key[cur];
+            const uint8_t *sidx = nullptr;
+            if constexpr (VALS && FORM != kEscRankWindow) sidx = moved ? S.idx[1] : S.idx[cur];
+            if (lane < 32) S.hstart[lane] = 0x7fffffff;  // columns without runs stay unset
             __syncwarp();
-            if constexpr (VALS) {
-                const int64_t cbase = __shfl_sync(0xffffffffu, cb, c & 31);
-                const int64_t cc = __shfl_sync(0xffffffffu, ccap, c & 31);
-                if (head) {
-                    VT sum;
-                    if constexpr (FORM == kEscRankWindow) {  // values in sorted order
-                        const VT *sv = wval<VT>(S);
-                        sum = sv[i];
-                        for (int m2 = i + 1; m2 < n && skey[m2] == k; ++m2) sum += sv[m2];
-                    } else {
-                        sum = S.val[sidx[i]];
-                        for (int m2 = i + 1; m2 < n && skey[m2] == k; ++m2) sum += S.val[sidx[m2]];
-                    }
-                    const int64_t r = hr - S.hstart[c];
-                    // a column with more runs than its place holds is reported
-                    // below and not written past its place
-                    if (r < cc) {
-                        Crow[cbase + r] = ops.crow((int32_t)(k & rowmask));
-                        Cval[cbase + r] = sum;
+            int hbase = 0;
+            for (int i0 = 0; i0 < n; i0 += 32) {
+                const int i = i0 + lane;
+                const bool valid = i < n;
+                const uint32_t k = valid ? skey[i] : 0u;
+                const uint32_t kp = valid && i > 0 ? skey[i - 1] : 0u;
+                const bool head = valid && (i == 0 || kp != k);
+                const unsigned hm = __ballot_sync(0xffffffffu, head);
+                const int hr = hbase + __popc(hm & lt);
+                hbase += __popc(hm);
+                const int c = (int)(k >> e.rb);
+                if (head && (i == 0 || (int)(kp >> e.rb) != c)) S.hstart[c] = hr;
+                __syncwarp();
+                if constexpr (VALS) {
+                    const int64_t cbase = __shfl_sync(0xffffffffu, cb, c & 31);
+                    const int64_t cc = __shfl_sync(0xffffffffu, ccap, c & 31);
+                    if (head) {
+                        VT sum;
+                        if constexpr (FORM == kEscRankWindow) {  // values in sorted order
+                            const VT *sv = wval<VT>(S);
+                            sum = sv[i];
+                            for (int m2 = i + 1; m2 < n && skey[m2] == k; ++m2) sum += sv[m2];
+                        } else {
+                            sum = S.val[sidx[i]];
+                            for (int m2 = i + 1; m2 < n && skey[m2] == k; ++m2) sum += S.val[sidx[m2]];
+                        }
+                        const int64_t r = hr - S.hstart[c];
+                        // a column with more runs than its place holds is reported
+                        // below and not written past its place
+                        if (r < cc) {
+                            Crow[cbase + r] = ops.crow((int32_t)(k & rowmask));
+                            Cval[cbase + r] = sum;
+                        }
                     }
                 }
             }
-        }
-        __syncwarp();
-        // ---- per-column run counts: written (symbolic, single pass) or checked.
-        // A column's runs end where the next column with runs starts.
-        const int st = lane < nc ? S.hstart[lane] : 0x7fffffff;
-        int nxt = st;
+            __syncwarp();
+            // ---- per-column run counts: written (symbolic, single pass) or checked.
+            // A column's runs end where the next column with runs starts.
+            const int st = lane < nc ? S.hstart[lane] : 0x7fffffff;
+            int nxt = st;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int v = __shfl_down_sync(0xffffffffu, nxt, d);
-            if (lane + d < 32 && v < nxt) nxt = v;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_down_sync(0xffffffffu, nxt, d);
+                if (lane + d < 32 && v < nxt) nxt = v;
+            }
+            nxt = __shfl_down_sync(0xffffffffu, nxt, 1);
+            if (lane == 31 || nxt > hbase) nxt = hbase;
+            cnt = st == 0x7fffffff ? 0 : (int64_t)(nxt - st);
         }
-        nxt = __shfl_down_sync(0xffffffffu, nxt, 1);
-        if (lane == 31 || nxt > hbase) nxt = hbase;
         if (lane < nc) {
-            const int64_t cnt = st == 0x7fffffff ? 0 : (int64_t)(nxt - st);
             if (cnt_out) {
                 cnt_out[j + 1] = cnt;
                 if ((unsigned long long)cnt > my_max) my_max = (unsigned long long)cnt;
