@@ -114,7 +114,7 @@ __device__ __forceinline__ int64_t sym_dense_column(const TOps<float> &o, int32_
         for (int i = threadIdx.x; i < W4; i += blockDim.x) {
             const uint4 v = b4[i];
             cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-            if (keep) k4[i] = v;
+            if (keep) __stcs(k4 + i, v);  // read back by the numeric phase only
             b4[i] = make_uint4(0u, 0u, 0u, 0u);
         }
     } else {
