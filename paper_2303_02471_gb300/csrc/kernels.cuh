@@ -120,8 +120,11 @@ constexpr int kWalkBatch = 4;
 
 // ------------------------------------------------------------- CTA walk
 // Entries whose A column has at least this many entries are walked one
-// 32-product window at a time with a single owner per window.
-constexpr int kLongEntry = 32;
+// 32-product window at a time with a single owner per window (and, in the
+// value walk, a ring of windows); shorter ones share windows.  On R-MAT 16
+// measured as fast as 24 or 32 or up to 2 % faster (a half-full window in
+// the ring against the shared windows' search for their entries), 64 slower.
+constexpr int kLongEntry = 16;
 // Windows of a long entry in the register ring of the dense bin's value
 // walk (cta_walk's AHEAD; other callers keep one): four 256-thread CTAs per
 // SM leave 64 registers a thread, which hold five without spilling.
