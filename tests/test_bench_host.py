@@ -107,3 +107,36 @@ def test_roofline_kernel_is_the_bin_with_most_bytes():
     # the empty-column bin never counts
     st["count"][0] = 10 ** 6
     assert bench.dominant_bin(st, 8) == 6
+
+
+class _DoneProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_are_summarised(tmp_path):
+    # nvidia-smi --format=csv,noheader,nounits rows: index, clocks.sm,
+    # clocks.max.sm, power.draw, reasons.active, hw_slowdown,
+    # hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    p = tmp_path / "clocks.csv"
+    p.write_text("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+                 "0, [N/A], 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "a short line\n")
+    s = bench.ClockSampler()
+    s.proc, s.path = _DoneProc(), str(p)
+    out = s.stop()
+    assert out["samples"] == 4
+    assert out["sm_mhz"] == 2070.0  # median of the three numeric samples
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert not p.exists()
+
+
+def test_clock_sampler_without_nvidia_smi():
+    s = bench.ClockSampler()
+    assert s.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
